@@ -1,0 +1,352 @@
+/*
+ * kb_oracle.c -- plain, slow FP64 CPU oracle for the shift-and-stack likelihood
+ * search of Whidden et al., "Fast algorithms for slow moving asteroids"
+ * (arXiv:1901.02492).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant with the CUDA library; it is written directly from
+ * the definitions in the paper so that a reader can check it by eye:
+ *
+ *   weights            Sec. 2.1.5: inverse variance 1/sigma^2, zero for masked pixels
+ *   psi / phi images   Sec. 2.1.5: Psi(y) = sum_i n(x_i) T(x_i - y) / sigma_i^2,
+ *                                  Phi(y) = sum_i T(x_i - y)^2 / sigma_i^2
+ *                      (inverse-variance weighted cross-correlation with the PSF)
+ *   trajectory pixels  Sec. 2.1.5 / 2.2: y_i = y_0 + v t_i on the pixel grid
+ *   coadd              Sec. 2.1.5: Psi = sum_i Psi_i(y_i), Phi = sum_i Phi_i(y_i)
+ *   scores             Sec. 2.1.5: alpha_ML = Psi / Phi, nu = Psi / sqrt(Phi)
+ *   search             Sec. 2.2: evaluate nu for every start pixel and velocity
+ *
+ * Readings of points the paper leaves open (all listed in the design doc):
+ *   - a pixel is masked when its mask byte is non-zero, when n or sigma^2 is not
+ *     finite, when sigma^2 <= 0, or when n exceeds the optional bright-pixel
+ *     limit (Sec. 5.2); masked pixels get weight 0 and contribute exactly 0;
+ *   - PSF taps that fall outside the image contribute 0 (no renormalisation);
+ *   - trajectory pixel = start pixel + floor(v t + 1/2), evaluated in fixed
+ *     point: v_q = llround(v * 2^16), t_q = llround((t - t_min) * 2^20),
+ *     offset = floor((v_q * t_q + 2^35) / 2^36) in 64-bit integers;
+ *   - epochs whose trajectory pixel lies outside the image add nothing and are
+ *     not counted in nobs; a trajectory with Phi == 0 is not a valid result;
+ *   - per start pixel the k best valid trajectories are kept, ordered by
+ *     (nu descending, velocity index ascending), optionally only nu >= nu_min.
+ * The oracle sums epochs in time order (ties by epoch index).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int kbo_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void kbo_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* Sec. 2.1.5: masked pixels carry zero inverse variance, so they add nothing. */
+static int pixel_masked(float n, float var, const uint8_t *mask, size_t i, double bright_max) {
+    if (mask && mask[i]) return 1;
+    if (!isfinite(n) || !isfinite(var)) return 1;
+    if (var <= 0.0f) return 1;
+    if ((double)n > bright_max) return 1;
+    return 0;
+}
+
+/* Weights of one epoch: w = 1/sigma^2 and nw = n/sigma^2, both 0 where masked. */
+void kbo_weights(const float *sci, const float *var, const uint8_t *mask, size_t npix,
+                 double bright_max, double *w, double *nw) {
+    for (size_t i = 0; i < npix; ++i) {
+        if (pixel_masked(sci[i], var[i], mask, i, bright_max)) {
+            w[i] = 0.0;
+            nw[i] = 0.0;
+        } else {
+            w[i] = 1.0 / (double)var[i];
+            nw[i] = (double)sci[i] * w[i];
+        }
+    }
+}
+
+/*
+ * Sec. 2.1.5, psi and phi images of one epoch by direct 2-D cross-correlation
+ * over the full K x K PSF (r = K/2):
+ *   psi(y, x) = sum_{dy,dx in [-r,r]} nw(y+dy, x+dx) * T(dy, dx)
+ *   phi(y, x) = sum_{dy,dx in [-r,r]}  w(y+dy, x+dx) * T(dy, dx)^2
+ * T is stored row-major, T(dy, dx) = psf[(dy + r) * K + (dx + r)].
+ */
+static void psi_phi_epoch(const double *w, const double *nw, const float *psf, int H, int W, int K,
+                          double *psi, double *phi) {
+    const int r = K / 2;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            double sp = 0.0, sf = 0.0;
+            for (int dy = -r; dy <= r; ++dy) {
+                int yy = y + dy;
+                if (yy < 0 || yy >= H) continue;
+                for (int dx = -r; dx <= r; ++dx) {
+                    int xx = x + dx;
+                    if (xx < 0 || xx >= W) continue;
+                    double t = (double)psf[(dy + r) * K + (dx + r)];
+                    size_t i = (size_t)yy * W + xx;
+                    sp += nw[i] * t;
+                    sf += w[i] * (t * t);
+                }
+            }
+            psi[(size_t)y * W + x] = sp;
+            phi[(size_t)y * W + x] = sf;
+        }
+    }
+}
+
+/* All epochs: inputs [N][H][W] (mask may be NULL), psf [N][K][K], outputs [N][H][W]. */
+void kbo_psi_phi(const float *sci, const float *var, const uint8_t *mask, const float *psf, int N, int H,
+                 int W, int K, double bright_max, double *psi, double *phi) {
+    size_t npix = (size_t)H * W;
+    double *w = (double *)malloc(npix * sizeof(double));
+    double *nw = (double *)malloc(npix * sizeof(double));
+    for (int e = 0; e < N; ++e) {
+        kbo_weights(sci + e * npix, var + e * npix, mask ? mask + e * npix : NULL, npix, bright_max, w, nw);
+        psi_phi_epoch(w, nw, psf + (size_t)e * K * K, H, W, K, psi + e * npix, phi + e * npix);
+    }
+    free(w);
+    free(nw);
+}
+
+/* The same definition evaluated at one pixel (x, y) of one epoch. */
+void kbo_psi_phi_at(const float *sci, const float *var, const uint8_t *mask, const float *psf, int H, int W,
+                    int K, double bright_max, int x, int y, double *psi, double *phi) {
+    const int r = K / 2;
+    double sp = 0.0, sf = 0.0;
+    for (int dy = -r; dy <= r; ++dy) {
+        int yy = y + dy;
+        if (yy < 0 || yy >= H) continue;
+        for (int dx = -r; dx <= r; ++dx) {
+            int xx = x + dx;
+            if (xx < 0 || xx >= W) continue;
+            size_t i = (size_t)yy * W + xx;
+            if (pixel_masked(sci[i], var[i], mask, i, bright_max)) continue;
+            double t = (double)psf[(dy + r) * K + (dx + r)];
+            double w = 1.0 / (double)var[i];
+            sp += ((double)sci[i] * w) * t;
+            sf += w * (t * t);
+        }
+    }
+    *psi = sp;
+    *phi = sf;
+}
+
+/* ---- trajectory pixels (fixed point) ------------------------------------ */
+
+int64_t kbo_quant_velocity(double v) { return llround(v * 65536.0); }        /* 2^16 per px/day */
+int64_t kbo_quant_time(double dt) { return llround(dt * 1048576.0); }        /* 2^20 per day */
+
+/* floor(a / 2^36) for any signed 64-bit a, written without relying on >> of negatives */
+static int64_t floor_div_2p36(int64_t a) {
+    const int64_t d = (int64_t)1 << 36;
+    if (a >= 0) return a / d;
+    return -((-a + d - 1) / d);
+}
+
+/* Pixel offset of one velocity component at one time: floor(v t + 1/2) in fixed point. */
+int64_t kbo_offset(int64_t vq, int64_t tq) {
+    return floor_div_2p36(vq * tq + ((int64_t)1 << 35));
+}
+
+/*
+ * Offsets for every velocity and epoch, dx/dy laid out [V][N] in the caller's
+ * epoch order; times are relative to the earliest epoch (the search starts at
+ * every pixel of the earliest image, Sec. 3.2).
+ */
+void kbo_offsets(const double *times, int N, const double *vx, const double *vy, int V, int32_t *dx,
+                 int32_t *dy) {
+    double tmin = times[0];
+    for (int e = 1; e < N; ++e)
+        if (times[e] < tmin) tmin = times[e];
+    for (int v = 0; v < V; ++v) {
+        int64_t qx = kbo_quant_velocity(vx[v]), qy = kbo_quant_velocity(vy[v]);
+        for (int e = 0; e < N; ++e) {
+            int64_t tq = kbo_quant_time(times[e] - tmin);
+            dx[(size_t)v * N + e] = (int32_t)kbo_offset(qx, tq);
+            dy[(size_t)v * N + e] = (int32_t)kbo_offset(qy, tq);
+        }
+    }
+}
+
+/* Epoch indices sorted by (time, index): the order in which the oracle sums. */
+static void time_order(const double *times, int N, int *order) {
+    for (int e = 0; e < N; ++e) order[e] = e;
+    for (int i = 1; i < N; ++i) { /* insertion sort, stable */
+        int c = order[i], j = i - 1;
+        while (j >= 0 && times[order[j]] > times[c]) {
+            order[j + 1] = order[j];
+            --j;
+        }
+        order[j + 1] = c;
+    }
+}
+
+/* ---- coadd sums and scores ---------------------------------------------- */
+
+typedef struct {
+    int32_t x0, y0, vidx, nobs;
+    double psi, phi, nu, alpha;
+} kbo_rec;
+
+/*
+ * Sec. 2.1.5 coadd of one trajectory: Psi = sum_t psi_t(y_t), Phi = sum_t phi_t(y_t)
+ * over the epochs whose pixel is inside the image, in time order.
+ */
+static void trajectory_sums(const double *psi, const double *phi, int N, int H, int W, const int32_t *dx,
+                            const int32_t *dy, const int *order, int x0, int y0, double *P, double *F,
+                            int *nobs) {
+    size_t npix = (size_t)H * W;
+    double sp = 0.0, sf = 0.0;
+    int n = 0;
+    for (int j = 0; j < N; ++j) {
+        int e = order[j];
+        int x = x0 + dx[e], y = y0 + dy[e];
+        if (x < 0 || x >= W || y < 0 || y >= H) continue;
+        size_t i = (size_t)e * npix + (size_t)y * W + x;
+        sp += psi[i];
+        sf += phi[i];
+        ++n;
+    }
+    *P = sp;
+    *F = sf;
+    *nobs = n;
+}
+
+/* Sums for every start pixel at one velocity: Psi, Phi, nobs maps [H][W]. */
+void kbo_sums_one_velocity(const double *psi, const double *phi, const double *times, int N, int H, int W,
+                           const int32_t *dx_v, const int32_t *dy_v, double *Pmap, double *Fmap,
+                           int32_t *nobs) {
+    int order[4096];
+    time_order(times, N, order);
+#pragma omp parallel for schedule(static)
+    for (int y0 = 0; y0 < H; ++y0)
+        for (int x0 = 0; x0 < W; ++x0) {
+            int n;
+            size_t i = (size_t)y0 * W + x0;
+            trajectory_sums(psi, phi, N, H, W, dx_v, dy_v, order, x0, y0, &Pmap[i], &Fmap[i], &n);
+            nobs[i] = n;
+        }
+}
+
+/* (nu desc, vidx asc): does a rank before b?  Empty slots (vidx < 0) rank last. */
+static int ranks_before(double a_nu, int a_v, const kbo_rec *b) {
+    if (b->vidx < 0) return 1;
+    if (a_nu != b->nu) return a_nu > b->nu;
+    return a_v < b->vidx;
+}
+
+/*
+ * Sec. 2.2 exhaustive search at one start pixel: every velocity, scores of Sec.
+ * 2.1.5, keep the k best valid trajectories (Phi > 0 and nu >= nu_min).
+ */
+static void search_pixel(const double *psi, const double *phi, int N, int H, int W, const int32_t *dx,
+                         const int32_t *dy, int V, const int *order, int k, double nu_min, int x0, int y0,
+                         kbo_rec *out) {
+    for (int i = 0; i < k; ++i) {
+        out[i].x0 = x0;
+        out[i].y0 = y0;
+        out[i].vidx = -1;
+        out[i].nobs = 0;
+        out[i].psi = 0.0;
+        out[i].phi = 0.0;
+        out[i].nu = -INFINITY;
+        out[i].alpha = 0.0;
+    }
+    for (int v = 0; v < V; ++v) {
+        double P, F;
+        int nobs;
+        trajectory_sums(psi, phi, N, H, W, dx + (size_t)v * N, dy + (size_t)v * N, order, x0, y0, &P, &F,
+                        &nobs);
+        if (!(F > 0.0)) continue;
+        double nu = P / sqrt(F);
+        double alpha = P / F;
+        if (!(nu >= nu_min)) continue;
+        /* insertion into the sorted list */
+        int pos = k;
+        for (int i = 0; i < k; ++i)
+            if (ranks_before(nu, v, &out[i])) {
+                pos = i;
+                break;
+            }
+        if (pos == k) continue;
+        for (int i = k - 1; i > pos; --i) out[i] = out[i - 1];
+        out[pos].vidx = v;
+        out[pos].nobs = nobs;
+        out[pos].psi = P;
+        out[pos].phi = F;
+        out[pos].nu = nu;
+        out[pos].alpha = alpha;
+    }
+}
+
+/* Search over a list of start pixels (px[i], py[i]); out is [npix][k]. */
+void kbo_search_pixels(const double *psi, const double *phi, const double *times, int N, int H, int W,
+                       const int32_t *dx, const int32_t *dy, int V, int k, double nu_min, const int32_t *px,
+                       const int32_t *py, int64_t npix, kbo_rec *out) {
+    int order[4096];
+    time_order(times, N, order);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < npix; ++i)
+        search_pixel(psi, phi, N, H, W, dx, dy, V, order, k, nu_min, px[i], py[i], out + (size_t)i * k);
+}
+
+/* Search over the rectangle [x_lo, x_hi) x [y_lo, y_hi); out is [rows][cols][k]. */
+void kbo_search_region(const double *psi, const double *phi, const double *times, int N, int H, int W,
+                       const int32_t *dx, const int32_t *dy, int V, int k, double nu_min, int x_lo, int x_hi,
+                       int y_lo, int y_hi, kbo_rec *out) {
+    int order[4096];
+    time_order(times, N, order);
+    int cols = x_hi - x_lo;
+    int64_t n = (int64_t)(y_hi - y_lo) * cols;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        int x0 = x_lo + (int)(i % cols), y0 = y_lo + (int)(i / cols);
+        search_pixel(psi, phi, N, H, W, dx, dy, V, order, k, nu_min, x0, y0, out + (size_t)i * k);
+    }
+}
+
+/*
+ * One trajectory from the raw inputs, without precomputed planes: psi/phi at each
+ * trajectory pixel by the point definition, coadded in time order.  Used to check
+ * sampled outputs of full-size searches.
+ */
+void kbo_trajectory_from_images(const float *sci, const float *var, const uint8_t *mask, const float *psf,
+                                const double *times, int N, int H, int W, int K, double bright_max,
+                                const int32_t *dx_v, const int32_t *dy_v, int x0, int y0, double *P,
+                                double *F, int32_t *nobs) {
+    int order[4096];
+    time_order(times, N, order);
+    size_t npix = (size_t)H * W;
+    double sp = 0.0, sf = 0.0;
+    int n = 0;
+    for (int j = 0; j < N; ++j) {
+        int e = order[j];
+        int x = x0 + dx_v[e], y = y0 + dy_v[e];
+        if (x < 0 || x >= W || y < 0 || y >= H) continue;
+        double a, b;
+        kbo_psi_phi_at(sci + e * npix, var + e * npix, mask ? mask + e * npix : NULL,
+                       psf + (size_t)e * K * K, H, W, K, bright_max, x, y, &a, &b);
+        sp += a;
+        sf += b;
+        ++n;
+    }
+    *P = sp;
+    *F = sf;
+    *nobs = n;
+}

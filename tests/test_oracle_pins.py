@@ -1,0 +1,351 @@
+"""Pins of the FP64 oracle against things other than itself (no GPU needed).
+
+Each test names the paper passage whose definition it pins and the independent
+source of the expected value: a library routine (scipy), a closed form, exact
+rational arithmetic, a distributional law, a different formulation (numpy
+slicing) or brute-force enumeration.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy import signal, stats
+
+import oracle
+import synth
+
+
+def _weights(sci, var, mask=None, bright=np.inf):
+    bad = ~np.isfinite(sci) | ~np.isfinite(var) | (var <= 0) | (sci > bright)
+    if mask is not None:
+        bad |= mask != 0
+    w = np.where(bad, 0.0, 1.0 / np.where(bad, 1.0, var.astype(np.float64)))
+    nw = np.where(bad, 0.0, np.where(bad, 0.0, sci.astype(np.float64)) * w)
+    return w, nw
+
+
+def _asym_psf(K, rng):
+    p = rng.uniform(0.1, 1.0, (K, K)).astype(np.float32)
+    return (p / p.sum()).astype(np.float32)
+
+
+# ---------------------------------------------------------------- psi / phi images (Sec. 2.1.5)
+
+def test_psi_phi_equals_scipy_correlate2d():
+    """psi = corr(n/s^2, T), phi = corr(1/s^2, T^2) with zero fill: scipy.signal.correlate2d."""
+    rng = np.random.default_rng(10)
+    N, H, W, K = 3, 23, 17, 7
+    sci = rng.normal(0, 3, (N, H, W)).astype(np.float32)
+    var = rng.uniform(0.5, 4.0, (N, H, W)).astype(np.float32)
+    sci[0, 3, 4] = np.nan
+    var[1, 10, 2] = -1.0
+    var[2, 0, 0] = np.inf
+    mask = (rng.random((N, H, W)) < 0.05).astype(np.uint8)
+    psf = np.stack([_asym_psf(K, rng) for _ in range(N)])  # asymmetric: correlation != convolution
+    psi, phi = oracle.psi_phi(sci, var, mask, psf)
+    for e in range(N):
+        w, nw = _weights(sci[e], var[e], mask[e])
+        k = psf[e].astype(np.float64)
+        exp_psi = signal.correlate2d(nw, k, mode="same", boundary="fill", fillvalue=0.0)
+        exp_phi = signal.correlate2d(w, k * k, mode="same", boundary="fill", fillvalue=0.0)
+        np.testing.assert_allclose(psi[e], exp_psi, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(phi[e], exp_phi, rtol=1e-12, atol=1e-14)
+
+
+def test_psi_of_delta_image_is_reflected_psf():
+    """Closed form: a unit delta at c gives psi(c - d) = T(d)/s^2 (cross-correlation orientation)."""
+    rng = np.random.default_rng(11)
+    H, W, K = 15, 19, 5
+    r = K // 2
+    sci = np.zeros((1, H, W), np.float32)
+    cy, cx = 7, 9
+    sci[0, cy, cx] = 1.0
+    var = np.full((1, H, W), 2.0, np.float32)
+    psf = _asym_psf(K, rng)[None]
+    psi, _ = oracle.psi_phi(sci, var, None, psf)
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            assert psi[0, cy - dy, cx - dx] == pytest.approx(psf[0, dy + r, dx + r] / 2.0, rel=1e-14)
+    assert np.count_nonzero(psi) == K * K
+
+
+def test_constant_image_interior_closed_form():
+    """Constant n = c and s^2 = V, no mask: interior psi = c/V * sum T, phi = sum T^2 / V; edges smaller."""
+    H, W, K = 20, 24, 7
+    r = K // 2
+    psf = synth.gaussian_psf(K, 1.3)[None]
+    sci = np.full((1, H, W), 3.0, np.float32)
+    var = np.full((1, H, W), 5.0, np.float32)
+    psi, phi = oracle.psi_phi(sci, var, None, psf)
+    t = psf[0].astype(np.float64)
+    assert np.allclose(psi[0, r:H - r, r:W - r], 3.0 / 5.0 * t.sum(), rtol=1e-13)
+    assert np.allclose(phi[0, r:H - r, r:W - r], (t * t).sum() / 5.0, rtol=1e-13)
+    assert phi[0, 0, 0] < phi[0, H // 2, W // 2]  # zero padding, no renormalisation
+
+
+def test_masked_pixels_add_nothing():
+    """Sec. 2.1.5: masked pixels get zero weight, so their values cannot change psi or phi."""
+    rng = np.random.default_rng(12)
+    st = synth.small_stack(12, 2, 16, 18, K=5, mask_frac=0.1)
+    psi1, phi1 = oracle.psi_phi(st.sci, st.var, st.mask, st.psf)
+    sci2, var2 = st.sci.copy(), st.var.copy()
+    m = st.mask != 0
+    sci2[m] = rng.normal(0, 1e6, m.sum())
+    var2[m] = rng.uniform(-5, 5, m.sum())
+    psi2, phi2 = oracle.psi_phi(sci2, var2, st.mask, st.psf)
+    assert np.array_equal(psi1, psi2) and np.array_equal(phi1, phi2)
+
+
+def test_bright_pixel_limit_masks():
+    """Sec. 5.2 bright-pixel mask: pixels above the limit behave as masked."""
+    st = synth.small_stack(13, 1, 12, 12, K=5)
+    sci = st.sci.copy()
+    sci[0, 5, 6] = 500.0
+    mask = np.zeros(sci.shape, np.uint8)
+    mask[0, 5, 6] = 1
+    a = oracle.psi_phi(sci, st.var, None, st.psf, bright_max=120.0)
+    b = oracle.psi_phi(sci, st.var, mask, st.psf)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_point_definition_matches_planes():
+    st = synth.small_stack(14, 3, 14, 11, K=5, nan_frac=0.05, mask_frac=0.05)
+    psi, phi = oracle.psi_phi(st.sci, st.var, st.mask, st.psf)
+    for (e, y, x) in [(0, 0, 0), (1, 7, 5), (2, 13, 10), (2, 3, 9)]:
+        a, b = oracle.psi_phi_at(st.sci[e], st.var[e], st.mask[e], st.psf[e], x, y)
+        assert a == pytest.approx(psi[e, y, x], rel=1e-13, abs=1e-15)
+        assert b == pytest.approx(phi[e, y, x], rel=1e-13, abs=1e-15)
+
+
+# ---------------------------------------------------------------- trajectory pixels
+
+def _exact_offset(v, dt):
+    """floor(v_q t_q / 2^36 + 1/2) with exact rationals (v_q, t_q: nearest integers, ties away)."""
+    def rnd(x):  # llround: nearest, halves away from zero, on the exact value of the double
+        f = Fraction(x)
+        a = abs(f)
+        n = math.floor(a + Fraction(1, 2))
+        return n if f >= 0 else -n
+    vq = rnd(Fraction(v) * 65536)
+    tq = rnd(Fraction(dt) * 1048576)
+    return math.floor(Fraction(vq * tq, 2 ** 36) + Fraction(1, 2)), vq, tq
+
+
+def test_offsets_match_exact_rationals():
+    rng = np.random.default_rng(20)
+    times = np.concatenate([[3.25], 3.25 + np.sort(rng.uniform(0, 3.0, 9))])
+    vx = rng.uniform(-600, 600, 40)
+    vy = rng.uniform(-600, 600, 40)
+    dx, dy = oracle.offsets(times, vx, vy)
+    for v in range(40):
+        for e in range(times.size):
+            dt = times[e] - times.min()
+            assert dx[v, e] == _exact_offset(vx[v], dt)[0]
+            assert dy[v, e] == _exact_offset(vy[v], dt)[0]
+
+
+def test_offsets_round_half_up_and_reference_epoch():
+    """v t exactly at k + 1/2 rounds up (also for negatives); the earliest epoch has offset 0."""
+    cases = [(1.5, 1.0, 2), (2.5, 1.0, 3), (-2.5, 1.0, -2), (-1.5, 1.0, -1), (0.75, 2.0, 2),
+             (-0.25, 2.0, 0), (3.0, 0.5, 2), (-3.0, 0.5, -1), (0.0, 5.0, 0), (10.0, 0.0, 0)]
+    for v, t, expect in cases:
+        times = np.array([7.0, 7.0 + t]) if t > 0 else np.array([7.0])
+        dx, _ = oracle.offsets(times, np.array([v]), np.array([0.0]))
+        assert dx[0, 0] == 0
+        if t > 0:
+            assert dx[0, 1] == expect, (v, t)
+    # unordered epochs: offsets relative to the minimum time
+    dx, dy = oracle.offsets(np.array([2.0, 1.0, 1.5]), np.array([4.0]), np.array([-4.0]))
+    assert list(dx[0]) == [4, 0, 2] and list(dy[0]) == [-4, 0, -2]
+
+
+# ---------------------------------------------------------------- coadd, scores, search (Sec. 2.1.5, 2.2)
+
+def _stamp_psf(img, cy, cx, psf, scale):
+    K = psf.shape[0]
+    r = K // 2
+    img[cy - r:cy + r + 1, cx - r:cx + r + 1] += (scale * psf).astype(np.float32)
+
+
+def test_noiseless_injection_closed_form():
+    """A noiseless source f*T_t on the trajectory pixels gives Psi_t = f S_t, Phi_t = S_t with
+    S_t = sum T_t^2 / V_t, hence alpha = f and nu = f sqrt(sum_t S_t); it is also the top result."""
+    rng = np.random.default_rng(30)
+    N, H, W, K = 4, 40, 44, 7
+    times = np.array([0.0, 0.4, 1.1, 1.7])
+    vx, vy = synth.velocity_grid(8, 5, -math.pi, math.pi, 2.0, 6.0, angle_endpoint=False)
+    dx, dy = oracle.offsets(times, vx, vy)
+    vt = 13
+    x0, y0 = 20, 22
+    f = 8.0  # power of two: the float32 stamp f*T is exact
+    V_t = rng.uniform(1.0, 3.0, N).astype(np.float32)
+    psf = np.stack([_asym_psf(K, rng) for _ in range(N)])
+    sci = np.zeros((N, H, W), np.float32)
+    var = np.empty((N, H, W), np.float32)
+    for e in range(N):
+        var[e] = V_t[e]
+        _stamp_psf(sci[e], y0 + dy[vt, e], x0 + dx[vt, e], psf[e], f)
+    S = np.array([(psf[e].astype(np.float64) ** 2).sum() / np.float64(V_t[e]) for e in range(N)])
+    psi, phi = oracle.psi_phi(sci, var, None, psf)
+    rec = oracle.search_pixels(psi, phi, times, dx, dy, 3, [x0], [y0])[0]
+    P, F, n = oracle.sums_one_velocity(psi, phi, times, dx[vt], dy[vt])
+    assert P[y0, x0] == pytest.approx(f * S.sum(), rel=1e-12)
+    assert F[y0, x0] == pytest.approx(S.sum(), rel=1e-12)
+    assert n[y0, x0] == N
+    top = rec[0]
+    assert np.array_equal(dx[top["vidx"]], dx[vt]) and np.array_equal(dy[top["vidx"]], dy[vt])
+    assert top["nu"] == pytest.approx(f * math.sqrt(S.sum()), rel=1e-12)
+    assert top["alpha"] == pytest.approx(f, rel=1e-12)
+    assert top["nobs"] == N and rec[1]["nu"] < top["nu"]
+
+
+def test_noise_only_nu_is_standard_normal():
+    """With n ~ N(0, s^2) per pixel, Var(psi_t) = phi_t, so nu of a fixed trajectory is N(0, 1)."""
+    rng = np.random.default_rng(31)
+    N, H, W, K = 5, 160, 170, 7
+    times = np.array([0.0, 0.3, 0.9, 1.2, 2.0])
+    var = rng.uniform(1.0, 6.0, (N, H, W)).astype(np.float32)
+    sci = (rng.standard_normal((N, H, W)) * np.sqrt(var)).astype(np.float32)
+    psf = np.stack([synth.gaussian_psf(K, s) for s in rng.uniform(0.9, 1.4, N)])
+    vx, vy = np.array([4.0]), np.array([-3.0])
+    dx, dy = oracle.offsets(times, vx, vy)
+    psi, phi = oracle.psi_phi(sci, var, None, psf)
+    P, F, n = oracle.sums_one_velocity(psi, phi, times, dx[0], dy[0])
+    r = K // 2
+    ys = np.arange(r + 8, H - r - 8, K + 1)   # disjoint PSF supports -> independent samples
+    xs = np.arange(r + 1, W - r - 10, K + 1)
+    nu = (P / np.sqrt(F))[np.ix_(ys, xs)].ravel()
+    m = nu.size
+    assert m > 300
+    assert abs(nu.mean()) < 4.0 / math.sqrt(m)
+    assert abs(nu.var() - 1.0) < 4.0 * math.sqrt(2.0 / m)
+    assert stats.kstest(nu, "norm").pvalue > 1e-3
+
+
+def _shift_stack(planes, times, dxv, dyv):
+    """Textbook shift-and-stack with numpy slicing: sum_t planes_t(y + dy_t, x + dx_t), zero outside."""
+    N, H, W = planes.shape
+    out = np.zeros((H, W))
+    cnt = np.zeros((H, W), np.int32)
+    for e in np.argsort(times, kind="stable"):
+        sx, sy = int(dxv[e]), int(dyv[e])
+        ys, ye = max(0, -sy), min(H, H - sy)
+        xs, xe = max(0, -sx), min(W, W - sx)
+        if ys >= ye or xs >= xe:
+            continue
+        out[ys:ye, xs:xe] += planes[e, ys + sy:ye + sy, xs + sx:xe + sx]
+        cnt[ys:ye, xs:xe] += 1
+    return out, cnt
+
+
+def test_coadd_equals_shift_and_stack():
+    """Sec. 2.1.5: summing psi along the trajectory equals shifting the planes and stacking them."""
+    st = synth.small_stack(32, 5, 30, 26, K=5, nan_frac=0.02, s_hi=9.0)
+    psi, phi = oracle.psi_phi(st.sci, st.var, None, st.psf)
+    dx, dy = oracle.offsets(st.times, st.vx, st.vy)
+    for v in [0, 7, 21, 40, 63]:
+        P, F, n = oracle.sums_one_velocity(psi, phi, st.times, dx[v], dy[v])
+        P2, c2 = _shift_stack(psi, st.times, dx[v], dy[v])
+        F2, _ = _shift_stack(phi, st.times, dx[v], dy[v])
+        np.testing.assert_allclose(P, P2, rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(F, F2, rtol=1e-13, atol=1e-15)
+        assert np.array_equal(n, c2)
+
+
+def _brute_topk(psi, phi, times, dx, dy, k, nu_min=-np.inf):
+    V = dx.shape[0]
+    N, H, W = psi.shape
+    nu = np.full((V, H, W), -np.inf)
+    for v in range(V):
+        P, _ = _shift_stack(psi, times, dx[v], dy[v])
+        F, _ = _shift_stack(phi, times, dx[v], dy[v])
+        ok = F > 0
+        nu[v][ok] = P[ok] / np.sqrt(F[ok])
+    out = np.full((H, W, k), -1, np.int64)
+    for y in range(H):
+        for x in range(W):
+            col = nu[:, y, x]
+            valid = np.nonzero((col > -np.inf) & (col >= nu_min))[0]
+            order = valid[np.lexsort((valid, -col[valid]))]
+            out[y, x, :min(k, order.size)] = order[:k]
+    return out, nu
+
+
+def test_topk_equals_brute_force_sort_with_exact_ties():
+    """Sec. 2.2 exhaustive search: the kept list is the full sort by (nu desc, vidx asc); duplicated
+    velocities give bit-identical sums (exact ties broken by index)."""
+    st = synth.small_stack(33, 3, 9, 11, K=3, mask_frac=0.05, n_angles=4, n_speeds=3, s_hi=3.0)
+    vx = np.concatenate([st.vx, st.vx[:4], [0.01, 0.02]])
+    vy = np.concatenate([st.vy, st.vy[:4], [0.0, 0.0]])
+    psi, phi = oracle.psi_phi(st.sci, st.var, st.mask, st.psf)
+    dx, dy = oracle.offsets(st.times, vx, vy)
+    k = 5
+    rec = oracle.search_region(psi, phi, st.times, dx, dy, k)
+    expect, nu = _brute_topk(psi, phi, st.times, dx, dy, k)
+    assert np.array_equal(rec["vidx"], expect)
+    got = rec["nu"][expect >= 0]
+    ref = np.take_along_axis(nu.transpose(1, 2, 0), np.maximum(expect, 0), axis=2)[expect >= 0]
+    np.testing.assert_allclose(got, ref, rtol=1e-13)
+    # thresholded list keeps only nu >= nu_min, in the same order
+    rec2 = oracle.search_region(psi, phi, st.times, dx, dy, k, nu_min=0.5)
+    expect2, _ = _brute_topk(psi, phi, st.times, dx, dy, k, nu_min=0.5)
+    assert np.array_equal(rec2["vidx"], expect2)
+
+
+def test_scaling_laws_exact():
+    """n -> 2n doubles nu and alpha; s^2 -> 4 s^2 halves nu and keeps alpha (exact in binary FP)."""
+    st = synth.small_stack(34, 4, 12, 13, K=5, var_lo=1.0, var_hi=3.0)
+    dx, dy = oracle.offsets(st.times, st.vx, st.vy)
+    base = oracle.search_region(*oracle.psi_phi(st.sci, st.var, None, st.psf), st.times, dx, dy, 3)
+    two = oracle.search_region(*oracle.psi_phi(2 * st.sci, st.var, None, st.psf), st.times, dx, dy, 3)
+    four = oracle.search_region(*oracle.psi_phi(st.sci, 4 * st.var, None, st.psf), st.times, dx, dy, 3)
+    assert np.array_equal(two["vidx"], base["vidx"]) and np.array_equal(two["nu"], 2 * base["nu"])
+    assert np.array_equal(two["alpha"], 2 * base["alpha"])
+    assert np.array_equal(four["vidx"], base["vidx"]) and np.array_equal(four["nu"], base["nu"] / 2)
+    assert np.array_equal(four["alpha"], base["alpha"])
+
+
+def test_epoch_permutation_invariance():
+    """Permuting (image, time) pairs together leaves every result unchanged."""
+    st = synth.small_stack(35, 5, 12, 10, K=5, nan_frac=0.03)
+    perm = np.array([3, 0, 4, 2, 1])
+    dx, dy = oracle.offsets(st.times, st.vx, st.vy)
+    a = oracle.search_region(*oracle.psi_phi(st.sci, st.var, None, st.psf), st.times, dx, dy, 4)
+    dxp, dyp = oracle.offsets(st.times[perm], st.vx, st.vy)
+    b = oracle.search_region(*oracle.psi_phi(st.sci[perm], st.var[perm], None, st.psf[perm]),
+                             st.times[perm], dxp, dyp, 4)
+    assert np.array_equal(a, b)
+
+
+def test_trajectory_from_images_matches_planes():
+    st = synth.small_stack(36, 4, 20, 18, K=5, nan_frac=0.03, mask_frac=0.03)
+    dx, dy = oracle.offsets(st.times, st.vx, st.vy)
+    psi, phi = oracle.psi_phi(st.sci, st.var, st.mask, st.psf)
+    for v, x0, y0 in [(0, 3, 4), (17, 10, 10), (50, 17, 0), (63, 0, 19)]:
+        P, F, n = oracle.sums_one_velocity(psi, phi, st.times, dx[v], dy[v])
+        a, b, c = oracle.trajectory_from_images(st.sci, st.var, st.mask, st.psf, st.times, dx[v], dy[v],
+                                                x0, y0)
+        assert a == pytest.approx(P[y0, x0], rel=1e-12, abs=1e-14)
+        assert b == pytest.approx(F[y0, x0], rel=1e-12, abs=1e-14)
+        assert c == n[y0, x0]
+
+
+def test_off_image_trajectory_is_invalid():
+    """Epochs off the image add nothing; a trajectory with no valid epoch (Phi = 0) is never kept."""
+    st = synth.small_stack(37, 3, 8, 8, K=3)
+    times = np.array([0.0, 1.0, 2.0])
+    vx = np.array([100.0, 1.0])
+    vy = np.array([0.0, 0.0])
+    dx, dy = oracle.offsets(times, vx, vy)
+    var = st.var.copy()
+    var[0] = -1.0   # epoch 0 fully masked -> phi_0 = 0 everywhere
+    psi, phi = oracle.psi_phi(st.sci, var, None, st.psf)
+    rec = oracle.search_region(psi, phi, times, dx, dy, 2)
+    # velocity 0 leaves the image after t = 0 and epoch 0 has phi = 0: never valid.  Velocity 1
+    # visits x0, x0 + 1, x0 + 2: nobs counts in-image epochs (masked or not), and at x0 = 7 only
+    # the masked epoch 0 is inside, so Phi = 0 and nothing is kept.
+    assert np.all(rec["vidx"][:, :7, 0] == 1)
+    assert np.all(rec["nobs"][:, :6, 0] == 3) and np.all(rec["nobs"][:, 6, 0] == 2)
+    assert np.all(rec["vidx"][:, 7, :] == -1) and np.all(rec["nu"][:, 7, :] == -np.inf)
+    assert np.all(rec["vidx"][..., 1] == -1) and np.all(rec["nu"][..., 1] == -np.inf)
