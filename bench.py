@@ -1,0 +1,357 @@
+"""Benchmark of the shift-and-stack likelihood search on GB300.
+
+One step is one pass of the whole hot path over the DECam-shaped stack
+(12 epochs of 4096 x 4096, 32 x 32 = 1024 velocities, k = 8):
+psi/phi images (kb_make_psi_phi) and the exhaustive search (kb_search), plus
+16-bit quantisation and FP64 rescoring when --storage bf16/f16 --rescore.
+Metric: trajectory-epoch evaluations per second (H * W * V * N per step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--storage f32|bf16|f16] [--rescore]
+                  [--impl ours|reference] [--size S]
+
+--impl reference times the FP64 CPU oracle on the host cores instead (bounded
+samples of start pixels of the same workload, whole path from the raw images).
+Multi-GPU runs (torchrun) are independent replicas, one stack per GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# search-kernel algorithmic bytes per trajectory-epoch evaluation (one psi, phi pair)
+BYTES_PER_EVAL = {"f32": 8, "bf16": 4, "f16": 4}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--rescore", action="store_true")
+    ap.add_argument("--size", type=int, default=4096, help="image side (4096 = the DECam workload)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(size):
+    import synth
+    st = synth.decam(H=size, W=size)
+    return st
+
+
+def workload_config(args, st, world):
+    N, H, W = st.sci.shape
+    name = "decam %dx%dx%d, %d velocities, k=%d" % (N, H, W, st.vx.size, st.k)
+    return {"workload": name, "epochs": N, "height": H, "width": W, "velocities": int(st.vx.size),
+            "topk": st.k, "psf": "17x17 Gaussian, FWHM 3.5-4.5 px", "storage": args.storage,
+            "rescore_fp64": bool(args.rescore), "evals_per_step": int(N * H * W * st.vx.size),
+            "l2": "inputs larger than L2 (%.2f GB of psi/phi planes)" % (N * H * W * 8 / 1e9),
+            "parallelism": "replicas%d" % world}
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 ".bench_clocks_%d.csv" % os.getpid())
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        try:
+            self.f.close()
+        except Exception:
+            pass
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[3:7]))
+                except ValueError:
+                    continue
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------- roofline helpers
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def recorded_traffic(kernel_tag):
+    """DRAM bytes per launch recorded by an ncu capture in profiles/, if the kernel
+    source has not changed since (matching sha256 prefix)."""
+    src = os.path.join(ROOT, "paper_1901_02492_gb300", "csrc", "kb_search.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))) if os.path.isdir(os.path.join(ROOT, "profiles")) else []:
+        if not fn.endswith(".md"):
+            continue
+        for line in open(os.path.join(ROOT, "profiles", fn)):
+            m = re.match(r"traffic\s+%s\s+bytes_per_launch=(\d+)\s+source_sha=([0-9a-f]+)" % re.escape(kernel_tag),
+                         line.strip())
+            if m and m.group(2) == sha:
+                return int(m.group(1))
+    return None
+
+
+# ----------------------------------------------------------------------------- reference arm (oracle)
+
+def oracle_sample(st, seconds, rng):
+    """Time the oracle's whole path (psi/phi from the raw images + search) on a bounded
+    sample of start pixels of the workload; returns (evals, seconds, pixels)."""
+    import oracle
+    N, H, W = st.sci.shape
+    dx, dy = oracle.offsets(st.times, st.vx, st.vy)
+    n = max(1, oracle.num_threads())
+    done, spent = 0, 0.0
+    while spent < min(0.5, seconds / 4):        # calibrate on at least 0.5 s of work
+        m = n * max(1, 2 ** min(done // n, 6))
+        px = rng.integers(0, W, m)
+        py = rng.integers(0, H, m)
+        t0 = time.perf_counter()
+        oracle.search_pixels_from_images(st.sci, st.var, None, st.psf, st.times, dx, dy, st.k, px, py)
+        spent += time.perf_counter() - t0
+        done += m
+    per_pix = spent / done
+    npix = max(n, int(seconds / max(per_pix, 1e-9)) // n * n)
+    px = rng.integers(0, W, npix)
+    py = rng.integers(0, H, npix)
+    t0 = time.perf_counter()
+    oracle.search_pixels_from_images(st.sci, st.var, None, st.psf, st.times, dx, dy, st.k, px, py)
+    dt = time.perf_counter() - t0
+    return npix * st.vx.size * N, dt, npix
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    st = workload(args.size)
+    cfg = workload_config(args, st, 1)
+    rng = np.random.default_rng(1234)
+    per_step = max(2.0, min(10.0, 150.0 / max(args.steps + args.warmup, 1)))
+    for _ in range(args.warmup):
+        oracle_sample(st, per_step / 4, rng)
+    evals = 0
+    secs = 0.0
+    pix = 0
+    for _ in range(args.steps):
+        e, s, p = oracle_sample(st, per_step, rng)
+        evals += e
+        secs += s
+        pix += p
+    value = evals / secs
+    line = {"impl": "reference", "metric": "trajectory-epoch evals/sec on 12x4096^2 stack",
+            "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d random start pixels x %d velocities x %d epochs of the workload, "
+                                       "psi/phi evaluated from the raw images" % (pix, st.vx.size, st.sci.shape[0])},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1901_02492_gb300 import binding as kb
+
+    st = workload(args.size)
+    N, H, W = st.sci.shape
+    V = st.vx.size
+    k = st.k
+    evals = N * H * W * V
+    flags = kb.KB_RESCORE_FP64 if args.rescore else 0
+    ctx = kb.Context(dev.index)
+    stack = kb.Stack(ctx, N, H, W, args.storage)
+    job = kb.Job(ctx, H, W, N, V, k, flags)
+    sci_h = torch.from_numpy(st.sci).pin_memory()
+    var_h = torch.from_numpy(st.var).pin_memory()
+    sci = sci_h.to(dev)
+    var = var_h.to(dev)
+    stream = torch.cuda.current_stream(dev)
+    launches_per_step = 2 + (1 if args.storage != "f32" else 0) + (1 if args.rescore else 0)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(timers=None):
+        if timers is not None:
+            timers[0].record(stream)
+        stack.make_psi_phi(sci, var, None, st.psf, stream=stream)
+        if timers is not None:
+            timers[1].record(stream)
+        job.search(stack, st.times, st.vx, st.vy, k, -math.inf, flags, stream=stream)
+        if timers is not None:
+            timers[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    timers = [[ev(), ev(), ev()] for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        t0, t1 = ev(), ev()
+        t0.record(stream)
+        for i in range(args.steps):
+            step(timers[i])
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1)
+    ms_psiphi = sum(t[0].elapsed_time(t[1]) for t in timers) / args.steps
+    ms_search = sum(t[1].elapsed_time(t[2]) for t in timers) / args.steps
+    clocks = clk.summary()
+
+    # end to end through the C ABI: pinned host inputs -> device -> psi/phi -> search -> host results
+    res_h = torch.empty(H * W * k * kb.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    res_np = res_h.numpy().view(kb.RESULT_DTYPE)
+    e2e_ms = []
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize(dev)
+        a = time.perf_counter()
+        sci.copy_(sci_h, non_blocking=True)
+        var.copy_(var_h, non_blocking=True)
+        step()
+        job.results(res_np, stream=stream)
+        torch.cuda.synchronize(dev)
+        if i > 0:
+            e2e_ms.append(1e3 * (time.perf_counter() - a))
+    e2e_ms = float(np.mean(e2e_ms))
+
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([ms, e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = t.tolist()
+    value = world * evals * args.steps / (ms * 1e-3)
+    peaks = measured_peaks()
+
+    # roofline of the dominant kernel (the search): algorithmic on-chip load bytes
+    # (one psi/phi pair per evaluation) against the SMs' L1/shared load bandwidth
+    # derived from unit counts and clocks: 152 SMs x 128 B/clk x max SM clock.
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    l1_peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e9   # GB/s
+    alg_bytes = evals * BYTES_PER_EVAL[args.storage]
+    achieved = alg_bytes / (ms_search * 1e-3) / 1e9
+    traffic = recorded_traffic("search_%s" % args.storage)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    psiphi_bytes = N * H * W * (8 + 8 + (4 + 8 if args.storage != "f32" else 0))
+    cfg = workload_config(args, st, world)
+    line = {"metric": "trajectory-epoch evals/sec on 12x4096^2 stack", "value": value, "unit": "evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+            "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "l1", "kernel": "search_kernel", "achieved": achieved, "peak": l1_peak,
+                         "unit": "GB/s", "frac": achieved / l1_peak, "traffic": traffic,
+                         "peak_source": "derived: SMs x 128 B/clk x max SM clock (no measured L1 peak)",
+                         "ms_per_launch": ms_search, "alg_bytes_per_launch": alg_bytes},
+            "roofline_psi_phi": {"bound": "hbm", "kernel": "psi_phi_kernel", "ms_per_launch": ms_psiphi,
+                                 "achieved": psiphi_bytes / (ms_psiphi * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                 "frac": psiphi_bytes / (ms_psiphi * 1e-3) / 1e9 / hbm,
+                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "clocks": clocks,
+            "e2e": {"value": world * evals / (e2e_ms * 1e-3), "unit": "evals/s",
+                    "h2d_bytes_per_step": int(sci_h.numel() * 4 + var_h.numel() * 4),
+                    "d2h_bytes_per_step": int(H * W * k * kb.RESULT_DTYPE.itemsize), "ms_per_step": e2e_ms},
+            "gpu_launches": launches_per_step * args.steps}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        e, s, p = oracle_sample(st, args.cpu_seconds, np.random.default_rng(7))
+        line["cpu_baseline"] = {"value": e / s, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": "%d random start pixels x %d velocities x %d epochs of the workload, "
+                                          "psi/phi evaluated from the raw images, %.1f s" % (p, V, N, s)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    job.free()
+    stack.free()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * kb.h -- C ABI of the GB300 (sm_103a) shift-and-stack likelihood search.
+ *
+ * The method is the one of Whidden et al., "Fast algorithms for slow moving
+ * asteroids" (arXiv:1901.02492):
+ *   stage (a)  per epoch t, the likelihood images of Sec. 2.1.5
+ *                psi_t(y) = sum_i n_t(x_i) T_t(x_i - y) / sigma_t,i^2
+ *                phi_t(y) = sum_i T_t(x_i - y)^2 / sigma_t,i^2
+ *              with masked pixels given zero inverse variance (Sec. 2.1.5);
+ *   stage (b)  for every start pixel y0 of the earliest image and every velocity
+ *              v of a grid (Sec. 2.2, Sec. 3.2), the coadd of Sec. 2.1.5
+ *                Psi = sum_t psi_t(y0 + v t),  Phi = sum_t phi_t(y0 + v t),
+ *              the scores alpha = Psi / Phi (maxLikeFlux) and nu = Psi / sqrt(Phi),
+ *              keeping the k best trajectories per start pixel.
+ *
+ * Conventions shared by every call:
+ *   - Images are row-major [N][H][W] (epoch, row y, column x); a trajectory
+ *     pixel is (x0 + dx, y0 + dy).
+ *   - "device pointer" means memory of the context's CUDA device (cudaMalloc,
+ *     torch CUDA tensors, ...); "host pointer" means ordinary CPU memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is stream-ordered: inputs must stay valid until the stream has
+ *     executed the call's work; outputs are ready when it has.
+ *   - Every call returns KB_OK (0) or a KB_E* status; no exception crosses the
+ *     ABI.  The text of the last error of a context is kb_last_error(ctx).
+ *   - A context, and the stacks and jobs made from it, are used from one host
+ *     thread at a time.
+ *
+ * Trajectory pixels are computed in fixed point, identically for every call
+ * (the paper rounds y0 + v t to a pixel without saying how):
+ *   v_q = llround(v * 2^16)                  (v in px/day)
+ *   t_q = llround((t - t_min) * 2^20)        (t in days, t_min = earliest epoch)
+ *   d   = floor((v_q * t_q + 2^35) / 2^36)   (64-bit integers; round half up)
+ * so |v| < 2^12 px/day and t - t_min < 2^6 days are required.
+ */
+#ifndef KB_H
+#define KB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define KB_OK 0
+#define KB_EINVAL 1   /* bad argument: NULL pointer, bad shape or size, K even, ... */
+#define KB_ENOMEM 2   /* device allocation failed or the context's HBM budget is exceeded */
+#define KB_ECUDA 3    /* a CUDA runtime call failed (message in kb_last_error) */
+#define KB_ETIMEOUT 4 /* a bounded device-side wait gave up */
+#define KB_ERANGE 5   /* output buffer too small; *n_written holds the required count */
+
+/* ---- storage of the psi/phi planes used by the search ------------------- */
+#define KB_F32 0   /* (psi, phi) as two float32 per pixel, 8 bytes */
+#define KB_BF16 1  /* (psi, phi) as two bfloat16 per pixel with per-epoch power-of-two scales, 4 bytes */
+#define KB_F16 2   /* (psi, phi) as two float16 per pixel with per-epoch power-of-two scales, 4 bytes */
+
+/* ---- search flags -------------------------------------------------------- */
+#define KB_RESCORE_FP64 1 /* re-rank the kept candidates with FP64 sums of the FP32 planes */
+
+/* ---- limits -------------------------------------------------------------- */
+#define KB_MAX_EPOCHS 128   /* N */
+#define KB_MAX_PSF 63       /* K (odd) */
+#define KB_MAX_TOPK 16      /* k */
+#define KB_MAX_VELOCITIES 65535
+#define KB_MAX_SIDE 32767   /* H and W */
+
+typedef struct kb_ctx kb_ctx;     /* one CUDA device, an HBM budget, the last error */
+typedef struct kb_stack kb_stack; /* device-resident psi/phi planes of one image stack */
+typedef struct kb_job kb_job;     /* device-resident results of one search */
+
+/* One kept trajectory (Sec. 2.2), as written by kb_results (48 bytes). */
+typedef struct kb_result {
+    int32_t x0, y0;   /* start pixel in the earliest epoch (column, row) */
+    int32_t vidx;     /* index into the caller's velocity arrays; -1 = empty slot */
+    int32_t nobs;     /* epochs whose trajectory pixel lies inside the image */
+    float vx, vy;     /* the velocity as quantised by the library, px/day (v_q / 2^16) */
+    float psi, phi;   /* coadded Psi and Phi (Sec. 2.1.5) */
+    double nu, alpha; /* nu = Psi / sqrt(Phi), alpha = Psi / Phi; empty slot: nu = -inf, alpha = 0 */
+} kb_result;
+
+/* ---- context ------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps what the
+ * context's stacks and jobs may hold on the device (0 = no cap); allocations
+ * beyond it fail with KB_ENOMEM.  *ctx is owned by the caller: kb_destroy. */
+int kb_init(kb_ctx **ctx, int device, size_t hbm_budget_bytes);
+
+/* Free the context.  Stacks and jobs made from it must be freed first. */
+void kb_destroy(kb_ctx *ctx);
+
+/* NUL-terminated text of the context's last error ("" if none); owned by ctx. */
+const char *kb_last_error(const kb_ctx *ctx);
+
+/* Bytes of device memory currently held by the context's stacks and jobs. */
+size_t kb_hbm_in_use(const kb_ctx *ctx);
+
+/* ---- stage (a): likelihood images --------------------------------------- */
+
+/* Allocate the device planes for an N x H x W stack (1 <= N <= KB_MAX_EPOCHS,
+ * 1 <= H, W <= KB_MAX_SIDE).  The FP32 (psi, phi) planes are always kept; with
+ * storage KB_BF16 or KB_F16 a 16-bit copy with per-epoch scales is kept as well
+ * and is what kb_search reads.  *out is owned by the caller: kb_stack_free. */
+int kb_stack_create(kb_ctx *ctx, int N, int H, int W, int storage, kb_stack **out);
+void kb_stack_free(kb_stack *s);
+
+/* Sec. 2.1.5: fill the stack with psi_t and phi_t of every epoch.
+ *   sci   device, float [N][H][W]: background-subtracted counts n(x)
+ *   var   device, float [N][H][W]: variance sigma^2
+ *   mask  device, uint8 [N][H][W] or NULL: non-zero = masked
+ *   psf   HOST, float [N][K][K]: PSF T_t of each epoch, row-major, T(dy, dx) at
+ *         [(dy + K/2) * K + (dx + K/2)]; K odd, 1 <= K <= KB_MAX_PSF.  Separable
+ *         (rank-1) kernels take a two-pass path, others a single-pass 2-D path.
+ *   bright_max  pixels with n > bright_max are masked (Sec. 5.2); pass +inf or
+ *         NaN to disable.
+ * A pixel is masked when its mask byte is non-zero, when n or sigma^2 is not
+ * finite, when sigma^2 <= 0, or when n > bright_max; it then contributes exactly
+ * zero.  PSF taps falling outside the image contribute zero.  The psf array is
+ * read before the call returns; the device inputs are read in stream order. */
+int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8_t *mask, const float *psf,
+                    int K, float bright_max, void *stream);
+
+/* Copy the stack's planes to dst (host or device), stream-ordered.
+ *   which = 0: FP32 planes, float [N][H][W][2] = (psi, phi), dst_bytes >= N*H*W*8
+ *   which = 1: 16-bit planes, uint16 [N][H][W][2] = (psi, phi) codes, dst_bytes >= N*H*W*4
+ *              (value = code * scale of that epoch, see kb_stack_scales)
+ * Host destinations make the call synchronous.  KB_EINVAL if the stack has no
+ * such planes or dst_bytes is too small. */
+int kb_stack_copy_planes(const kb_stack *s, int which, void *dst, size_t dst_bytes, void *stream);
+
+/* Per-epoch power-of-two scales of the 16-bit planes (host arrays of N floats);
+ * synchronises with the work that made them.  All 1.0 for KB_F32 stacks. */
+int kb_stack_scales(const kb_stack *s, float *psi_scale, float *phi_scale);
+
+/* ---- stage (b): trajectory search ---------------------------------------- */
+
+/* The trajectory offsets the search uses, in the fixed point defined above:
+ * dx, dy host int32 [V][N] for the caller's epoch order.  times host [N] days,
+ * vx, vy host [V] px/day.  Pure host function. */
+int kb_offsets(const double *times, int N, const double *vx, const double *vy, int V, int32_t *dx,
+               int32_t *dy);
+
+/* Allocate a search job for H x W start pixels, up to N epochs, up to V
+ * velocities and up to topk results per pixel (1 <= topk <= KB_MAX_TOPK).
+ * flags may include KB_RESCORE_FP64 (reserves the candidate buffers).
+ * *out is owned by the caller: kb_job_free. */
+int kb_job_create(kb_ctx *ctx, int H, int W, int N, int V, int topk, int flags, kb_job **out);
+void kb_job_free(kb_job *j);
+
+/* Sec. 2.2 exhaustive search of the stack s into job:
+ *   times   host double [N]: epoch times in days, in the stack's epoch order
+ *   vx, vy  host double [V]: velocity grid in px/day (the caller's index = vidx)
+ *   topk    results kept per start pixel (<= the job's topk)
+ *   nu_min  only trajectories with nu >= nu_min are kept (-inf keeps all valid)
+ *   flags   KB_RESCORE_FP64: search the stack's planes keeping extra
+ *           candidates, then recompute each candidate's sums in FP64 from the
+ *           FP32 planes, re-rank in FP64 and keep the top-k
+ * Every start pixel of the earliest epoch is searched.  Epochs whose trajectory
+ * pixel is outside the image contribute nothing; trajectories with Phi == 0 are
+ * not kept; ranking is by (nu descending, vidx ascending); empty slots have
+ * vidx = -1.  The host arrays are read before the call returns; the kernels run
+ * in stream order and may be re-run by calling kb_search again. */
+int kb_search(kb_job *job, const kb_stack *s, const double *times, const double *vx, const double *vy, int V,
+              int topk, float nu_min, int flags, void *stream);
+
+/* Write the job's results as kb_result records, [H][W][topk] in start-pixel
+ * row-major order, best first within a pixel.  out is a host or device pointer
+ * with room for `capacity` records; a host destination makes the call wait for
+ * the stream.  KB_ERANGE (with *n_written = H*W*topk) if capacity is too small. */
+int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KB_H */

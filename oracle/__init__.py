@@ -12,8 +12,9 @@ Functions and the paper passages they follow:
   sums_one_velocity  Sec. 2.1.5 coadd Psi = sum_t psi_t(y_t), Phi = sum_t phi_t(y_t)
   search_region / search_pixels
                      Sec. 2.2 exhaustive search, scores of Sec. 2.1.5, top-k per pixel
-  trajectory_from_images
-                     one trajectory straight from the raw images (sampled checks)
+  trajectory_from_images / search_pixels_from_images
+                     one trajectory / the search at listed pixels straight from the raw
+                     images (sampled checks of full-size runs)
 """
 from __future__ import annotations
 
@@ -69,6 +70,8 @@ def _load():
                                               i32, i32, i32, i32, P]
             lib.kbo_trajectory_from_images.argtypes = [P, P, P, P, P, i32, i32, i32, i32, f64,
                                                        P, P, i32, i32, P, P, P]
+            lib.kbo_search_pixels_from_images.argtypes = [P, P, P, P, P, i32, i32, i32, i32, f64, P, P, i32,
+                                                          i32, f64, P, P, i64, P]
             lib.kbo_num_threads.restype = i32
             lib.kbo_set_num_threads.argtypes = [i32]
             _lib = lib
@@ -225,3 +228,25 @@ def trajectory_from_images(sci, var, mask, psf, times, dx_v, dy_v, x0, y0, brigh
                                    _bright(bright_max), _ptr(dx_v), _ptr(dy_v), int(x0), int(y0),
                                    ctypes.byref(P), ctypes.byref(F), ctypes.byref(n))
     return P.value, F.value, n.value
+
+
+def search_pixels_from_images(sci, var, mask, psf, times, dx, dy, k, px, py, nu_min=-np.inf, bright_max=None):
+    """Top-k records [npix][k] at start pixels (px[i], py[i]) computed from the raw images."""
+    lib = _load()
+    sci = _c(sci, np.float32)
+    var = _c(var, np.float32)
+    mask = None if mask is None else _c(mask, np.uint8)
+    psf = _c(psf, np.float32)
+    times = _c(times, np.float64)
+    dx = _c(dx, np.int32)
+    dy = _c(dy, np.int32)
+    px = _c(px, np.int32)
+    py = _c(py, np.int32)
+    N, H, W = sci.shape
+    K = psf.shape[-1]
+    V = dx.shape[0]
+    out = np.empty((px.size, k), REC_DTYPE)
+    lib.kbo_search_pixels_from_images(_ptr(sci), _ptr(var), _ptr(mask), _ptr(psf), _ptr(times), N, H, W, K,
+                                      _bright(bright_max), _ptr(dx), _ptr(dy), V, int(k), float(nu_min),
+                                      _ptr(px), _ptr(py), px.size, _ptr(out))
+    return out

@@ -251,13 +251,7 @@ static int ranks_before(double a_nu, int a_v, const kbo_rec *b) {
     return a_v < b->vidx;
 }
 
-/*
- * Sec. 2.2 exhaustive search at one start pixel: every velocity, scores of Sec.
- * 2.1.5, keep the k best valid trajectories (Phi > 0 and nu >= nu_min).
- */
-static void search_pixel(const double *psi, const double *phi, int N, int H, int W, const int32_t *dx,
-                         const int32_t *dy, int V, const int *order, int k, double nu_min, int x0, int y0,
-                         kbo_rec *out) {
+static void empty_list(int x0, int y0, int k, kbo_rec *out) {
     for (int i = 0; i < k; ++i) {
         out[i].x0 = x0;
         out[i].y0 = y0;
@@ -268,30 +262,45 @@ static void search_pixel(const double *psi, const double *phi, int N, int H, int
         out[i].nu = -INFINITY;
         out[i].alpha = 0.0;
     }
+}
+
+/* Scores of Sec. 2.1.5 for one trajectory and insertion into the sorted list when
+ * it is valid (Phi > 0, nu >= nu_min) and ranks among the k best. */
+static void offer(double P, double F, int nobs, int v, int k, double nu_min, kbo_rec *out) {
+    if (!(F > 0.0)) return;
+    double nu = P / sqrt(F);
+    double alpha = P / F;
+    if (!(nu >= nu_min)) return;
+    int pos = k;
+    for (int i = 0; i < k; ++i)
+        if (ranks_before(nu, v, &out[i])) {
+            pos = i;
+            break;
+        }
+    if (pos == k) return;
+    for (int i = k - 1; i > pos; --i) out[i] = out[i - 1];
+    out[pos].vidx = v;
+    out[pos].nobs = nobs;
+    out[pos].psi = P;
+    out[pos].phi = F;
+    out[pos].nu = nu;
+    out[pos].alpha = alpha;
+}
+
+/*
+ * Sec. 2.2 exhaustive search at one start pixel: every velocity, scores of Sec.
+ * 2.1.5, keep the k best valid trajectories (Phi > 0 and nu >= nu_min).
+ */
+static void search_pixel(const double *psi, const double *phi, int N, int H, int W, const int32_t *dx,
+                         const int32_t *dy, int V, const int *order, int k, double nu_min, int x0, int y0,
+                         kbo_rec *out) {
+    empty_list(x0, y0, k, out);
     for (int v = 0; v < V; ++v) {
         double P, F;
         int nobs;
         trajectory_sums(psi, phi, N, H, W, dx + (size_t)v * N, dy + (size_t)v * N, order, x0, y0, &P, &F,
                         &nobs);
-        if (!(F > 0.0)) continue;
-        double nu = P / sqrt(F);
-        double alpha = P / F;
-        if (!(nu >= nu_min)) continue;
-        /* insertion into the sorted list */
-        int pos = k;
-        for (int i = 0; i < k; ++i)
-            if (ranks_before(nu, v, &out[i])) {
-                pos = i;
-                break;
-            }
-        if (pos == k) continue;
-        for (int i = k - 1; i > pos; --i) out[i] = out[i - 1];
-        out[pos].vidx = v;
-        out[pos].nobs = nobs;
-        out[pos].psi = P;
-        out[pos].phi = F;
-        out[pos].nu = nu;
-        out[pos].alpha = alpha;
+        offer(P, F, nobs, v, k, nu_min, out);
     }
 }
 
@@ -349,4 +358,27 @@ void kbo_trajectory_from_images(const float *sci, const float *var, const uint8_
     *P = sp;
     *F = sf;
     *nobs = n;
+}
+
+/*
+ * The Sec. 2.2 search at listed start pixels straight from the raw images: every
+ * trajectory's psi/phi values come from the point definition, so no planes are
+ * held.  Used to check sampled pixels of full-size searches.
+ */
+void kbo_search_pixels_from_images(const float *sci, const float *var, const uint8_t *mask, const float *psf,
+                                   const double *times, int N, int H, int W, int K, double bright_max,
+                                   const int32_t *dx, const int32_t *dy, int V, int k, double nu_min,
+                                   const int32_t *px, const int32_t *py, int64_t npix, kbo_rec *out) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < npix; ++i) {
+        kbo_rec *o = out + (size_t)i * k;
+        empty_list(px[i], py[i], k, o);
+        for (int v = 0; v < V; ++v) {
+            double P, F;
+            int32_t nobs;
+            kbo_trajectory_from_images(sci, var, mask, psf, times, N, H, W, K, bright_max, dx + (size_t)v * N,
+                                       dy + (size_t)v * N, px[i], py[i], &P, &F, &nobs);
+            offer(P, F, nobs, v, k, nu_min, o);
+        }
+    }
 }

@@ -1,0 +1,223 @@
+"""Thin ctypes binding of libkb (include/kb.h): argument marshalling only.
+
+Every step of the search runs in the library's CUDA kernels; this module only
+turns torch tensors / numpy arrays into pointers, sizes and a cudaStream_t and
+raises KBError on a non-zero status.  There is no CPU fallback: importing it
+fails when libkb.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkb.so")
+
+KB_OK, KB_EINVAL, KB_ENOMEM, KB_ECUDA, KB_ETIMEOUT, KB_ERANGE = 0, 1, 2, 3, 4, 5
+KB_F32, KB_BF16, KB_F16 = 0, 1, 2
+KB_RESCORE_FP64 = 1
+STORAGE = {"f32": KB_F32, "bf16": KB_BF16, "f16": KB_F16}
+
+RESULT_DTYPE = np.dtype([("x0", "<i4"), ("y0", "<i4"), ("vidx", "<i4"), ("nobs", "<i4"),
+                         ("vx", "<f4"), ("vy", "<f4"), ("psi", "<f4"), ("phi", "<f4"),
+                         ("nu", "<f8"), ("alpha", "<f8")])
+assert RESULT_DTYPE.itemsize == 48
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libkb.so is not built (run paper_1901_02492_gb300.build.build() or "
+                      "__graft_entry__.build()); there is no fallback path")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_P = ctypes.c_void_p
+_i32, _f32, _sz = ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_kb_init = _sig("kb_init", _i32, [ctypes.POINTER(_P), _i32, _sz])
+_kb_destroy = _sig("kb_destroy", None, [_P])
+_kb_last_error = _sig("kb_last_error", ctypes.c_char_p, [_P])
+_kb_hbm_in_use = _sig("kb_hbm_in_use", _sz, [_P])
+_kb_stack_create = _sig("kb_stack_create", _i32, [_P, _i32, _i32, _i32, _i32, ctypes.POINTER(_P)])
+_kb_stack_free = _sig("kb_stack_free", None, [_P])
+_kb_make_psi_phi = _sig("kb_make_psi_phi", _i32, [_P, _P, _P, _P, _P, _i32, _f32, _P])
+_kb_stack_copy_planes = _sig("kb_stack_copy_planes", _i32, [_P, _i32, _P, _sz, _P])
+_kb_stack_scales = _sig("kb_stack_scales", _i32, [_P, _P, _P])
+_kb_offsets = _sig("kb_offsets", _i32, [_P, _i32, _P, _P, _i32, _P, _P])
+_kb_job_create = _sig("kb_job_create", _i32, [_P, _i32, _i32, _i32, _i32, _i32, _i32, ctypes.POINTER(_P)])
+_kb_job_free = _sig("kb_job_free", None, [_P])
+_kb_search = _sig("kb_search", _i32, [_P, _P, _P, _P, _P, _i32, _i32, _f32, _i32, _P])
+_kb_results = _sig("kb_results", _i32, [_P, _P, _sz, ctypes.POINTER(_sz), _P])
+
+EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_stack_create", "kb_stack_free",
+            "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
+            "kb_job_free", "kb_search", "kb_results"]
+
+
+class KBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("kb status %d: %s" % (code, msg))
+        self.code = code
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Context:
+    """kb_ctx: one CUDA device and an HBM budget (0 = none)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        h = _P()
+        rc = _kb_init(ctypes.byref(h), int(device), int(hbm_budget))
+        if rc != KB_OK:
+            raise KBError(rc, "kb_init(device=%d) failed" % device)
+        self.h = h
+        self.device = device
+
+    def check(self, rc):
+        if rc != KB_OK:
+            raise KBError(rc, _kb_last_error(self.h).decode())
+
+    @property
+    def last_error(self) -> str:
+        return _kb_last_error(self.h).decode()
+
+    @property
+    def hbm_in_use(self) -> int:
+        return int(_kb_hbm_in_use(self.h))
+
+    def close(self):
+        if self.h:
+            _kb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Stack:
+    """kb_stack: device-resident psi/phi planes of an N x H x W stack."""
+
+    def __init__(self, ctx: Context, N: int, H: int, W: int, storage="f32"):
+        self.ctx = ctx
+        self.N, self.H, self.W = N, H, W
+        self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        h = _P()
+        ctx.check(_kb_stack_create(ctx.h, N, H, W, self.storage, ctypes.byref(h)))
+        self.h = h
+
+    def make_psi_phi(self, sci, var, mask, psf, bright_max=math.inf, stream=None):
+        """sci/var: CUDA float32 [N][H][W]; mask: CUDA uint8 or None; psf: host float32 [N][K][K]."""
+        psf = np.ascontiguousarray(psf, dtype=np.float32)
+        K = psf.shape[-1]
+        self.ctx.check(_kb_make_psi_phi(self.h, _ptr(sci), _ptr(var), _ptr(mask), psf.ctypes.data, K,
+                                        float(bright_max), _stream(stream)))
+
+    def copy_planes(self, which: int, dst, stream=None):
+        nbytes = dst.numel() * dst.element_size() if hasattr(dst, "numel") else dst.nbytes
+        self.ctx.check(_kb_stack_copy_planes(self.h, which, _ptr(dst), nbytes, _stream(stream)))
+
+    def scales(self):
+        sp = np.empty(self.N, np.float32)
+        sf = np.empty(self.N, np.float32)
+        self.ctx.check(_kb_stack_scales(self.h, sp.ctypes.data, sf.ctypes.data))
+        return sp, sf
+
+    def free(self):
+        if self.h:
+            _kb_stack_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def offsets(times, vx, vy):
+    """The library's fixed-point trajectory offsets: dx, dy int32 [V][N]."""
+    times, vx, vy = _f64(times), _f64(vx), _f64(vy)
+    N, V = times.size, vx.size
+    dx = np.empty((V, N), np.int32)
+    dy = np.empty((V, N), np.int32)
+    rc = _kb_offsets(times.ctypes.data, N, vx.ctypes.data, vy.ctypes.data, V, dx.ctypes.data, dy.ctypes.data)
+    if rc != KB_OK:
+        raise KBError(rc, "kb_offsets rejected the times or velocities")
+    return dx, dy
+
+
+class Job:
+    """kb_job: device results of searches over H x W start pixels."""
+
+    def __init__(self, ctx: Context, H: int, W: int, N: int, V: int, topk: int, flags: int = 0):
+        self.ctx = ctx
+        self.H, self.W, self.topk = H, W, topk
+        h = _P()
+        ctx.check(_kb_job_create(ctx.h, H, W, N, V, topk, flags, ctypes.byref(h)))
+        self.h = h
+        self.k = None
+
+    def search(self, stack: Stack, times, vx, vy, topk=None, nu_min=-math.inf, flags=0, stream=None):
+        times, vx, vy = _f64(times), _f64(vx), _f64(vy)
+        topk = self.topk if topk is None else topk
+        self.ctx.check(_kb_search(self.h, stack.h, times.ctypes.data, vx.ctypes.data, vy.ctypes.data, vx.size,
+                                  int(topk), float(nu_min), int(flags), _stream(stream)))
+        self.k = topk
+
+    def results(self, out=None, stream=None):
+        """Records [H][W][k] of RESULT_DTYPE.  out: None (new numpy array), a numpy array of
+        RESULT_DTYPE, or a CUDA uint8 tensor of >= H*W*k*48 bytes (device output)."""
+        n = self.H * self.W * self.k
+        if out is None:
+            out = np.empty(n, RESULT_DTYPE)
+        if hasattr(out, "numel"):
+            cap = out.numel() * out.element_size() // RESULT_DTYPE.itemsize
+        else:
+            cap = out.nbytes // RESULT_DTYPE.itemsize
+        written = _sz()
+        self.ctx.check(_kb_results(self.h, _ptr(out), cap, ctypes.byref(written), _stream(stream)))
+        if isinstance(out, np.ndarray):
+            return out.reshape(self.H, self.W, self.k)
+        return out
+
+    def free(self):
+        if self.h:
+            _kb_job_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,603 @@
+// Host side of the C ABI declared in include/kb.h: argument checks, device
+// memory and HBM-budget accounting, PSF analysis, the fixed-point trajectory
+// offset table, and the launches of the stage (a) / stage (b) kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+
+#include <cmath>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "kb_internal.h"
+
+namespace {
+
+// Sets the context's device for the duration of a call, restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(kb_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        char buf[1024];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(kb_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, KB_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// Device allocation under the context's HBM budget.
+int dev_alloc(kb_ctx *ctx, size_t bytes, void **p, size_t *acct) {
+    *p = nullptr;
+    if (bytes == 0) return KB_OK;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+            return fail(ctx, KB_ENOMEM, "HBM budget exceeded: %zu in use + %zu requested > %zu", ctx->in_use, bytes,
+                        ctx->budget);
+        ctx->in_use += bytes;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->in_use -= bytes;
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, KB_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    *acct += bytes;
+    return KB_OK;
+}
+
+void dev_release(kb_ctx *ctx, size_t bytes) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->in_use -= std::min(ctx->in_use, bytes);
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ---- fixed-point trajectory offsets (see include/kb.h) ----------------------
+constexpr int64_t kVelOne = 1LL << 16;    // v_q units per px/day
+constexpr int64_t kTimeOne = 1LL << 20;   // t_q units per day
+constexpr int64_t kVelMax = 1LL << 28;    // |v| < 2^12 px/day
+constexpr int64_t kTimeMax = 1LL << 26;   // t - t_min < 2^6 days
+
+// floor((vq * tq + 2^35) / 2^36): round half up of v t, exact in 64-bit integers
+inline int64_t offset_q(int64_t vq, int64_t tq) {
+    int64_t num = vq * tq + (1LL << 35);
+    int64_t q = num / (1LL << 36);           // truncates toward zero
+    if ((num % (1LL << 36)) < 0) q -= 1;     // floor for negative remainders
+    return q;
+}
+
+struct Plan {
+    std::vector<int> epoch_of;   // time-order position -> epoch
+    std::vector<int64_t> tq;     // per time-order position
+    int n0 = 0;                  // leading positions with tq == 0
+};
+
+int plan_times(kb_ctx *ctx, const double *times, int N, Plan &pl) {
+    for (int e = 0; e < N; ++e)
+        if (!std::isfinite(times[e])) return fail(ctx, KB_EINVAL, "times[%d] is not finite", e);
+    double tmin = *std::min_element(times, times + N);
+    pl.epoch_of.resize(N);
+    std::iota(pl.epoch_of.begin(), pl.epoch_of.end(), 0);
+    std::stable_sort(pl.epoch_of.begin(), pl.epoch_of.end(), [&](int a, int b) { return times[a] < times[b]; });
+    pl.tq.resize(N);
+    pl.n0 = 0;
+    for (int j = 0; j < N; ++j) {
+        double dt = times[pl.epoch_of[j]] - tmin;
+        if (!(dt * (double)kTimeOne < (double)kTimeMax))
+            return fail(ctx, KB_EINVAL, "epoch span %.6g days exceeds the supported 64 days", dt);
+        pl.tq[j] = llround(dt * (double)kTimeOne);
+        if (pl.tq[j] == 0 && pl.n0 == j) pl.n0 = j + 1;
+    }
+    return KB_OK;
+}
+
+int quant_velocity(kb_ctx *ctx, double v, int64_t *q) {
+    if (!std::isfinite(v) || !(fabs(v) * (double)kVelOne < (double)kVelMax))
+        return fail(ctx, KB_EINVAL, "velocity %.6g px/day outside the supported |v| < 4096", v);
+    *q = llround(v * (double)kVelOne);
+    return KB_OK;
+}
+
+// ---- PSF analysis ------------------------------------------------------------
+// A K x K kernel is separable when T(i, j) = a(i) b(j); the factors are read off
+// the row and column through the largest tap and checked against every tap.
+bool factor_psf(const float *T, int K, std::vector<double> &a, std::vector<double> &b) {
+    int bi = 0, bj = 0;
+    double best = 0.0;
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j)
+            if (fabs((double)T[i * K + j]) > best) {
+                best = fabs((double)T[i * K + j]);
+                bi = i;
+                bj = j;
+            }
+    a.assign(K, 0.0);
+    b.assign(K, 0.0);
+    if (best == 0.0) return true;   // all-zero kernel: any factors of zero
+    double piv = (double)T[bi * K + bj];
+    for (int i = 0; i < K; ++i) a[i] = (double)T[i * K + bj];
+    for (int j = 0; j < K; ++j) b[j] = (double)T[bi * K + j] / piv;
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j)
+            if (fabs(a[i] * b[j] - (double)T[i * K + j]) > 1e-6 * best) return false;
+    return true;
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+int kb_init(kb_ctx **out, int device, size_t hbm_budget_bytes) {
+    if (!out) return KB_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return KB_EINVAL;
+    }
+    kb_ctx *ctx = new kb_ctx();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    DeviceGuard g(device);
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return KB_ECUDA;
+    }
+    ctx->sm_count = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    *out = ctx;
+    return KB_OK;
+}
+
+void kb_destroy(kb_ctx *ctx) { delete ctx; }
+
+const char *kb_last_error(const kb_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t kb_hbm_in_use(const kb_ctx *ctx) { return ctx ? ctx->in_use : 0; }
+
+// ---- stacks ------------------------------------------------------------------
+
+int kb_stack_create(kb_ctx *ctx, int N, int H, int W, int storage, kb_stack **out) {
+    if (!ctx || !out) return KB_EINVAL;
+    *out = nullptr;
+    if (N < 1 || N > KB_MAX_EPOCHS || H < 1 || W < 1 || H > KB_MAX_SIDE || W > KB_MAX_SIDE)
+        return fail(ctx, KB_EINVAL, "stack shape N=%d H=%d W=%d outside 1..%d x 1..%d x 1..%d", N, H, W,
+                    KB_MAX_EPOCHS, KB_MAX_SIDE, KB_MAX_SIDE);
+    if (storage != KB_F32 && storage != KB_BF16 && storage != KB_F16)
+        return fail(ctx, KB_EINVAL, "unknown storage %d", storage);
+    DeviceGuard g(ctx->device);
+    kb_stack *s = new kb_stack();
+    s->ctx = ctx;
+    s->N = N;
+    s->H = H;
+    s->W = W;
+    s->pitch = (W + 3) & ~3;
+    s->storage = storage;
+    size_t plane = (size_t)H * s->pitch;
+    int rc = dev_alloc(ctx, (size_t)N * plane * sizeof(float2), (void **)&s->f32, &s->bytes);
+    if (rc == KB_OK && storage != KB_F32)
+        rc = dev_alloc(ctx, (size_t)N * plane * sizeof(kb::pair16), (void **)&s->q16, &s->bytes);
+    if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)N * sizeof(float2), (void **)&s->scales, &s->bytes);
+    if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)2 * N * sizeof(unsigned), (void **)&s->maxbits, &s->bytes);
+    cudaError_t e = cudaSuccess;
+    if (rc == KB_OK) e = cudaMemset(s->f32, 0, (size_t)N * plane * sizeof(float2));
+    if (rc == KB_OK && e == cudaSuccess && s->q16) e = cudaMemset(s->q16, 0, (size_t)N * plane * sizeof(kb::pair16));
+    if (rc == KB_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&s->taps_done, cudaEventDisableTiming);
+    if (rc == KB_OK && e != cudaSuccess) rc = cuda_fail(ctx, e, "kb_stack_create");
+    if (rc != KB_OK) {
+        kb_stack_free(s);
+        return rc;
+    }
+    *out = s;
+    return KB_OK;
+}
+
+void kb_stack_free(kb_stack *s) {
+    if (!s) return;
+    DeviceGuard g(s->ctx->device);
+    if (s->taps_done) {
+        cudaEventSynchronize(s->taps_done);
+        cudaEventDestroy(s->taps_done);
+    }
+    cudaFree(s->f32);
+    cudaFree(s->q16);
+    cudaFree(s->scales);
+    cudaFree(s->maxbits);
+    cudaFree(s->taps);
+    cudaFreeHost(s->taps_host);
+    dev_release(s->ctx, s->bytes);
+    delete s;
+}
+
+int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8_t *mask, const float *psf, int K,
+                    float bright_max, void *stream) {
+    if (!s) return KB_EINVAL;
+    kb_ctx *ctx = s->ctx;
+    if (!sci || !var || !psf) return fail(ctx, KB_EINVAL, "kb_make_psi_phi: sci, var and psf are required");
+    if (K < 1 || K > KB_MAX_PSF || (K % 2) == 0)
+        return fail(ctx, KB_EINVAL, "PSF size K=%d must be odd and in 1..%d", K, KB_MAX_PSF);
+    DeviceGuard g(ctx->device);
+    if (!is_device_ptr(sci) || !is_device_ptr(var) || (mask && !is_device_ptr(mask)))
+        return fail(ctx, KB_EINVAL, "kb_make_psi_phi: sci, var and mask must be device pointers");
+    const int N = s->N;
+    for (size_t i = 0; i < (size_t)N * K * K; ++i)
+        if (!std::isfinite(psf[i])) return fail(ctx, KB_EINVAL, "psf[%zu] is not finite", i);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // analyse the PSFs: separable for every epoch -> two-pass kernel
+    bool sep = true;
+    std::vector<std::vector<double>> fa(N), fb(N);
+    for (int e = 0; e < N && sep; ++e) sep = factor_psf(psf + (size_t)e * K * K, K, fa[e], fb[e]);
+    size_t nt = kb::taps_floats(N, K, sep);
+    if (nt > s->taps_floats) {
+        if (s->taps_done) cudaEventSynchronize(s->taps_done);
+        cudaFree(s->taps);
+        cudaFreeHost(s->taps_host);
+        dev_release(ctx, s->taps_floats * sizeof(float));
+        s->bytes -= std::min(s->bytes, s->taps_floats * sizeof(float));
+        s->taps = nullptr;
+        s->taps_host = nullptr;
+        s->taps_floats = 0;
+        int rc = dev_alloc(ctx, nt * sizeof(float), (void **)&s->taps, &s->bytes);
+        if (rc != KB_OK) return rc;
+        cudaError_t e = cudaMallocHost((void **)&s->taps_host, nt * sizeof(float));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMallocHost(taps)");
+        s->taps_floats = nt;
+    } else {
+        cudaEventSynchronize(s->taps_done);   // previous upload finished reading the staging
+    }
+    float *th = s->taps_host;
+    for (int e = 0; e < N; ++e) {
+        const float *T = psf + (size_t)e * K * K;
+        if (sep) {
+            float *o = th + (size_t)e * 4 * K;
+            for (int i = 0; i < K; ++i) {
+                o[2 * i] = (float)fa[e][i];
+                o[2 * i + 1] = (float)(fa[e][i] * fa[e][i]);
+                o[2 * K + 2 * i] = (float)fb[e][i];
+                o[2 * K + 2 * i + 1] = (float)(fb[e][i] * fb[e][i]);
+            }
+        } else {
+            float *o = th + (size_t)e * 2 * K * K;
+            for (int i = 0; i < K * K; ++i) {
+                o[2 * i] = T[i];
+                o[2 * i + 1] = (float)((double)T[i] * (double)T[i]);
+            }
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(s->taps, th, nt * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->taps_done, st);
+    bool q = s->q16 != nullptr;
+    if (e == cudaSuccess && q) e = cudaMemsetAsync(s->maxbits, 0, 2 * N * sizeof(unsigned), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_make_psi_phi upload");
+
+    kb::PsiPhiArgs a;
+    a.sci = sci;
+    a.var = var;
+    a.mask = mask;
+    a.bright_max = std::isnan(bright_max) ? INFINITY : bright_max;
+    a.N = N;
+    a.H = s->H;
+    a.W = s->W;
+    a.pitch = s->pitch;
+    a.K = K;
+    a.separable = sep;
+    a.taps = s->taps;
+    a.out = s->f32;
+    a.maxbits = q ? s->maxbits : nullptr;
+    e = kb::launch_psi_phi(a, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "psi/phi kernel");
+    if (q) {
+        e = kb::launch_quantize(s->f32, s->q16, s->scales, s->maxbits, N, s->H, s->pitch, s->storage, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "quantize kernel");
+    }
+    s->filled = true;
+    return KB_OK;
+}
+
+int kb_stack_copy_planes(const kb_stack *s, int which, void *dst, size_t dst_bytes, void *stream) {
+    if (!s) return KB_EINVAL;
+    kb_ctx *ctx = s->ctx;
+    if (!dst) return fail(ctx, KB_EINVAL, "kb_stack_copy_planes: dst is NULL");
+    const void *src = which == 0 ? (const void *)s->f32 : (const void *)s->q16;
+    size_t elem = which == 0 ? sizeof(float2) : sizeof(kb::pair16);
+    if ((which != 0 && which != 1) || !src) return fail(ctx, KB_EINVAL, "stack has no planes of kind %d", which);
+    size_t need = (size_t)s->N * s->H * s->W * elem;
+    if (dst_bytes < need) return fail(ctx, KB_EINVAL, "dst_bytes %zu < %zu", dst_bytes, need);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    bool dev = is_device_ptr(dst);
+    cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)s->W * elem, src, (size_t)s->pitch * elem, (size_t)s->W * elem,
+                                      (size_t)s->N * s->H, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_stack_copy_planes");
+    return KB_OK;
+}
+
+int kb_stack_scales(const kb_stack *s, float *psi_scale, float *phi_scale) {
+    if (!s || !psi_scale || !phi_scale) return KB_EINVAL;
+    DeviceGuard g(s->ctx->device);
+    if (!s->q16) {
+        for (int e = 0; e < s->N; ++e) psi_scale[e] = phi_scale[e] = 1.0f;
+        return KB_OK;
+    }
+    std::vector<float2> h(s->N);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), s->scales, s->N * sizeof(float2), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(s->ctx, e, "kb_stack_scales");
+    for (int i = 0; i < s->N; ++i) {
+        psi_scale[i] = h[i].x;
+        phi_scale[i] = h[i].y;
+    }
+    return KB_OK;
+}
+
+// ---- offsets -----------------------------------------------------------------
+
+int kb_offsets(const double *times, int N, const double *vx, const double *vy, int V, int32_t *dx, int32_t *dy) {
+    if (!times || !vx || !vy || !dx || !dy || N < 1 || V < 1) return KB_EINVAL;
+    Plan pl;
+    int rc = plan_times(nullptr, times, N, pl);
+    if (rc != KB_OK) return rc;
+    std::vector<int64_t> tq(N);
+    for (int j = 0; j < N; ++j) tq[pl.epoch_of[j]] = pl.tq[j];
+    for (int v = 0; v < V; ++v) {
+        int64_t qx, qy;
+        if ((rc = quant_velocity(nullptr, vx[v], &qx)) != KB_OK) return rc;
+        if ((rc = quant_velocity(nullptr, vy[v], &qy)) != KB_OK) return rc;
+        for (int e = 0; e < N; ++e) {
+            dx[(size_t)v * N + e] = (int32_t)offset_q(qx, tq[e]);
+            dy[(size_t)v * N + e] = (int32_t)offset_q(qy, tq[e]);
+        }
+    }
+    return KB_OK;
+}
+
+// ---- jobs --------------------------------------------------------------------
+
+static int job_kkeep(int topk, int flags) { return (flags & KB_RESCORE_FP64) ? std::min(2 * topk, 32) : topk; }
+
+int kb_job_create(kb_ctx *ctx, int H, int W, int N, int V, int topk, int flags, kb_job **out) {
+    if (!ctx || !out) return KB_EINVAL;
+    *out = nullptr;
+    if (H < 1 || W < 1 || H > KB_MAX_SIDE || W > KB_MAX_SIDE || N < 1 || N > KB_MAX_EPOCHS || V < 1 ||
+        V > KB_MAX_VELOCITIES || topk < 1 || topk > KB_MAX_TOPK)
+        return fail(ctx, KB_EINVAL, "job shape H=%d W=%d N=%d V=%d topk=%d out of range", H, W, N, V, topk);
+    if (flags & ~KB_RESCORE_FP64) return fail(ctx, KB_EINVAL, "unknown flags 0x%x", flags);
+    DeviceGuard g(ctx->device);
+    kb_job *j = new kb_job();
+    j->ctx = ctx;
+    j->H = H;
+    j->W = W;
+    j->Ncap = N;
+    j->Vcap = V;
+    j->kcap = topk;
+    j->flags = flags;
+    j->kkeep_cap = job_kkeep(topk, flags);
+    size_t npix = (size_t)H * W;
+    int rc = dev_alloc(ctx, (size_t)V * N * sizeof(int2), (void **)&j->offs, &j->bytes);
+    if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)V * sizeof(int), (void **)&j->vorder, &j->bytes);
+    if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)N * sizeof(int), (void **)&j->epoch_of, &j->bytes);
+    if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)V * sizeof(float2), (void **)&j->vq, &j->bytes);
+    if (rc == KB_OK) rc = dev_alloc(ctx, npix * j->kkeep_cap * sizeof(kb::Rec), (void **)&j->recs, &j->bytes);
+    if (rc == KB_OK && (flags & KB_RESCORE_FP64))
+        rc = dev_alloc(ctx, npix * topk * sizeof(kb::Rec64), (void **)&j->recs64, &j->bytes);
+    if (rc == KB_OK) {
+        j->stage_bytes = (size_t)V * N * sizeof(int2) + (size_t)V * sizeof(int) + (size_t)N * sizeof(int) +
+                         (size_t)V * sizeof(float2);
+        cudaError_t e = cudaMallocHost(&j->stage, j->stage_bytes);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->stage_done, cudaEventDisableTiming);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "kb_job_create");
+    }
+    if (rc != KB_OK) {
+        kb_job_free(j);
+        return rc;
+    }
+    *out = j;
+    return KB_OK;
+}
+
+void kb_job_free(kb_job *j) {
+    if (!j) return;
+    DeviceGuard g(j->ctx->device);
+    if (j->stage_done) {
+        cudaEventSynchronize(j->stage_done);
+        cudaEventDestroy(j->stage_done);
+    }
+    cudaFree(j->offs);
+    cudaFree(j->vorder);
+    cudaFree(j->epoch_of);
+    cudaFree(j->vq);
+    cudaFree(j->recs);
+    cudaFree(j->recs64);
+    cudaFree(j->expand);
+    cudaFreeHost(j->stage);
+    dev_release(j->ctx, j->bytes);
+    delete j;
+}
+
+int kb_search(kb_job *job, const kb_stack *s, const double *times, const double *vx, const double *vy, int V,
+              int topk, float nu_min, int flags, void *stream) {
+    if (!job) return KB_EINVAL;
+    kb_ctx *ctx = job->ctx;
+    if (!s || !times || !vx || !vy) return fail(ctx, KB_EINVAL, "kb_search: NULL argument");
+    if (!s->filled) return fail(ctx, KB_EINVAL, "kb_search: the stack has no psi/phi yet (kb_make_psi_phi)");
+    if (s->H != job->H || s->W != job->W || s->N > job->Ncap || V < 1 || V > job->Vcap || topk < 1 ||
+        topk > job->kcap)
+        return fail(ctx, KB_EINVAL, "kb_search: stack %dx%dx%d, V=%d, topk=%d do not fit the job (%dx%d, N<=%d, V<=%d, "
+                    "topk<=%d)", s->N, s->H, s->W, V, topk, job->H, job->W, job->Ncap, job->Vcap, job->kcap);
+    if ((flags & KB_RESCORE_FP64) && !(job->flags & KB_RESCORE_FP64))
+        return fail(ctx, KB_EINVAL, "kb_search: rescoring requested but the job was created without it");
+    if (flags & ~KB_RESCORE_FP64) return fail(ctx, KB_EINVAL, "unknown flags 0x%x", flags);
+    if (std::isnan(nu_min)) return fail(ctx, KB_EINVAL, "nu_min is NaN");
+    const int N = s->N;
+    Plan pl;
+    int rc = plan_times(ctx, times, N, pl);
+    if (rc != KB_OK) return rc;
+    std::vector<int64_t> qx(V), qy(V);
+    for (int v = 0; v < V; ++v) {
+        if ((rc = quant_velocity(ctx, vx[v], &qx[v])) != KB_OK) return rc;
+        if ((rc = quant_velocity(ctx, vy[v], &qy[v])) != KB_OK) return rc;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // host tables in the pinned staging buffer (wait until its previous upload is done)
+    cudaError_t e = cudaEventSynchronize(job->stage_done);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_search staging");
+    // staging layout for this V, N: offs [V][N] | vq [V] | vorder [V] | epoch [N] (8-byte members first)
+    int2 *h_offs = reinterpret_cast<int2 *>(job->stage);
+    float2 *h_vq = reinterpret_cast<float2 *>(h_offs + (size_t)V * N);
+    int *h_vorder = reinterpret_cast<int *>(h_vq + V);
+    int *h_epoch = h_vorder + V;
+    for (int v = 0; v < V; ++v) {
+        for (int j = 0; j < N; ++j)
+            h_offs[(size_t)v * N + j] = make_int2((int)offset_q(qx[v], pl.tq[j]), (int)offset_q(qy[v], pl.tq[j]));
+        h_vorder[v] = v;
+        h_vq[v] = make_float2((float)((double)qx[v] / (double)kVelOne), (float)((double)qy[v] / (double)kVelOne));
+    }
+    for (int j = 0; j < N; ++j) h_epoch[j] = pl.epoch_of[j];
+    e = cudaMemcpyAsync(job->offs, h_offs, (size_t)V * N * sizeof(int2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(job->vorder, h_vorder, (size_t)V * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(job->epoch_of, h_epoch, (size_t)N * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(job->vq, h_vq, (size_t)V * sizeof(float2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(job->stage_done, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_search upload");
+
+    const bool rescore = (flags & KB_RESCORE_FP64) != 0;
+    const int kkeep = rescore ? job_kkeep(topk, flags) : topk;
+    kb::SearchArgs a;
+    a.storage = s->q16 ? s->storage : KB_F32;
+    a.planes = s->q16 ? (const void *)s->q16 : (const void *)s->f32;
+    a.plane_elems = (long long)s->H * s->pitch;
+    a.H = s->H;
+    a.W = s->W;
+    a.pitch = s->pitch;
+    a.N = N;
+    a.n0 = pl.n0;
+    a.epoch_of = job->epoch_of;
+    a.offs = job->offs;
+    a.vorder = job->vorder;
+    a.V = V;
+    a.scales = s->scales;
+    a.nu_min = nu_min;
+    a.k = kkeep;
+    a.out = job->recs;
+    e = kb::launch_search(a, st, ctx->sm_count);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "search kernel");
+    if (rescore) {
+        kb::RescoreArgs r;
+        r.f32 = s->f32;
+        r.plane_elems = a.plane_elems;
+        r.H = s->H;
+        r.W = s->W;
+        r.pitch = s->pitch;
+        r.N = N;
+        r.epoch_of = job->epoch_of;
+        r.offs = job->offs;
+        r.cand = job->recs;
+        r.kc = kkeep;
+        r.k = topk;
+        r.nu_min = (double)nu_min;
+        r.out = job->recs64;
+        e = kb::launch_rescore(r, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rescore kernel");
+    }
+    job->N = N;
+    job->V = V;
+    job->k = topk;
+    job->kkeep = kkeep;
+    job->storage = a.storage;
+    job->rescored = rescore;
+    return KB_OK;
+}
+
+int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream) {
+    if (!job) return KB_EINVAL;
+    kb_ctx *ctx = job->ctx;
+    if (job->k == 0) return fail(ctx, KB_EINVAL, "kb_results: no search has run on this job");
+    size_t need = (size_t)job->H * job->W * job->k;
+    if (n_written) *n_written = need;
+    if (!out) return fail(ctx, KB_EINVAL, "kb_results: out is NULL");
+    if (capacity < need) return fail(ctx, KB_ERANGE, "kb_results: capacity %zu < %zu records", capacity, need);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    kb::ExpandArgs a;
+    a.recs = job->rescored ? nullptr : job->recs;
+    a.recs64 = job->rescored ? job->recs64 : nullptr;
+    a.krec = job->kkeep;
+    a.k = job->k;
+    a.H = job->H;
+    a.W = job->W;
+    a.vq = job->vq;
+    cudaError_t e;
+    if (is_device_ptr(out)) {
+        a.first = 0;
+        a.count = (long long)need;
+        a.out = out;
+        e = kb::launch_expand(a, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "expand kernel");
+        return KB_OK;
+    }
+    const size_t chunk = std::min(need, (size_t)1 << 22);
+    if (job->expand_cap < chunk) {
+        cudaFree(job->expand);
+        dev_release(ctx, job->expand_cap * sizeof(kb_result));
+        job->bytes -= std::min(job->bytes, job->expand_cap * sizeof(kb_result));
+        job->expand = nullptr;
+        job->expand_cap = 0;
+        int rc = dev_alloc(ctx, chunk * sizeof(kb_result), (void **)&job->expand, &job->bytes);
+        if (rc != KB_OK) return rc;
+        job->expand_cap = chunk;
+    }
+    for (size_t first = 0; first < need; first += chunk) {
+        size_t n = std::min(chunk, need - first);
+        a.first = (long long)first;
+        a.count = (long long)n;
+        a.out = job->expand;
+        e = kb::launch_expand(a, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out + first, job->expand, n * sizeof(kb_result), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_results");
+    }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_results");
+    return KB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,224 @@
+// Stage (a): likelihood images of Sec. 2.1.5 on sm_103a.
+//
+//   psi_t(y) = sum_d nw_t(y + d) T_t(d),   phi_t(y) = sum_d w_t(y + d) T_t(d)^2
+//   w = 1/sigma^2 (0 where masked),        nw = n * w (0 where masked, by select)
+//
+// One CTA produces a TY x TX output tile of one epoch.  It stages the input tile
+// plus a halo of r = K/2 pixels in shared memory as (nw, w) pairs (coalesced row
+// loads, zero outside the image), then either
+//   - separable PSF T(dy, dx) = a(dy) b(dx): a horizontal pass into a second
+//     shared tile and a vertical pass to the output (2 K taps per pixel), or
+//   - general PSF: a single pass over the K x K taps (the paper's own choice,
+//     Sec. 2.3, kept for non-Gaussian PSFs).
+// The (psi, phi) pair is carried through both passes as one 64-bit register pair
+// and updated with packed fma.rn.f32x2.  The kernel is HBM-bound: it reads 8 B
+// (9 B with a mask) and writes 8 B per pixel.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "kb_internal.h"
+
+namespace kb {
+
+namespace {
+
+constexpr int TX = 64;
+constexpr int TY = 32;
+constexpr int THREADS = 256;
+
+__device__ __forceinline__ unsigned long long as_u64(float2 v) {
+    return *reinterpret_cast<unsigned long long *>(&v);
+}
+__device__ __forceinline__ float2 as_f2(unsigned long long u) { return *reinterpret_cast<float2 *>(&u); }
+
+// d = a * b + c on both lanes of a float pair
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)), "l"(as_u64(c)));
+    return as_f2(d);
+}
+
+// Sec. 2.1.5 weights with the masking reading: any of mask, non-finite n or
+// sigma^2, sigma^2 <= 0, n > bright_max gives (0, 0).  Selects, never 0 * NaN.
+__device__ __forceinline__ float2 weighted(float n, float v, uint8_t m, float bright_max) {
+    bool bad = (m != 0) || !isfinite(n) || !isfinite(v) || !(v > 0.0f) || (n > bright_max);
+    float w = bad ? 0.0f : 1.0f / v;
+    float nw = bad ? 0.0f : n * w;
+    return make_float2(nw, w);
+}
+
+template <bool SEP>
+__global__ void __launch_bounds__(THREADS) psi_phi_kernel(PsiPhiArgs a) {
+    extern __shared__ float4 smem_raw[];
+    const int K = a.K, r = K / 2;
+    const int e = blockIdx.z;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int AW = TX + 2 * r, AH = TY + 2 * r;
+    const size_t npix = (size_t)a.H * a.W;
+
+    // shared layout: taps | A (AH x AW pairs) | B (AH x TX pairs, separable only)
+    float *s_taps = reinterpret_cast<float *>(smem_raw);
+    const int ntaps = SEP ? 4 * K : 2 * K * K;
+    const int taps_pad = (ntaps + 3) & ~3;
+    float2 *A = reinterpret_cast<float2 *>(s_taps + taps_pad);
+    float2 *B = A + AH * AW;
+
+    const float *taps = a.taps + (size_t)e * ntaps;
+    for (int i = threadIdx.x; i < ntaps; i += THREADS) s_taps[i] = taps[i];
+
+    const float *sci = a.sci + e * npix;
+    const float *var = a.var + e * npix;
+    const uint8_t *msk = a.mask ? a.mask + e * npix : nullptr;
+    for (int i = threadIdx.x; i < AH * AW; i += THREADS) {
+        int ty = i / AW, tx = i - ty * AW;
+        int y = y0 - r + ty, x = x0 - r + tx;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
+            size_t gi = (size_t)y * a.W + x;
+            v = weighted(__ldg(sci + gi), __ldg(var + gi), msk ? __ldg(msk + gi) : (uint8_t)0, a.bright_max);
+        }
+        A[i] = v;
+    }
+    __syncthreads();
+
+    float2 *out = a.out + (size_t)e * a.H * a.pitch;
+    float mpsi = 0.0f, mphi = 0.0f;
+    if (SEP) {
+        // taps: (a, a^2)[K] vertical, then (b, b^2)[K] horizontal, as float pairs
+        const float2 *ta = reinterpret_cast<const float2 *>(s_taps), *tb = ta + K;
+        for (int i = threadIdx.x; i < AH * TX; i += THREADS) {
+            int ty = i / TX, c = i - ty * TX;
+            const float2 *row = A + ty * AW + c;
+            float2 h = make_float2(0.0f, 0.0f);
+            for (int d = 0; d < K; ++d) h = fma2(row[d], tb[d], h);
+            B[i] = h;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < TY * TX; i += THREADS) {
+            int ty = i / TX, c = i - ty * TX;
+            int y = y0 + ty, x = x0 + c;
+            const float2 *col = B + ty * TX + c;
+            float2 o = make_float2(0.0f, 0.0f);
+            for (int d = 0; d < K; ++d) o = fma2(col[d * TX], ta[d], o);
+            if (y < a.H && x < a.W) {
+                out[(size_t)y * a.pitch + x] = o;
+                mpsi = fmaxf(mpsi, fabsf(o.x));
+                mphi = fmaxf(mphi, o.y);
+            }
+        }
+    } else {
+        // taps: (T, T^2)[K*K] as float pairs, row-major (dy, dx)
+        const float2 *t = reinterpret_cast<const float2 *>(s_taps);
+        for (int i = threadIdx.x; i < TY * TX; i += THREADS) {
+            int ty = i / TX, c = i - ty * TX;
+            int y = y0 + ty, x = x0 + c;
+            float2 o = make_float2(0.0f, 0.0f);
+            for (int dy = 0; dy < K; ++dy) {
+                const float2 *row = A + (ty + dy) * AW + c;
+                const float2 *k = t + dy * K;
+                for (int dx = 0; dx < K; ++dx) o = fma2(row[dx], k[dx], o);
+            }
+            if (y < a.H && x < a.W) {
+                out[(size_t)y * a.pitch + x] = o;
+                mpsi = fmaxf(mpsi, fabsf(o.x));
+                mphi = fmaxf(mphi, o.y);
+            }
+        }
+    }
+    if (a.maxbits) {
+        // non-negative floats order like their bit patterns
+        unsigned bp = __reduce_max_sync(0xffffffffu, __float_as_uint(mpsi));
+        unsigned bf = __reduce_max_sync(0xffffffffu, __float_as_uint(mphi));
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(a.maxbits + 2 * e, bp);
+            atomicMax(a.maxbits + 2 * e + 1, bf);
+        }
+    }
+}
+
+// Power-of-two scale s with max/s in [2^14, 2^15): exact to apply, keeps the
+// largest code below the float16 maximum (65504), 1 for an all-zero plane.
+__device__ __forceinline__ float pow2_scale(unsigned maxbits) {
+    float m = __uint_as_float(maxbits);
+    if (!(m > 0.0f)) return 1.0f;
+    int ex = (int)((maxbits >> 23) & 0xff) - 127;   // floor(log2 m) for normal m
+    int sh = ex + 1 - 15;
+    sh = max(-120, min(120, sh));
+    return __uint_as_float((unsigned)(sh + 127) << 23);
+}
+
+template <int STORAGE>
+__global__ void quantize_kernel(const float2 *__restrict__ f32, pair16 *__restrict__ q16, float2 *scales,
+                                const unsigned *__restrict__ maxbits, long long plane_elems) {
+    const int e = blockIdx.y;
+    const float sp = pow2_scale(maxbits[2 * e]), sf = pow2_scale(maxbits[2 * e + 1]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) scales[e] = make_float2(sp, sf);
+    const float ip = 1.0f / sp, iff = 1.0f / sf;   // exact: powers of two
+    const float4 *src = reinterpret_cast<const float4 *>(f32 + e * plane_elems);
+    uint2 *dst = reinterpret_cast<uint2 *>(q16 + e * plane_elems);
+    const long long n2 = plane_elems / 2;   // pitch is a multiple of 4
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2;
+         i += (long long)gridDim.x * blockDim.x) {
+        float4 v = src[i];
+        uint32_t lo, hi;
+        if (STORAGE == KB_BF16) {
+            __nv_bfloat162 p0 = __floats2bfloat162_rn(v.x * ip, v.y * iff);
+            __nv_bfloat162 p1 = __floats2bfloat162_rn(v.z * ip, v.w * iff);
+            lo = *reinterpret_cast<uint32_t *>(&p0);
+            hi = *reinterpret_cast<uint32_t *>(&p1);
+        } else {
+            __half2 p0 = __floats2half2_rn(v.x * ip, v.y * iff);
+            __half2 p1 = __floats2half2_rn(v.z * ip, v.w * iff);
+            lo = *reinterpret_cast<uint32_t *>(&p0);
+            hi = *reinterpret_cast<uint32_t *>(&p1);
+        }
+        dst[i] = make_uint2(lo, hi);
+    }
+}
+
+}  // namespace
+
+size_t taps_floats(int N, int K, bool separable) { return (size_t)N * (separable ? 4 * K : 2 * K * K); }
+
+static size_t psi_phi_smem(int K, bool sep) {
+    int r = K / 2;
+    int ntaps = sep ? 4 * K : 2 * K * K;
+    size_t taps = ((ntaps + 3) & ~3) * sizeof(float);
+    size_t A = (size_t)(TY + 2 * r) * (TX + 2 * r) * sizeof(float2);
+    size_t B = sep ? (size_t)(TY + 2 * r) * TX * sizeof(float2) : 0;
+    return taps + A + B;
+}
+
+cudaError_t launch_psi_phi(const PsiPhiArgs &a, cudaStream_t st) {
+    dim3 grid((a.W + TX - 1) / TX, (a.H + TY - 1) / TY, a.N);
+    size_t smem = psi_phi_smem(a.K, a.separable);
+    cudaError_t err;
+    if (a.separable) {
+        err = cudaFuncSetAttribute(psi_phi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        psi_phi_kernel<true><<<grid, THREADS, smem, st>>>(a);
+    } else {
+        err = cudaFuncSetAttribute(psi_phi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        psi_phi_kernel<false><<<grid, THREADS, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quantize(const float2 *f32, pair16 *q16, float2 *scales, const unsigned *maxbits, int N, int H,
+                            int pitch, int storage, cudaStream_t st) {
+    long long plane = (long long)H * pitch;
+    long long n2 = plane / 2;
+    int blocks = (int)((n2 + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    dim3 grid(blocks, N);
+    if (storage == KB_BF16)
+        quantize_kernel<KB_BF16><<<grid, 256, 0, st>>>(f32, q16, scales, maxbits, plane);
+    else
+        quantize_kernel<KB_F16><<<grid, 256, 0, st>>>(f32, q16, scales, maxbits, plane);
+    return cudaGetLastError();
+}
+
+}  // namespace kb

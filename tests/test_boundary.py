@@ -1,0 +1,81 @@
+"""C-ABI boundary checks that need no GPU: exports, struct layout, host-side offsets."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "kb.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1901_02492_gb300 import build
+    build.build()
+    from paper_1901_02492_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kb_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    so = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+    assert sorted(lib.EXPORTED) == names
+
+
+def test_result_struct_layout_matches_binding(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "kb.h"\nint main(void){'
+                   'printf("%zu", sizeof(kb_result));'
+                   + "".join('printf(" %%zu", offsetof(kb_result, %s));' % f for f in
+                             ["x0", "y0", "vidx", "nobs", "vx", "vy", "psi", "phi", "nu", "alpha"])
+                   + "return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    from paper_1901_02492_gb300 import binding
+    dt = binding.RESULT_DTYPE
+    assert vals[0] == dt.itemsize
+    assert vals[1:] == [dt.fields[f][1] for f in dt.names]
+
+
+def test_offsets_bit_exact_against_oracle(lib):
+    rng = np.random.default_rng(5)
+    for trial in range(5):
+        N = int(rng.integers(1, 40))
+        times = rng.uniform(100.0, 100.0 + rng.uniform(0.01, 60.0), N)
+        vx = rng.uniform(-4000, 4000, 300)
+        vy = rng.uniform(-4000, 4000, 300)
+        a = lib.offsets(times, vx, vy)
+        b = oracle.offsets(times, vx, vy)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # exact half-way products and the reference epoch
+    times = np.array([5.0, 6.0, 5.5, 5.0])
+    vx = np.array([1.5, -1.5, 2.5, -2.5, 0.0, 3.0])
+    a = lib.offsets(times, vx, -vx)
+    b = oracle.offsets(times, vx, -vx)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.all(a[0][:, 0] == 0) and np.all(a[0][:, 3] == 0)
+
+
+def test_offsets_reject_out_of_range(lib):
+    with pytest.raises(lib.KBError):
+        lib.offsets(np.array([0.0, 1.0]), np.array([4096.0]), np.array([0.0]))
+    with pytest.raises(lib.KBError):
+        lib.offsets(np.array([0.0, 64.0]), np.array([1.0]), np.array([0.0]))
+    with pytest.raises(lib.KBError):
+        lib.offsets(np.array([0.0, np.nan]), np.array([1.0]), np.array([0.0]))
+    lib.offsets(np.array([0.0, 63.9]), np.array([4095.9]), np.array([-4095.9]))

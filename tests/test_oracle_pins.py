@@ -349,3 +349,16 @@ def test_off_image_trajectory_is_invalid():
     assert np.all(rec["nobs"][:, :6, 0] == 3) and np.all(rec["nobs"][:, 6, 0] == 2)
     assert np.all(rec["vidx"][:, 7, :] == -1) and np.all(rec["nu"][:, 7, :] == -np.inf)
     assert np.all(rec["vidx"][..., 1] == -1) and np.all(rec["nu"][..., 1] == -np.inf)
+
+
+def test_search_from_images_matches_planes():
+    """The point-evaluated search (used for sampled full-size checks) equals the plane search."""
+    st = synth.small_stack(38, 4, 21, 19, K=5, nan_frac=0.03, mask_frac=0.03)
+    dx, dy = oracle.offsets(st.times, st.vx, st.vy)
+    psi, phi = oracle.psi_phi(st.sci, st.var, st.mask, st.psf)
+    px = np.array([0, 5, 18, 9, 3])
+    py = np.array([0, 11, 20, 2, 17])
+    a = oracle.search_pixels(psi, phi, st.times, dx, dy, 6, px, py)
+    b = oracle.search_pixels_from_images(st.sci, st.var, st.mask, st.psf, st.times, dx, dy, 6, px, py)
+    assert np.array_equal(a["vidx"], b["vidx"]) and np.array_equal(a["nobs"], b["nobs"])
+    np.testing.assert_allclose(a["nu"][a["vidx"] >= 0], b["nu"][b["vidx"] >= 0], rtol=1e-12)

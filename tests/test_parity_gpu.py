@@ -1,0 +1,257 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Small cases are compared element by element (psi/phi planes, every top-k slot);
+they span several kernel tiles (psi/phi 64x32, search 128x8 start pixels) and
+ragged tails.  The full DECam-shaped 12 x 4096 x 4096 search is checked on
+sampled start pixels that the oracle recomputes from the raw images.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from _compare import NU_RTOL, check_topk, nu_tol, oracle_nu_table
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def ctx(kb):
+    c = kb.Context(0)
+    yield c
+    c.close()
+
+
+def to_dev(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def gpu_planes(kb, ctx, st, storage="f32", bright=math.inf, mask=True):
+    N, H, W = st.sci.shape
+    s = kb.Stack(ctx, N, H, W, storage)
+    s.make_psi_phi(to_dev(st.sci), to_dev(st.var), to_dev(st.mask) if mask else None, st.psf, bright)
+    return s
+
+
+def gpu_search(kb, ctx, st, storage="f32", k=None, nu_min=-math.inf, flags=0, times=None, vx=None, vy=None,
+               bright=math.inf):
+    N, H, W = st.sci.shape
+    k = st.k if k is None else k
+    times = st.times if times is None else times
+    vx = st.vx if vx is None else vx
+    vy = st.vy if vy is None else vy
+    s = gpu_planes(kb, ctx, st, storage, bright)
+    job = kb.Job(ctx, H, W, N, len(vx), k, flags)
+    job.search(s, times, vx, vy, k, nu_min, flags)
+    res = job.results()
+    torch.cuda.synchronize()
+    job.free()
+    s.free()
+    return res
+
+
+def oracle_search(st, k=None, nu_min=-np.inf, times=None, vx=None, vy=None, bright=None):
+    k = st.k if k is None else k
+    times = st.times if times is None else times
+    vx = st.vx if vx is None else vx
+    vy = st.vy if vy is None else vy
+    psi, phi = oracle.psi_phi(st.sci, st.var, st.mask, st.psf, bright)
+    dx, dy = oracle.offsets(times, vx, vy)
+    ref = oracle.search_region(psi, phi, times, dx, dy, k, nu_min)
+    table = oracle_nu_table(psi, phi, times, dx, dy)
+    return ref, (lambda p, v: table[p, v])
+
+
+# ------------------------------------------------------------------ stage (a)
+
+def _asym(K, seed):
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(0.1, 1.0, (K, K)).astype(np.float32)
+    return (p / p.sum()).astype(np.float32)
+
+
+@pytest.mark.parametrize("K,sep,mask,bright", [(7, True, False, math.inf), (17, True, True, math.inf),
+                                               (5, False, True, 40.0), (1, True, False, math.inf),
+                                               (31, True, False, math.inf)])
+def test_psi_phi_planes_f32(kb, ctx, K, sep, mask, bright):
+    st = synth.small_stack(100 + K, 3, 77, 150, K=K, sigma=max(K / 6.0, 0.5), var_lo=50, var_hi=150,
+                           nan_frac=0.01, mask_frac=0.02 if mask else 0.0, flux=400.0)
+    if not sep:
+        st.psf = np.stack([_asym(K, e) for e in range(st.psf.shape[0])])
+    s = gpu_planes(kb, ctx, st, bright=bright)
+    N, H, W = st.sci.shape
+    out = torch.empty((N, H, W, 2), dtype=torch.float32, device=DEV)
+    s.copy_planes(0, out)
+    g = out.cpu().numpy()
+    psi, phi = oracle.psi_phi(st.sci, st.var, st.mask, st.psf, None if math.isinf(bright) else bright)
+    scale = np.abs(psi) + np.sqrt(phi)
+    assert np.all(np.abs(g[..., 0] - psi) <= 1e-5 * scale + 1e-30)
+    assert np.all(np.abs(g[..., 1] - phi) <= 1e-5 * phi + 1e-30)
+    assert np.array_equal(g[..., 1] == 0, phi == 0)
+    s.free()
+
+
+# ------------------------------------------------------------------ stage (b), FP32
+
+@pytest.mark.parametrize("k", [1, 4, 8, 16])
+def test_search_f32_small(kb, ctx, k):
+    st = synth.small_stack(7, 5, 70, 150, K=7, nan_frac=0.01, n_angles=8, n_speeds=8, s_hi=12.0,
+                           n_sources=3, flux=40.0)
+    res = gpu_search(kb, ctx, st, k=k)
+    ref, nu_of = oracle_search(st, k=k)
+    check_topk(res, ref, nu_of)
+
+
+def test_search_tiny_workload(kb, ctx):
+    """The 5 x 64 x 64 workload: full comparison of every slot."""
+    st = synth.tiny()
+    res = gpu_search(kb, ctx, st)
+    ref, nu_of = oracle_search(st)
+    check_topk(res, ref, nu_of)
+    assert np.array_equal(res["x0"][5, 7], np.full(st.k, 7)) and np.array_equal(res["y0"][5, 7], np.full(st.k, 5))
+
+
+EDGE_CASES = {
+    "one_epoch": dict(N=1, H=20, W=33),
+    "one_row": dict(N=4, H=1, W=300),
+    "one_column": dict(N=4, H=50, W=1),
+    "ragged": dict(N=6, H=13, W=37),
+    "wide_ragged": dict(N=3, H=9, W=261),
+    "same_time": dict(N=3, H=16, W=40, times=[1.0, 1.0, 1.0]),
+    "unordered_times": dict(N=4, H=24, W=70, times=[2.0, 0.5, 1.25, 0.5]),
+    "fast_off_image": dict(N=4, H=30, W=40, s_lo=30.0, s_hi=60.0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EDGE_CASES))
+def test_search_edge_cases(kb, ctx, name):
+    c = dict(EDGE_CASES[name])
+    times = c.pop("times", None)
+    st = synth.small_stack(11, c.pop("N"), c.pop("H"), c.pop("W"), K=5, nan_frac=0.02, n_angles=6,
+                           n_speeds=5, times=times, **c)
+    res = gpu_search(kb, ctx, st, k=3)
+    ref, nu_of = oracle_search(st, k=3)
+    check_topk(res, ref, nu_of)
+
+
+def test_search_threshold_and_masked_epoch(kb, ctx):
+    st = synth.small_stack(12, 4, 40, 90, K=5, mask_frac=0.05, n_sources=2, flux=30.0)
+    st.var[1, :, :30] = -1.0          # a fully masked band in one epoch
+    res = gpu_search(kb, ctx, st, k=5, nu_min=1.0)
+    ref, nu_of = oracle_search(st, k=5, nu_min=1.0)
+    check_topk(res, ref, nu_of)
+    assert np.all(res["nu"][res["vidx"] >= 0] >= 1.0)
+
+
+def test_search_single_velocity_and_duplicates(kb, ctx):
+    st = synth.small_stack(13, 5, 33, 65, K=5)
+    vx = np.array([3.0, 3.0, 3.01, -2.0])
+    vy = np.array([1.0, 1.0, 1.0, 0.5])
+    res = gpu_search(kb, ctx, st, k=4, vx=vx, vy=vy)
+    ref, nu_of = oracle_search(st, k=4, vx=vx, vy=vy)
+    check_topk(res, ref, nu_of, max_mismatch_frac=0.0)
+    one = gpu_search(kb, ctx, st, k=2, vx=vx[:1], vy=vy[:1])
+    ref1, nu_of1 = oracle_search(st, k=2, vx=vx[:1], vy=vy[:1])
+    check_topk(one, ref1, nu_of1)
+
+
+def test_bright_pixel_limit(kb, ctx):
+    st = synth.small_stack(14, 3, 40, 64, K=5, var_lo=100, var_hi=100, n_sources=3, flux=3000.0)
+    res = gpu_search(kb, ctx, st, k=3, bright=120.0)
+    ref, nu_of = oracle_search(st, k=3, bright=120.0)
+    check_topk(res, ref, nu_of)
+
+
+def test_results_to_device_buffer(kb, ctx):
+    st = synth.small_stack(15, 4, 30, 50, K=5)
+    N, H, W = st.sci.shape
+    s = gpu_planes(kb, ctx, st)
+    job = kb.Job(ctx, H, W, N, st.vx.size, 4)
+    job.search(s, st.times, st.vx, st.vy, 4)
+    host = job.results()
+    dev = torch.empty(H * W * 4 * kb.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=DEV)
+    job.results(dev)
+    torch.cuda.synchronize()
+    devh = dev.cpu().numpy().view(kb.RESULT_DTYPE).reshape(H, W, 4)
+    assert np.array_equal(host, devh)
+    # re-running the same job with a different k and grid reuses its buffers
+    job.search(s, st.times, st.vx[:10], st.vy[:10], 2)
+    again = job.results()
+    ref, nu_of = oracle_search(st, k=2, vx=st.vx[:10], vy=st.vy[:10])
+    check_topk(again, ref, nu_of)
+    job.free()
+    s.free()
+
+
+def test_api_rejects_bad_arguments(kb, ctx):
+    st = synth.small_stack(16, 2, 8, 8, K=3)
+    s = kb.Stack(ctx, 2, 8, 8)
+    with pytest.raises(kb.KBError) as e:   # K even
+        s.make_psi_phi(to_dev(st.sci), to_dev(st.var), None, np.ones((2, 4, 4), np.float32))
+    assert e.value.code == kb.KB_EINVAL
+    with pytest.raises(kb.KBError) as e:   # host pointers for the images
+        s.make_psi_phi(st.sci, st.var, None, st.psf)
+    assert e.value.code == kb.KB_EINVAL
+    job = kb.Job(ctx, 8, 8, 2, 4, 2)
+    with pytest.raises(kb.KBError):        # search before psi/phi exist
+        job.search(s, st.times, st.vx[:4], st.vy[:4])
+    s.make_psi_phi(to_dev(st.sci), to_dev(st.var), None, st.psf)
+    with pytest.raises(kb.KBError):        # more velocities than the job holds
+        job.search(s, st.times, st.vx[:5], st.vy[:5])
+    with pytest.raises(kb.KBError):        # k above the job's k
+        job.search(s, st.times, st.vx[:4], st.vy[:4], topk=3)
+    with pytest.raises(kb.KBError) as e:   # velocity outside the fixed-point range
+        job.search(s, st.times, np.array([5000.0]), np.array([0.0]))
+    assert e.value.code == kb.KB_EINVAL
+    with pytest.raises(kb.KBError) as e:
+        kb.Job(ctx, 8, 8, 2, 4, 17)
+    job.free()
+    s.free()
+
+
+def test_hbm_budget(kb):
+    c = kb.Context(0, hbm_budget=1 << 20)
+    with pytest.raises(kb.KBError) as e:
+        kb.Stack(c, 4, 512, 512)
+    assert e.value.code == kb.KB_ENOMEM
+    assert c.hbm_in_use == 0
+    s = kb.Stack(c, 1, 64, 64)
+    assert 0 < c.hbm_in_use <= 1 << 20
+    s.free()
+    assert c.hbm_in_use == 0
+    c.close()
+
+
+# ------------------------------------------------------------------ full DECam-shaped size
+
+@pytest.fixture(scope="module")
+def decam_stack():
+    return synth.decam()
+
+
+def test_decam_full_size_sampled(kb, ctx, decam_stack):
+    """12 x 4096 x 4096, 1024 velocities, k = 8 (the benchmark's launch configuration):
+    sampled start pixels (corners, edges, injected sources, random) against the oracle."""
+    st = decam_stack
+    N, H, W = st.sci.shape
+    res = gpu_search(kb, ctx, st)
+    rng = np.random.default_rng(99)
+    px = [0, W - 1, 0, W - 1, W // 2, 1, W - 2] + list(rng.integers(0, W, 90))
+    py = [0, 0, H - 1, H - 1, H // 2, H - 2, 1] + list(rng.integers(0, H, 90))
+    for s in st.sources[:20]:
+        px.append(min(max(int(round(s["x0"])), 0), W - 1))
+        py.append(min(max(int(round(s["y0"])), 0), H - 1))
+    px, py = np.array(px), np.array(py)
+    dx, dy = oracle.offsets(st.times, st.vx, st.vy)
+    ref = oracle.search_pixels_from_images(st.sci, st.var, None, st.psf, st.times, dx, dy, st.k, px, py)
+    g = res[py, px]
+
+    def nu_of(p, v):
+        P, F, _ = oracle.trajectory_from_images(st.sci, st.var, None, st.psf, st.times, dx[v], dy[v], px[p], py[p])
+        return P / math.sqrt(F) if F > 0 else -math.inf
+    check_topk(g, ref, nu_of)
+    assert np.all(g["x0"] == px[:, None]) and np.all(g["y0"] == py[:, None])
