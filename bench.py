@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--variant", type=int, default=0, help="search kernel shape (0 = automatic)")
     return ap.parse_args()
 
 
@@ -67,7 +68,8 @@ def workload_config(args, st, world):
     name = "decam %dx%dx%d, %d velocities, k=%d" % (N, H, W, st.vx.size, st.k)
     return {"workload": name, "epochs": N, "height": H, "width": W, "velocities": int(st.vx.size),
             "topk": st.k, "psf": "17x17 Gaussian, FWHM 3.5-4.5 px", "storage": args.storage,
-            "rescore_fp64": bool(args.rescore), "evals_per_step": int(N * H * W * st.vx.size),
+            "rescore_fp64": bool(args.rescore), "search_variant": args.variant,
+            "evals_per_step": int(N * H * W * st.vx.size),
             "l2": "inputs larger than L2 (%.2f GB of psi/phi planes)" % (N * H * W * 8 / 1e9),
             "parallelism": "replicas%d" % world}
 
@@ -234,6 +236,7 @@ def run_ours(args):
     evals = N * H * W * V
     flags = kb.KB_RESCORE_FP64 if args.rescore else 0
     ctx = kb.Context(dev.index)
+    ctx.set_search_variant(args.variant)
     stack = kb.Stack(ctx, N, H, W, args.storage)
     job = kb.Job(ctx, H, W, N, V, k, flags)
     sci_h = torch.from_numpy(st.sci).pin_memory()

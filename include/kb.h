@@ -57,7 +57,8 @@ extern "C" {
 #define KB_F16 2   /* (psi, phi) as two float16 per pixel with per-epoch power-of-two scales, 4 bytes */
 
 /* ---- search flags -------------------------------------------------------- */
-#define KB_RESCORE_FP64 1 /* re-rank the kept candidates with FP64 sums of the FP32 planes */
+#define KB_RESCORE_FP64 1 /* re-rank the kept candidates with FP64 sums of the FP32 planes;
+                           * pixels the certificate cannot clear are re-searched in FP64 */
 
 /* ---- limits -------------------------------------------------------------- */
 #define KB_MAX_EPOCHS 128   /* N */
@@ -96,12 +97,26 @@ const char *kb_last_error(const kb_ctx *ctx);
 /* Bytes of device memory currently held by the context's stacks and jobs. */
 size_t kb_hbm_in_use(const kb_ctx *ctx);
 
+/* Tuning hook: force the search kernel used by later kb_search calls of this
+ * context; results do not depend on the choice.
+ *   0      automatic: the register-gather kernel in its default shape
+ *   1..4   register-gather kernel, (loads per lane, epochs per load batch) =
+ *          (4,4), (2,4), (4,8), (2,8) for FP32 and (2,4), (1,4), (2,8), (1,8)
+ *          for 16-bit storage, whose loads are pixel pairs; default (2,8) / (1,8)
+ *   5..8   TMA-pipelined kernel, (pixels per lane, stages, epochs per wait
+ *          group) = (2,8,2), (2,12,4), (4,8,2), (4,12,4)
+ * KB_EINVAL for other values. */
+int kb_set_search_variant(kb_ctx *ctx, int variant);
+
 /* ---- stage (a): likelihood images --------------------------------------- */
 
 /* Allocate the device planes for an N x H x W stack (1 <= N <= KB_MAX_EPOCHS,
  * 1 <= H, W <= KB_MAX_SIDE).  The FP32 (psi, phi) planes are always kept; with
  * storage KB_BF16 or KB_F16 a 16-bit copy with per-epoch scales is kept as well
- * and is what kb_search reads.  *out is owned by the caller: kb_stack_free. */
+ * (twice: also shifted by one pixel, so that any two adjacent pixels are one
+ * aligned load) and is what kb_search reads.  Device memory: N * H * (W + 260)
+ * * 8 bytes, twice that with 16-bit storage.  *out is owned by the caller:
+ * kb_stack_free. */
 int kb_stack_create(kb_ctx *ctx, int N, int H, int W, int storage, kb_stack **out);
 void kb_stack_free(kb_stack *s);
 
@@ -163,6 +178,21 @@ void kb_job_free(kb_job *j);
  * in stream order and may be re-run by calling kb_search again. */
 int kb_search(kb_job *job, const kb_stack *s, const double *times, const double *vx, const double *vy, int V,
               int topk, float nu_min, int flags, void *stream);
+
+/* Wait for the job's last search and report its device status: KB_OK, or
+ * KB_ETIMEOUT when a bounded device-side wait of the pipelined kernel gave up
+ * (its results are then invalid).  kb_results with a host destination calls it. */
+int kb_job_wait(kb_job *job);
+
+/* After a search with KB_RESCORE_FP64: the number of start pixels whose
+ * rescored top-k the certificate could not clear and that were searched again
+ * exhaustively in FP64 (waits for the job like kb_job_wait).  The certificate:
+ * a trajectory outside the k_c candidates of the reduced-precision pass scored
+ * at most nu16 of the last candidate; the pixel is cleared when the k-th FP64
+ * nu (or nu_min) exceeds that by more than twice the largest |nu16 - nu64| of
+ * the pixel's own candidates plus the storage unit roundoff times (1 + |nu|).
+ * 0 for searches without rescoring. */
+int kb_job_repaired(kb_job *job, size_t *n_pixels);
 
 /* Write the job's results as kb_result records, [H][W][topk] in start-pixel
  * row-major order, best first within a pixel.  out is a host or device pointer

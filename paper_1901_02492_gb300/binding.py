@@ -46,6 +46,7 @@ _kb_init = _sig("kb_init", _i32, [ctypes.POINTER(_P), _i32, _sz])
 _kb_destroy = _sig("kb_destroy", None, [_P])
 _kb_last_error = _sig("kb_last_error", ctypes.c_char_p, [_P])
 _kb_hbm_in_use = _sig("kb_hbm_in_use", _sz, [_P])
+_kb_set_search_variant = _sig("kb_set_search_variant", _i32, [_P, _i32])
 _kb_stack_create = _sig("kb_stack_create", _i32, [_P, _i32, _i32, _i32, _i32, ctypes.POINTER(_P)])
 _kb_stack_free = _sig("kb_stack_free", None, [_P])
 _kb_make_psi_phi = _sig("kb_make_psi_phi", _i32, [_P, _P, _P, _P, _P, _i32, _f32, _P])
@@ -56,10 +57,12 @@ _kb_job_create = _sig("kb_job_create", _i32, [_P, _i32, _i32, _i32, _i32, _i32, 
 _kb_job_free = _sig("kb_job_free", None, [_P])
 _kb_search = _sig("kb_search", _i32, [_P, _P, _P, _P, _P, _i32, _i32, _f32, _i32, _P])
 _kb_results = _sig("kb_results", _i32, [_P, _P, _sz, ctypes.POINTER(_sz), _P])
+_kb_job_wait = _sig("kb_job_wait", _i32, [_P])
+_kb_job_repaired = _sig("kb_job_repaired", _i32, [_P, ctypes.POINTER(_sz)])
 
-EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_stack_create", "kb_stack_free",
+EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_search_variant", "kb_stack_create", "kb_stack_free",
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
-            "kb_job_free", "kb_search", "kb_results"]
+            "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results"]
 
 
 class KBError(RuntimeError):
@@ -108,6 +111,9 @@ class Context:
     @property
     def last_error(self) -> str:
         return _kb_last_error(self.h).decode()
+
+    def set_search_variant(self, variant: int):
+        self.check(_kb_set_search_variant(self.h, int(variant)))
 
     @property
     def hbm_in_use(self) -> int:
@@ -195,6 +201,16 @@ class Job:
                                   int(topk), float(nu_min), int(flags), _stream(stream)))
         self.k = topk
 
+    def wait(self):
+        """Wait for the last search; raises KBError(KB_ETIMEOUT) if a device wait gave up."""
+        self.ctx.check(_kb_job_wait(self.h))
+
+    def repaired(self) -> int:
+        """Pixels re-searched in FP64 because the rescoring certificate could not clear them."""
+        n = _sz()
+        self.ctx.check(_kb_job_repaired(self.h, ctypes.byref(n)))
+        return int(n.value)
+
     def results(self, out=None, stream=None):
         """Records [H][W][k] of RESULT_DTYPE.  out: None (new numpy array), a numpy array of
         RESULT_DTYPE, or a CUDA uint8 tensor of >= H*W*k*48 bytes (device output)."""
@@ -221,3 +237,4 @@ class Job:
             self.free()
         except Exception:
             pass
+

@@ -190,6 +190,13 @@ const char *kb_last_error(const kb_ctx *ctx) { return ctx ? ctx->err.c_str() : "
 
 size_t kb_hbm_in_use(const kb_ctx *ctx) { return ctx ? ctx->in_use : 0; }
 
+int kb_set_search_variant(kb_ctx *ctx, int variant) {
+    if (!ctx) return KB_EINVAL;
+    if (variant < 0 || variant > 8) return fail(ctx, KB_EINVAL, "search variant %d not in 0..8", variant);
+    ctx->search_variant = variant;
+    return KB_OK;
+}
+
 // ---- stacks ------------------------------------------------------------------
 
 int kb_stack_create(kb_ctx *ctx, int N, int H, int W, int storage, kb_stack **out) {
@@ -206,17 +213,17 @@ int kb_stack_create(kb_ctx *ctx, int N, int H, int W, int storage, kb_stack **ou
     s->N = N;
     s->H = H;
     s->W = W;
-    s->pitch = (W + 3) & ~3;
+    s->L = kb::make_layout(H, W);
     s->storage = storage;
-    size_t plane = (size_t)H * s->pitch;
+    size_t plane = (size_t)s->L.plane_elems;
     int rc = dev_alloc(ctx, (size_t)N * plane * sizeof(float2), (void **)&s->f32, &s->bytes);
     if (rc == KB_OK && storage != KB_F32)
-        rc = dev_alloc(ctx, (size_t)N * plane * sizeof(kb::pair16), (void **)&s->q16, &s->bytes);
+        rc = dev_alloc(ctx, (size_t)2 * N * plane * sizeof(kb::pair16), (void **)&s->q16, &s->bytes);
     if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)N * sizeof(float2), (void **)&s->scales, &s->bytes);
     if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)2 * N * sizeof(unsigned), (void **)&s->maxbits, &s->bytes);
     cudaError_t e = cudaSuccess;
     if (rc == KB_OK) e = cudaMemset(s->f32, 0, (size_t)N * plane * sizeof(float2));
-    if (rc == KB_OK && e == cudaSuccess && s->q16) e = cudaMemset(s->q16, 0, (size_t)N * plane * sizeof(kb::pair16));
+    if (rc == KB_OK && e == cudaSuccess && s->q16) e = cudaMemset(s->q16, 0, (size_t)2 * N * plane * sizeof(kb::pair16));
     if (rc == KB_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&s->taps_done, cudaEventDisableTiming);
     if (rc == KB_OK && e != cudaSuccess) rc = cuda_fail(ctx, e, "kb_stack_create");
     if (rc != KB_OK) {
@@ -314,7 +321,9 @@ int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8
     a.N = N;
     a.H = s->H;
     a.W = s->W;
-    a.pitch = s->pitch;
+    a.pitch = s->L.pitch;
+    a.plane_elems = s->L.plane_elems;
+    a.origin = s->L.origin;
     a.K = K;
     a.separable = sep;
     a.taps = s->taps;
@@ -323,7 +332,7 @@ int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8
     e = kb::launch_psi_phi(a, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "psi/phi kernel");
     if (q) {
-        e = kb::launch_quantize(s->f32, s->q16, s->scales, s->maxbits, N, s->H, s->pitch, s->storage, st);
+        e = kb::launch_quantize(s->f32, s->q16, s->scales, s->maxbits, N, s->L.plane_elems, s->storage, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "quantize kernel");
     }
     s->filled = true;
@@ -342,8 +351,13 @@ int kb_stack_copy_planes(const kb_stack *s, int which, void *dst, size_t dst_byt
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     bool dev = is_device_ptr(dst);
-    cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)s->W * elem, src, (size_t)s->pitch * elem, (size_t)s->W * elem,
-                                      (size_t)s->N * s->H, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaSuccess;
+    for (int ep = 0; ep < s->N && e == cudaSuccess; ++ep) {
+        const char *from = (const char *)src + (size_t)(ep * s->L.plane_elems + s->L.origin) * elem;
+        char *to = (char *)dst + (size_t)ep * s->H * s->W * elem;
+        e = cudaMemcpy2DAsync(to, (size_t)s->W * elem, from, (size_t)s->L.pitch * elem, (size_t)s->W * elem,
+                              (size_t)s->H, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    }
     if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_stack_copy_planes");
     return KB_OK;
@@ -412,16 +426,22 @@ int kb_job_create(kb_ctx *ctx, int H, int W, int N, int V, int topk, int flags, 
     size_t npix = (size_t)H * W;
     int rc = dev_alloc(ctx, (size_t)V * N * sizeof(int2), (void **)&j->offs, &j->bytes);
     if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)V * sizeof(int), (void **)&j->vorder, &j->bytes);
+    if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)V * N * sizeof(uint32_t), (void **)&j->ptab, &j->bytes);
+    if (rc == KB_OK) rc = dev_alloc(ctx, sizeof(int), (void **)&j->status, &j->bytes);
     if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)N * sizeof(int), (void **)&j->epoch_of, &j->bytes);
     if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)V * sizeof(float2), (void **)&j->vq, &j->bytes);
     if (rc == KB_OK) rc = dev_alloc(ctx, npix * j->kkeep_cap * sizeof(kb::Rec), (void **)&j->recs, &j->bytes);
     if (rc == KB_OK && (flags & KB_RESCORE_FP64))
         rc = dev_alloc(ctx, npix * topk * sizeof(kb::Rec64), (void **)&j->recs64, &j->bytes);
+    if (rc == KB_OK && (flags & KB_RESCORE_FP64)) rc = dev_alloc(ctx, npix * sizeof(int), (void **)&j->ulist, &j->bytes);
+    if (rc == KB_OK && (flags & KB_RESCORE_FP64)) rc = dev_alloc(ctx, sizeof(int), (void **)&j->ucount, &j->bytes);
     if (rc == KB_OK) {
         j->stage_bytes = (size_t)V * N * sizeof(int2) + (size_t)V * sizeof(int) + (size_t)N * sizeof(int) +
-                         (size_t)V * sizeof(float2);
+                         (size_t)V * sizeof(float2) + (size_t)V * N * sizeof(uint32_t);
         cudaError_t e = cudaMallocHost(&j->stage, j->stage_bytes);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->stage_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMemset(j->status, 0, sizeof(int));
         if (e != cudaSuccess) rc = cuda_fail(ctx, e, "kb_job_create");
     }
     if (rc != KB_OK) {
@@ -439,12 +459,17 @@ void kb_job_free(kb_job *j) {
         cudaEventSynchronize(j->stage_done);
         cudaEventDestroy(j->stage_done);
     }
+    if (j->done) cudaEventDestroy(j->done);
     cudaFree(j->offs);
     cudaFree(j->vorder);
+    cudaFree(j->ptab);
+    cudaFree(j->status);
     cudaFree(j->epoch_of);
     cudaFree(j->vq);
     cudaFree(j->recs);
     cudaFree(j->recs64);
+    cudaFree(j->ulist);
+    cudaFree(j->ucount);
     cudaFree(j->expand);
     cudaFreeHost(j->stage);
     dev_release(j->ctx, j->bytes);
@@ -485,17 +510,43 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     float2 *h_vq = reinterpret_cast<float2 *>(h_offs + (size_t)V * N);
     int *h_vorder = reinterpret_cast<int *>(h_vq + V);
     int *h_epoch = h_vorder + V;
+    uint32_t *h_ptab = reinterpret_cast<uint32_t *>(h_epoch + N);
     for (int v = 0; v < V; ++v) {
         for (int j = 0; j < N; ++j)
             h_offs[(size_t)v * N + j] = make_int2((int)offset_q(qx[v], pl.tq[j]), (int)offset_q(qy[v], pl.tq[j]));
         h_vorder[v] = v;
         h_vq[v] = make_float2((float)((double)qx[v] / (double)kVelOne), (float)((double)qy[v] / (double)kVelOne));
     }
+    // Processing order: by the offset at the latest epoch (dy, then dx).  The CTAs
+    // resident at one time cover a band of start rows; in this order the rows of
+    // every epoch's plane that a band reads are used by a contiguous run of
+    // velocities, so the live set of all epochs stays in L2 instead of each
+    // velocity re-fetching its rows from HBM.
+    {
+        const int2 *last = h_offs + (N - 1);
+        std::stable_sort(h_vorder, h_vorder + V, [&](int a, int b) {
+            int2 oa = last[(size_t)a * N], ob = last[(size_t)b * N];
+            return oa.y < ob.y || (oa.y == ob.y && oa.x < ob.x);
+        });
+    }
     for (int j = 0; j < N; ++j) h_epoch[j] = pl.epoch_of[j];
+    // producer table of the pipelined kernel: (dx, dy) as int16 pairs for the
+    // non-reference epochs, in processing order (offsets beyond +-32767 are
+    // outside any image the library accepts, so clamping keeps them outside)
+    const int NJ = N - pl.n0;
+    for (int i = 0; i < V; ++i)
+        for (int jj = 0; jj < NJ; ++jj) {
+            int2 o = h_offs[(size_t)h_vorder[i] * N + pl.n0 + jj];
+            int ox = std::max(-32767, std::min(32767, o.x)), oy = std::max(-32767, std::min(32767, o.y));
+            h_ptab[(size_t)i * NJ + jj] = ((uint32_t)oy << 16) | ((uint32_t)ox & 0xffffu);
+        }
     e = cudaMemcpyAsync(job->offs, h_offs, (size_t)V * N * sizeof(int2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(job->vorder, h_vorder, (size_t)V * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(job->epoch_of, h_epoch, (size_t)N * sizeof(int), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(job->vq, h_vq, (size_t)V * sizeof(float2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && NJ > 0)
+        e = cudaMemcpyAsync(job->ptab, h_ptab, (size_t)V * NJ * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(job->status, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaEventRecord(job->stage_done, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_search upload");
 
@@ -504,10 +555,13 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     kb::SearchArgs a;
     a.storage = s->q16 ? s->storage : KB_F32;
     a.planes = s->q16 ? (const void *)s->q16 : (const void *)s->f32;
-    a.plane_elems = (long long)s->H * s->pitch;
+    a.plane_elems = s->L.plane_elems;
+    a.origin = s->L.origin;
+    a.phase1 = (long long)N * s->L.plane_elems;
+    a.pad_x = s->L.pad_x;
     a.H = s->H;
     a.W = s->W;
-    a.pitch = s->pitch;
+    a.pitch = s->L.pitch;
     a.N = N;
     a.n0 = pl.n0;
     a.epoch_of = job->epoch_of;
@@ -518,15 +572,22 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     a.nu_min = nu_min;
     a.k = kkeep;
     a.out = job->recs;
-    e = kb::launch_search(a, st, ctx->sm_count);
+    a.variant = ctx->search_variant;
+    a.ptab = job->ptab;
+    a.status = job->status;
+    if (a.variant >= 5)
+        e = kb::launch_search_tma(a, st);
+    else
+        e = kb::launch_search(a, st, ctx->sm_count);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "search kernel");
     if (rescore) {
         kb::RescoreArgs r;
         r.f32 = s->f32;
         r.plane_elems = a.plane_elems;
+        r.origin = a.origin;
         r.H = s->H;
         r.W = s->W;
-        r.pitch = s->pitch;
+        r.pitch = s->L.pitch;
         r.N = N;
         r.epoch_of = job->epoch_of;
         r.offs = job->offs;
@@ -535,9 +596,17 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
         r.k = topk;
         r.nu_min = (double)nu_min;
         r.out = job->recs64;
-        e = kb::launch_rescore(r, st);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "rescore kernel");
+        r.V = V;
+        r.unit = s->q16 ? (s->storage == KB_BF16 ? 0x1p-8 : 0x1p-11) : 0x1p-24;
+        r.ulist = job->ulist;
+        r.ucount = job->ucount;
+        e = cudaMemsetAsync(job->ucount, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = kb::launch_rescore(r, st);
+        if (e == cudaSuccess) e = kb::launch_repair(r, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rescore kernels");
     }
+    e = cudaEventRecord(job->done, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_search");
     job->N = N;
     job->V = V;
     job->k = topk;
@@ -597,6 +666,31 @@ int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, 
     }
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_results");
+    return kb_job_wait(job);
+}
+
+int kb_job_repaired(kb_job *job, size_t *n_pixels) {
+    if (!job || !n_pixels) return KB_EINVAL;
+    *n_pixels = 0;
+    int rc = kb_job_wait(job);
+    if (rc != KB_OK || !job->rescored) return rc;
+    DeviceGuard g(job->ctx->device);
+    int n = 0;
+    cudaError_t e = cudaMemcpy(&n, job->ucount, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(job->ctx, e, "kb_job_repaired");
+    *n_pixels = (size_t)n;
+    return KB_OK;
+}
+
+int kb_job_wait(kb_job *job) {
+    if (!job) return KB_EINVAL;
+    kb_ctx *ctx = job->ctx;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaEventSynchronize(job->done);
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, job->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_job_wait");
+    if (st != 0) return fail(ctx, KB_ETIMEOUT, "a bounded device-side wait of the search gave up; results are invalid");
     return KB_OK;
 }
 

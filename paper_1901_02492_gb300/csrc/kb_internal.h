@@ -15,6 +15,27 @@ namespace kb {
 // Packed 16-bit (psi, phi) pair: low half psi, high half phi.
 typedef uint32_t pair16;
 
+// Plane layout.  Every psi/phi plane row carries pad_x = kSpan zero pixels on
+// its left and right; pixel (x, y) of epoch e is element
+// e * plane_elems + origin + y * pitch + x with origin = pad_x.  A warp span of
+// up to kSpan pixels that overlaps the image only partly therefore reads exactly
+// 0 for its off-image pixels ("outside contributes nothing") with no per-lane
+// bounds checks.
+constexpr int kSpan = 128;
+struct Layout {
+    int pad_x = 0, pitch = 0, rows = 0;
+    long long plane_elems = 0, origin = 0;
+};
+inline Layout make_layout(int H, int W) {
+    Layout L;
+    L.pad_x = kSpan;
+    L.pitch = (W + 2 * kSpan + 3) & ~3;
+    L.rows = H;
+    L.plane_elems = (long long)L.rows * L.pitch;
+    L.origin = L.pad_x;
+    return L;
+}
+
 // Device record of one kept trajectory (16 bytes, one vector store).
 struct Rec {
     float psi, phi, nu;
@@ -38,6 +59,7 @@ struct kb_ctx {
     size_t in_use = 0;
     int sm_count = 0;
     size_t smem_optin = 0;
+    int search_variant = 0;   // 0 = automatic
     std::string err;
     std::mutex mu;
 };
@@ -45,10 +67,11 @@ struct kb_ctx {
 struct kb_stack {
     kb_ctx *ctx = nullptr;
     int N = 0, H = 0, W = 0;
-    int pitch = 0;         // elements per row (>= W, multiple of 4)
+    kb::Layout L;
     int storage = KB_F32;
-    float2 *f32 = nullptr;        // [N][H][pitch] (psi, phi)
-    kb::pair16 *q16 = nullptr;    // [N][H][pitch] packed 16-bit codes, or null
+    float2 *f32 = nullptr;        // [N][plane] (psi, phi), zero border
+    kb::pair16 *q16 = nullptr;    // [2][N][plane] packed 16-bit codes: phase 0, and phase 1 shifted by one
+                                  // element (phase1[i] = phase0[i + 1]); null for FP32 storage
     float2 *scales = nullptr;     // device [N] (psi scale, phi scale)
     unsigned *maxbits = nullptr;  // device [2N] max |psi|, max phi (float bits) for the scales
     float *taps = nullptr;        // device per-epoch PSF taps (layout in kb_psiphi.cu)
@@ -69,6 +92,9 @@ struct kb_job {
     // device tables
     int2 *offs = nullptr;        // [Vcap][Ncap] (dx, dy) in time order of epochs
     int *vorder = nullptr;       // [Vcap] processing order -> caller vidx
+    uint32_t *ptab = nullptr;    // [Vcap][Ncap] producer table, processing order
+    int *status = nullptr;       // device status word of the last search
+    cudaEvent_t done = nullptr;  // recorded after the last search's kernels
     int *epoch_of = nullptr;     // [Ncap] time-order position -> stack epoch
     float2 *vq = nullptr;        // [Vcap] quantised velocity (px/day) for the results
     // pinned staging for the tables
@@ -78,6 +104,8 @@ struct kb_job {
     // results
     kb::Rec *recs = nullptr;     // [H*W][kkeep_cap]
     kb::Rec64 *recs64 = nullptr; // [H*W][kcap] (rescoring)
+    int *ulist = nullptr;        // [H*W] pixels whose rescored top-k was not certified (rescoring)
+    int *ucount = nullptr;       // their number (rescoring)
     int kkeep_cap = 0;
     kb_result *expand = nullptr; // device staging for host-bound kb_results (lazy)
     size_t expand_cap = 0;
@@ -92,6 +120,7 @@ struct PsiPhiArgs {
     const uint8_t *mask;   // may be null
     float bright_max;
     int N, H, W, pitch, K;
+    long long plane_elems, origin;
     bool separable;
     const float *taps;     // device taps (see kb_psiphi.cu)
     float2 *out;           // [N][H][pitch]
@@ -99,41 +128,57 @@ struct PsiPhiArgs {
 };
 cudaError_t launch_psi_phi(const PsiPhiArgs &a, cudaStream_t st);
 cudaError_t launch_quantize(const float2 *f32, pair16 *q16, float2 *scales, const unsigned *maxbits, int N,
-                            int H, int pitch, int storage, cudaStream_t st);
+                            long long plane_elems, int storage, cudaStream_t st);
 // layout helper: floats needed for the taps of N epochs with kernel size K
 size_t taps_floats(int N, int K, bool separable);
 
 // ---- stage (b) ---------------------------------------------------------------
 struct SearchArgs {
-    const void *planes;      // float2 or pair16 planes [N][H][pitch]
+    const void *planes;      // float2 planes, or pair16 planes of both phases
     int storage;             // KB_F32 / KB_BF16 / KB_F16
-    long long plane_elems;   // H * pitch
+    long long plane_elems;   // elements per plane (layout)
+    long long origin;        // element of pixel (0, 0) within a plane
+    long long phase1;        // element offset of the 16-bit phase-1 copy (N * plane_elems)
+    int pad_x;               // zero columns left of every row (layout)
     int H, W, pitch, N;      // N epochs, in time order through epoch_of
     int n0;                  // leading time-ordered epochs at offset 0 for every velocity
     const int *epoch_of;     // [N]
     const int2 *offs;        // [V][N] time order
     const int *vorder;       // [V]
     int V;
-    const float2 *scales;    // [N] stack epochs (16-bit storage)
+    const float2 *scales;    // [N] stack epochs (16-bit storage), device
     float nu_min;
-    int k;                   // results kept per pixel (<= 16)
+    int k;                   // results kept per pixel (<= 32)
     Rec *out;                // [H*W][k]
+    int variant;             // kernel shape, 0 = automatic
+    const uint32_t *ptab;    // [V][N - n0] packed (dx, dy) int16 in processing order (pipelined kernel)
+    int *status;             // device status word: KB_ETIMEOUT if a bounded wait gave up
 };
+// register-gather kernel (variant 0 = its default shape, 1..4)
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, int sm_count);
+// TMA-pipelined kernel (variants 5..8)
+cudaError_t launch_search_tma(const SearchArgs &a, cudaStream_t st);
 
 struct RescoreArgs {
-    const float2 *f32;       // FP32 planes [N][H][pitch]
-    long long plane_elems;
-    int H, W, pitch, N;
+    const float2 *f32;       // FP32 planes
+    long long plane_elems, origin;
+    int H, W, pitch, N, V;
     const int *epoch_of;
     const int2 *offs;        // [V][N] time order
     const Rec *cand;         // [H*W][kc]
     int kc;                  // candidates per pixel
     int k;                   // results per pixel
     double nu_min;
+    double unit;             // unit roundoff of the searched storage (0 for FP32)
     Rec64 *out;              // [H*W][k]
+    int *ulist;              // uncertain pixels (capacity H*W)
+    int *ucount;             // their number
 };
+// FP64 rescoring of the candidates with the per-pixel certificate; uncertain
+// pixels are appended to ulist
 cudaError_t launch_rescore(const RescoreArgs &a, cudaStream_t st);
+// exhaustive FP64 re-search of the uncertain pixels (one warp per pixel)
+cudaError_t launch_repair(const RescoreArgs &a, cudaStream_t st);
 
 struct ExpandArgs {
     const Rec *recs;         // [H*W][krec] or null

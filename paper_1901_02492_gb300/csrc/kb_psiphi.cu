@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(THREADS) psi_phi_kernel(PsiPhiArgs a) {
     }
     __syncthreads();
 
-    float2 *out = a.out + (size_t)e * a.H * a.pitch;
+    float2 *out = a.out + e * a.plane_elems + a.origin;
     float mpsi = 0.0f, mphi = 0.0f;
     if (SEP) {
         // taps: (a, a^2)[K] vertical, then (b, b^2)[K] horizontal, as float pairs
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(THREADS) psi_phi_kernel(PsiPhiArgs a) {
             float2 o = make_float2(0.0f, 0.0f);
             for (int d = 0; d < K; ++d) o = fma2(col[d * TX], ta[d], o);
             if (y < a.H && x < a.W) {
-                out[(size_t)y * a.pitch + x] = o;
+                out[(long long)y * a.pitch + x] = o;
                 mpsi = fmaxf(mpsi, fabsf(o.x));
                 mphi = fmaxf(mphi, o.y);
             }
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(THREADS) psi_phi_kernel(PsiPhiArgs a) {
                 for (int dx = 0; dx < K; ++dx) o = fma2(row[dx], k[dx], o);
             }
             if (y < a.H && x < a.W) {
-                out[(size_t)y * a.pitch + x] = o;
+                out[(long long)y * a.pitch + x] = o;
                 mpsi = fmaxf(mpsi, fabsf(o.x));
                 mphi = fmaxf(mphi, o.y);
             }
@@ -150,31 +150,41 @@ __device__ __forceinline__ float pow2_scale(unsigned maxbits) {
 }
 
 template <int STORAGE>
+__device__ __forceinline__ uint32_t quant_pair(float2 v, float ip, float iff) {
+    if (STORAGE == KB_BF16) {
+        __nv_bfloat162 p = __floats2bfloat162_rn(v.x * ip, v.y * iff);
+        return *reinterpret_cast<uint32_t *>(&p);
+    } else {
+        __half2 p = __floats2half2_rn(v.x * ip, v.y * iff);
+        return *reinterpret_cast<uint32_t *>(&p);
+    }
+}
+
+// Writes both phases of the 16-bit copy of plane e: phase 0 holds the code of
+// element i at i, phase 1 holds the code of element i + 1 at i, so that any two
+// adjacent pixels are one 8-byte-aligned load in one of the two phases.  The
+// element after a plane's last one lies in the zero border of the next plane
+// (or past the last plane), whose code is 0 whatever the scale.
+template <int STORAGE>
 __global__ void quantize_kernel(const float2 *__restrict__ f32, pair16 *__restrict__ q16, float2 *scales,
-                                const unsigned *__restrict__ maxbits, long long plane_elems) {
+                                const unsigned *__restrict__ maxbits, int N, long long plane_elems) {
     const int e = blockIdx.y;
     const float sp = pow2_scale(maxbits[2 * e]), sf = pow2_scale(maxbits[2 * e + 1]);
     if (blockIdx.x == 0 && threadIdx.x == 0) scales[e] = make_float2(sp, sf);
     const float ip = 1.0f / sp, iff = 1.0f / sf;   // exact: powers of two
-    const float4 *src = reinterpret_cast<const float4 *>(f32 + e * plane_elems);
-    uint2 *dst = reinterpret_cast<uint2 *>(q16 + e * plane_elems);
-    const long long n2 = plane_elems / 2;   // pitch is a multiple of 4
+    const float2 *src = f32 + e * plane_elems;
+    pair16 *d0 = q16 + e * plane_elems;
+    pair16 *d1 = q16 + ((long long)N + e) * plane_elems;
+    const long long n2 = plane_elems / 2;   // plane_elems is a multiple of 4
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2;
          i += (long long)gridDim.x * blockDim.x) {
-        float4 v = src[i];
-        uint32_t lo, hi;
-        if (STORAGE == KB_BF16) {
-            __nv_bfloat162 p0 = __floats2bfloat162_rn(v.x * ip, v.y * iff);
-            __nv_bfloat162 p1 = __floats2bfloat162_rn(v.z * ip, v.w * iff);
-            lo = *reinterpret_cast<uint32_t *>(&p0);
-            hi = *reinterpret_cast<uint32_t *>(&p1);
-        } else {
-            __half2 p0 = __floats2half2_rn(v.x * ip, v.y * iff);
-            __half2 p1 = __floats2half2_rn(v.z * ip, v.w * iff);
-            lo = *reinterpret_cast<uint32_t *>(&p0);
-            hi = *reinterpret_cast<uint32_t *>(&p1);
-        }
-        dst[i] = make_uint2(lo, hi);
+        const float4 v = reinterpret_cast<const float4 *>(src)[i];
+        const uint32_t c0 = quant_pair<STORAGE>(make_float2(v.x, v.y), ip, iff);
+        const uint32_t c1 = quant_pair<STORAGE>(make_float2(v.z, v.w), ip, iff);
+        // the element after the plane's last one is the next plane's first: a border pixel, code 0
+        const uint32_t c2 = (2 * i + 2 < plane_elems) ? quant_pair<STORAGE>(src[2 * i + 2], ip, iff) : 0u;
+        reinterpret_cast<uint2 *>(d0)[i] = make_uint2(c0, c1);
+        reinterpret_cast<uint2 *>(d1)[i] = make_uint2(c1, c2);
     }
 }
 
@@ -207,17 +217,16 @@ cudaError_t launch_psi_phi(const PsiPhiArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_quantize(const float2 *f32, pair16 *q16, float2 *scales, const unsigned *maxbits, int N, int H,
-                            int pitch, int storage, cudaStream_t st) {
-    long long plane = (long long)H * pitch;
-    long long n2 = plane / 2;
+cudaError_t launch_quantize(const float2 *f32, pair16 *q16, float2 *scales, const unsigned *maxbits, int N,
+                            long long plane_elems, int storage, cudaStream_t st) {
+    long long n2 = plane_elems / 2;
     int blocks = (int)((n2 + 255) / 256);
-    if (blocks > 4096) blocks = 4096;
+    if (blocks > 2048) blocks = 2048;
     dim3 grid(blocks, N);
     if (storage == KB_BF16)
-        quantize_kernel<KB_BF16><<<grid, 256, 0, st>>>(f32, q16, scales, maxbits, plane);
+        quantize_kernel<KB_BF16><<<grid, 256, 0, st>>>(f32, q16, scales, maxbits, N, plane_elems);
     else
-        quantize_kernel<KB_F16><<<grid, 256, 0, st>>>(f32, q16, scales, maxbits, plane);
+        quantize_kernel<KB_F16><<<grid, 256, 0, st>>>(f32, q16, scales, maxbits, N, plane_elems);
     return cudaGetLastError();
 }
 

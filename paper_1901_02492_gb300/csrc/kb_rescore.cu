@@ -1,12 +1,15 @@
-// FP64 rescoring of kept candidates and expansion of results into kb_result.
+// FP64 rescoring of kept candidates, repair of uncertified pixels, and
+// expansion of results into kb_result.
 //
 // Rescoring: the reduced-precision search keeps kc >= k candidates per start
 // pixel.  For each candidate the coadd of Sec. 2.1.5 is recomputed from the
 // FP32 psi/phi planes with FP64 accumulation (epochs in time order), scored
 // nu = Psi / sqrt(Phi), alpha = Psi / Phi in FP64, and the k best by
-// (nu desc, vidx asc) are kept.  One thread per start pixel; the candidates'
-// FP32 plane reads are gathers (k_c * N per pixel).
+// (nu desc, vidx asc) are kept.  A per-pixel certificate decides whether a
+// trajectory outside the candidate list could still belong to the top-k; the
+// pixels it cannot clear are searched again exhaustively in FP64.
 #include <cuda_runtime.h>
+#include <limits.h>
 #include <math.h>
 
 #include "kb_internal.h"
@@ -15,6 +18,36 @@ namespace kb {
 
 namespace {
 
+__device__ __forceinline__ void traj64(const RescoreArgs &a, int x, int y, int v, double &P, double &F, int &nobs) {
+    const int2 *ov = a.offs + (long long)v * a.N;
+    P = 0.0;
+    F = 0.0;
+    nobs = 0;
+    for (int j = 0; j < a.N; ++j) {
+        const int2 o = __ldg(ov + j);
+        const int xx = x + o.x, yy = y + o.y;
+        if ((unsigned)xx < (unsigned)a.W && (unsigned)yy < (unsigned)a.H) {
+            const float2 pp = __ldg(a.f32 + (long long)a.epoch_of[j] * a.plane_elems + a.origin +
+                                    (long long)yy * a.pitch + xx);
+            P += (double)pp.x;
+            F += (double)pp.y;
+            ++nobs;
+        }
+    }
+}
+
+// (nu desc, vidx asc)
+__device__ __forceinline__ bool better64(double an, int av, double bn, int bv) {
+    return an > bn || (an == bn && av < bv);
+}
+
+// One thread per start pixel: FP64 sums of the kc candidates, re-ranking, and the
+// certificate.  A trajectory outside the candidate list had a 16-bit score at
+// most nu16 of the last candidate; the pixel is certified when the k-th
+// rescored nu (or nu_min, if fewer than k pass it) exceeds that score by more
+// than twice the largest 16-bit error seen among the pixel's own candidates
+// plus unit * (1 + |nu|).  Pixels whose candidate list was not full hold every
+// valid trajectory and are certified.  The others go to the repair list.
 __global__ void rescore_kernel(RescoreArgs a) {
     const long long npix = (long long)a.H * a.W;
     for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix;
@@ -22,30 +55,24 @@ __global__ void rescore_kernel(RescoreArgs a) {
         const int y = (int)(pix / a.W), x = (int)(pix - (long long)y * a.W);
         double ln[32], lp[32], lf[32];
         int lv[32], lo[32];
-        int n = 0;
+        int n = 0, ncand = 0;
+        double emax = 0.0;
+        float nu16_last = -INFINITY;
         const Rec *cand = a.cand + pix * a.kc;
         for (int c = 0; c < a.kc; ++c) {
-            uint32_t v = cand[c].meta & 0xffffu;
+            const uint32_t v = cand[c].meta & 0xffffu;
             if (v == kEmptyVidx) break;
-            const int2 *ov = a.offs + (long long)v * a.N;
-            double P = 0.0, F = 0.0;
-            int nobs = 0;
-            for (int j = 0; j < a.N; ++j) {
-                int2 o = __ldg(ov + j);
-                int xx = x + o.x, yy = y + o.y;
-                if ((unsigned)xx < (unsigned)a.W && (unsigned)yy < (unsigned)a.H) {
-                    float2 pp = __ldg(a.f32 + (long long)a.epoch_of[j] * a.plane_elems + (long long)yy * a.pitch + xx);
-                    P += (double)pp.x;
-                    F += (double)pp.y;
-                    ++nobs;
-                }
-            }
+            ++ncand;
+            nu16_last = cand[c].nu;
+            double P, F;
+            int nobs;
+            traj64(a, x, y, (int)v, P, F, nobs);
             if (!(F > 0.0)) continue;
-            double nu = P / sqrt(F);
+            const double nu = P / sqrt(F);
+            emax = fmax(emax, fabs(nu - (double)cand[c].nu));
             if (!(nu >= a.nu_min)) continue;
-            // insertion by (nu desc, vidx asc)
             int i = n;
-            while (i > 0 && (nu > ln[i - 1] || (nu == ln[i - 1] && (int)v < lv[i - 1]))) {
+            while (i > 0 && better64(nu, (int)v, ln[i - 1], lv[i - 1])) {
                 ln[i] = ln[i - 1];
                 lp[i] = lp[i - 1];
                 lf[i] = lf[i - 1];
@@ -77,6 +104,92 @@ __global__ void rescore_kernel(RescoreArgs a) {
                 r.nobs = 0;
             }
             out[i] = r;
+        }
+        if (ncand == a.kc && a.ucount) {
+            const double bar = (n >= a.k) ? ln[a.k - 1] : a.nu_min;
+            const double margin = 2.0 * emax + a.unit * (1.0 + fabs((double)nu16_last));
+            if (!((double)nu16_last + margin < bar)) {
+                const int slot = atomicAdd(a.ucount, 1);
+                a.ulist[slot] = (int)pix;
+            }
+        }
+    }
+}
+
+// One warp per uncertain pixel: every velocity's sums in FP64 from the FP32
+// planes (lanes take velocities lane, lane + 32, ...), a sorted top-k per lane,
+// then k rounds of a warp-shuffle arg-max merge (nu desc, vidx asc).
+__global__ void repair_kernel(RescoreArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int count = *a.ucount;
+    for (int u = gw; u < count; u += nw) {
+        const int pix = a.ulist[u];
+        const int y = pix / a.W, x = pix - y * a.W;
+        double ln[KB_MAX_TOPK], lp[KB_MAX_TOPK], lf[KB_MAX_TOPK];
+        int lv[KB_MAX_TOPK], lo[KB_MAX_TOPK];
+        int n = 0;
+        for (int v = lane; v < a.V; v += 32) {
+            double P, F;
+            int nobs;
+            traj64(a, x, y, v, P, F, nobs);
+            if (!(F > 0.0)) continue;
+            const double nu = P / sqrt(F);
+            if (!(nu >= a.nu_min)) continue;
+            if (n == a.k && !better64(nu, v, ln[n - 1], lv[n - 1])) continue;
+            int i = (n < a.k) ? n++ : a.k - 1;
+            while (i > 0 && better64(nu, v, ln[i - 1], lv[i - 1])) {
+                ln[i] = ln[i - 1];
+                lp[i] = lp[i - 1];
+                lf[i] = lf[i - 1];
+                lv[i] = lv[i - 1];
+                lo[i] = lo[i - 1];
+                --i;
+            }
+            ln[i] = nu;
+            lp[i] = P;
+            lf[i] = F;
+            lv[i] = v;
+            lo[i] = nobs;
+        }
+        // merge: each round the best head among the lanes is emitted and popped
+        int head = 0;
+        Rec64 *out = a.out + (long long)pix * a.k;
+        for (int r = 0; r < a.k; ++r) {
+            double bn = head < n ? ln[head] : -INFINITY;
+            int bv = head < n ? lv[head] : INT_MAX;
+            int bl = lane;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double on = __shfl_xor_sync(0xffffffffu, bn, o);
+                const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+                if (better64(on, ov, bn, bv)) {
+                    bn = on;
+                    bv = ov;
+                    bl = ol;
+                }
+            }
+            const bool mine = (bl == lane) && bv != INT_MAX;
+            if (mine) {
+                Rec64 q;
+                q.psi = lp[head];
+                q.phi = lf[head];
+                q.nu = ln[head];
+                q.vidx = (uint32_t)lv[head];
+                q.nobs = (uint32_t)lo[head];
+                out[r] = q;
+                ++head;
+            } else if (lane == 0 && bv == INT_MAX) {
+                Rec64 q;
+                q.psi = 0.0;
+                q.phi = 0.0;
+                q.nu = -INFINITY;
+                q.vidx = kEmptyVidx;
+                q.nobs = 0;
+                out[r] = q;
+            }
+            __syncwarp();
         }
     }
 }
@@ -130,6 +243,11 @@ cudaError_t launch_rescore(const RescoreArgs &a, cudaStream_t st) {
     long long blocks = (npix + 127) / 128;
     if (blocks > 152 * 64) blocks = 152 * 64;
     rescore_kernel<<<(int)blocks, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_repair(const RescoreArgs &a, cudaStream_t st) {
+    repair_kernel<<<152 * 8, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

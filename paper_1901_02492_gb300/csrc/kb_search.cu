@@ -6,258 +6,232 @@
 // k best (nu desc, vidx asc) valid trajectories per start pixel.
 //
 // Work decomposition (GB300-first, not the paper's 32x16 thread blocks):
-//   - a warp owns a row segment of 32*P start pixels (lane + 32 p) and runs the
-//     whole velocity loop for them, so each pixel's top-k list stays in that
-//     lane's registers and no cross-thread merge is needed;
-//   - for one (velocity, epoch) the warp's P loads cover 32*P consecutive pixels
-//     of one row of psi/phi: fully coalesced, no shared-memory staging needed
-//     (there is no reuse across start pixels within one velocity);
-//   - the velocity table (int16 dx, dy per epoch) is staged in shared memory in
-//     chunks and read as warp-uniform broadcasts;
+//   - a CTA owns 8 rows x SPAN columns of start pixels, one warp per row; a lane
+//     owns P loads' worth of pixels (FP32: pixel lane + 32 p; 16-bit: the pixel
+//     pair 2 lane + 64 p, + 1) and runs the whole velocity loop for them, so the
+//     per-pixel top-k is private to a lane (threshold in registers, list of
+//     (nu, 16-bit velocity index) in shared memory) and no cross-thread merge is
+//     needed.  Shared memory per CTA is kept small because the kernel is
+//     latency-bound: resident warps per SM set its throughput;
+//   - for one (velocity, epoch) a warp's loads cover SPAN consecutive pixels of
+//     one plane row: fully coalesced 8-byte loads.  16-bit pairs are 8-byte
+//     aligned because the planes also exist shifted by one pixel (the "phase 1"
+//     copy) and odd shifts read that copy;
+//   - the (velocity, epoch) table is staged per CTA in shared memory and checked
+//     there once: each entry holds the element offset of the shifted row start
+//     (epoch plane and phase included), a mask of the CTA's warps whose shifted
+//     span overlaps the image, and the epoch's power-of-two scale exponents.
+//     The inner loop is one broadcast load, one bit test, a select, the
+//     gathers and one packed f32x2 accumulate per pixel;
+//   - spans that overlap the image only partly read the zero columns the planes
+//     carry left and right of every row (kSpan wide); spans that miss it read a
+//     small zero block that stays in L1, so off-image steps cost no memory
+//     traffic and "outside contributes nothing" holds exactly;
 //   - epochs at t = t_min have offset 0 for every velocity: their contribution is
 //     loaded once per pixel before the velocity loop;
-//   - loads are issued four epochs at a time; when the whole 32*P span of every
-//     epoch in the group lies inside the image (the common case) the group takes
-//     an unpredicated path, otherwise per-lane predicates give exactly the
-//     "outside contributes nothing" rule;
-//   - (psi, phi) pairs are accumulated with packed add/fma.rn.f32x2; 16-bit
-//     storage is unpacked and scaled by the epoch's power-of-two scales.
+//   - velocities are processed in the order the host planner gives (sorted by
+//     their latest-epoch offset, for L2 locality of the resident CTAs); ties in
+//     nu are broken by the caller's velocity index, so the order changes no
+//     result.
 // The Psi/Phi of each kept trajectory are recomputed at the end by the same
 // sequence of operations (bit-identical) together with nobs.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <math.h>
 
-#include "kb_internal.h"
+#include "kb_device.cuh"
 
 namespace kb {
 
 namespace {
 
+using namespace dev;
+
 constexpr int WARPS = 8;
 constexpr int THREADS = WARPS * 32;
-constexpr int OFF_WORDS = 2048;   // packed offsets (8 KB) per velocity chunk
+constexpr int TAB = 512;    // (velocity, epoch) entries staged per chunk (small: occupancy)
+constexpr uint16_t kNoV = 0xFFFF;   // empty list slot (velocity indices are < 65535)
 
-__device__ __forceinline__ unsigned long long as_u64(float2 v) {
-    return *reinterpret_cast<unsigned long long *>(&v);
-}
-__device__ __forceinline__ float2 as_f2(unsigned long long u) { return *reinterpret_cast<float2 *>(&u); }
+// zero block read by spans that miss the image (static device memory is zero-initialised)
+__device__ __align__(16) float2 g_zero_block[4 * 32];
 
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-    unsigned long long d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)));
-    return as_f2(d);
+__device__ __forceinline__ float2 exp_scale(int e) {
+    return make_float2(__int_as_float((e & 0xff) << 23), __int_as_float(((e >> 8) & 0xff) << 23));
 }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(as_u64(a)), "l"(as_u64(b)), "l"(as_u64(c)));
-    return as_f2(d);
+__device__ __forceinline__ int scale_exp(float2 s) {
+    return (int)((__float_as_uint(s.x) >> 23) & 0xff) | (int)(((__float_as_uint(s.y) >> 23) & 0xff) << 8);
 }
 
-// storage traits: element type, load, accumulate
+// per-load traits: FP32 loads one pixel's (psi, phi), 16-bit loads two adjacent pixels' codes
 template <int STORAGE>
-struct Store;
-
+struct Gather;
 template <>
-struct Store<KB_F32> {
-    typedef float2 T;
-    __device__ __forceinline__ static T load(const T *p) { return __ldg(p); }
-    __device__ __forceinline__ static T zero() { return make_float2(0.0f, 0.0f); }
-    __device__ __forceinline__ static float2 acc(float2 a, T v, float2) { return add2(a, v); }
+struct Gather<KB_F32> {
+    typedef float2 LT;
+    static constexpr int PIX = 1;
+    __device__ __forceinline__ static void acc(float2 *a, LT v, float2) { a[0] = add2(a[0], v); }
 };
-
+template <int STORAGE>
+struct Gather16 {
+    typedef uint2 LT;
+    static constexpr int PIX = 2;
+    __device__ __forceinline__ static void acc(float2 *a, LT v, float2 s) {
+        a[0] = Store<STORAGE>::acc(a[0], v.x, s);
+        a[1] = Store<STORAGE>::acc(a[1], v.y, s);
+    }
+};
 template <>
-struct Store<KB_BF16> {
-    typedef pair16 T;
-    __device__ __forceinline__ static T load(const T *p) { return __ldg(p); }
-    __device__ __forceinline__ static T zero() { return 0u; }
-    __device__ __forceinline__ static float2 acc(float2 a, T v, float2 s) {
-        float2 f = make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
-        return fma2(f, s, a);
-    }
-};
-
+struct Gather<KB_BF16> : Gather16<KB_BF16> {};
 template <>
-struct Store<KB_F16> {
-    typedef pair16 T;
-    __device__ __forceinline__ static T load(const T *p) { return __ldg(p); }
-    __device__ __forceinline__ static T zero() { return 0u; }
-    __device__ __forceinline__ static float2 acc(float2 a, T v, float2 s) {
-        __half2 h = *reinterpret_cast<__half2 *>(&v);
-        return fma2(__half22float2(h), s, a);
-    }
+struct Gather<KB_F16> : Gather16<KB_F16> {};
+
+// staged table entry: element offset (32 or 64 bit) and (warp mask | scale exponents << 16)
+template <typename I>
+struct Entry {
+    I idx;
+    int info;
 };
 
-__device__ __forceinline__ int off_dx(uint32_t po) { return ((int)(po << 16)) >> 16; }
-__device__ __forceinline__ int off_dy(uint32_t po) { return ((int)po) >> 16; }
-
-// (nu desc, vidx asc)
-__device__ __forceinline__ bool better(float an, int av, float bn, int bv) {
-    return an > bn || (an == bn && av < bv);
-}
-
-template <int STORAGE, int P>
-struct Ctx {
-    typedef typename Store<STORAGE>::T T;
-    const T *const *base;   // shared: plane base per time-ordered epoch
-    const float2 *scale;    // shared: scale per time-ordered epoch
-    int H, W, pitch, y, xw, lane;
-};
-
-// Loads of C consecutive time-ordered epochs (j0 .. j0+C-1) for one velocity.
-template <int STORAGE, int P, int C>
-__device__ __forceinline__ void gather_group(const Ctx<STORAGE, P> &c, const uint32_t *op, int j0, float2 (&acc)[P]) {
-    typedef Store<STORAGE> S;
-    typedef typename S::T T;
-    int dx[C], dy[C];
-    bool full = true;
-#pragma unroll
-    for (int q = 0; q < C; ++q) {
-        uint32_t po = op[q];
-        dx[q] = off_dx(po);
-        dy[q] = off_dy(po);
-        int ys = c.y + dy[q], xs = c.xw + dx[q];
-        full &= ((unsigned)ys < (unsigned)c.H) && (xs >= 0) && (xs + 32 * P <= c.W);
-    }
-    T v[C][P];
-    if (full) {   // warp-uniform
-#pragma unroll
-        for (int q = 0; q < C; ++q) {
-            const T *row = c.base[j0 + q] + (long long)(c.y + dy[q]) * c.pitch + (c.xw + dx[q] + c.lane);
-#pragma unroll
-            for (int p = 0; p < P; ++p) v[q][p] = S::load(row + 32 * p);
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < C; ++q) {
-            int ys = c.y + dy[q];
-            bool rok = (unsigned)ys < (unsigned)c.H;
-            const T *row = c.base[j0 + q] + (long long)(rok ? ys : 0) * c.pitch;
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                int xx = c.xw + c.lane + 32 * p + dx[q];
-                v[q][p] = S::zero();
-                if (rok && (unsigned)xx < (unsigned)c.W) v[q][p] = S::load(row + xx);
-            }
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < C; ++q) {
-        float2 s = c.scale[j0 + q];
-#pragma unroll
-        for (int p = 0; p < P; ++p) acc[p] = S::acc(acc[p], v[q][p], s);
-    }
-}
-
-template <int STORAGE, int P>
+template <int STORAGE, int P, int C, typename I>
 __global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
-    typedef Store<STORAGE> S;
-    typedef typename S::T T;
-    __shared__ const T *s_base[KB_MAX_EPOCHS];
-    __shared__ float2 s_scale[KB_MAX_EPOCHS];
-    // dynamic: packed offsets [OFF_WORDS] | velocity ids [OFF_WORDS] | lists nu [k][THREADS*P], vid [k][THREADS*P]
-    extern __shared__ uint32_t s_dyn[];
-    uint32_t *s_off = s_dyn;
-    int *s_vid = reinterpret_cast<int *>(s_dyn + OFF_WORDS);
-    float *s_ln = reinterpret_cast<float *>(s_dyn + 2 * OFF_WORDS);
-    int *s_lv = reinterpret_cast<int *>(s_ln + a.k * THREADS * P);
-    constexpr int LS = THREADS * P;   // list stride
+    typedef Store<STORAGE> St;
+    typedef typename St::T T;         // one pixel's (psi, phi)
+    typedef Gather<STORAGE> G;
+    typedef typename G::LT LT;        // one load
+    typedef Entry<I> E;
+    constexpr int PX = P * G::PIX;    // pixels per lane
+    constexpr int SPAN = 32 * PX;     // pixels per warp row segment
+    constexpr int LS = THREADS * PX;  // list stride
+
+    __shared__ float2 s_scale[KB_MAX_EPOCHS];   // per time-ordered epoch
+    // dynamic: table E [TAB] | velocity ids [TAB] | list nu float [k][LS] | list vidx u16 [k][LS]
+    extern __shared__ int4 s_dyn4[];
+    E *s_tab = reinterpret_cast<E *>(s_dyn4);
+    int *s_vid = reinterpret_cast<int *>(s_tab + TAB);
+    float *s_ln = reinterpret_cast<float *>(s_vid + TAB);
+    uint16_t *s_lv = reinterpret_cast<uint16_t *>(s_ln + a.k * LS);
 
     const int N = a.N, n0 = a.n0, NJ = N - n0, k = a.k;
-    for (int j = threadIdx.x; j < N; j += THREADS) {
-        int e = a.epoch_of[j];
-        s_base[j] = reinterpret_cast<const T *>(a.planes) + (long long)e * a.plane_elems;
-        s_scale[j] = (STORAGE == KB_F32) ? make_float2(1.0f, 1.0f) : a.scales[e];
-    }
+    for (int j = threadIdx.x; j < N; j += THREADS)
+        s_scale[j] = (STORAGE == KB_F32) ? make_float2(1.0f, 1.0f) : exp_scale(scale_exp(a.scales[a.epoch_of[j]]));
     for (int i = threadIdx.x; i < k * LS; i += THREADS) {
         s_ln[i] = -INFINITY;
-        s_lv[i] = INT_MAX;
+        s_lv[i] = kNoV;
     }
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int y = blockIdx.y * WARPS + warp;
-    const int xw = blockIdx.x * (32 * P);
+    const int y0 = blockIdx.y * WARPS;
+    const int y = y0 + warp;
+    const int xw = blockIdx.x * SPAN;
     const bool active = y < a.H;
+    const T *planes = reinterpret_cast<const T *>(a.planes);
+    // element index of this lane's first pixel within a plane (even for 16-bit storage)
+    const I tb = (I)(a.origin + (long long)y * a.pitch + xw + lane * G::PIX);
+    const LT *zero = reinterpret_cast<const LT *>(g_zero_block) + lane;
 
-    Ctx<STORAGE, P> c;
-    c.base = s_base;
-    c.scale = s_scale;
-    c.H = a.H;
-    c.W = a.W;
-    c.pitch = a.pitch;
-    c.y = y;
-    c.xw = xw;
-    c.lane = lane;
-
-    // the k-th entry of each list (admission threshold) lives in registers
-    float thn[P];
-    int thv[P];
+    float thn[PX];
+    int thv[PX];
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
+    for (int p = 0; p < PX; ++p) {
         thn[p] = -INFINITY;
-        thv[p] = INT_MAX;
+        thv[p] = kNoV;
     }
-
     __syncthreads();
-    // epochs at the reference time: offset 0 for every velocity
-    float2 acc0[P];
+
+    // epochs at the reference time: offset 0 for every velocity (pixels past W read the zero columns)
+    float2 acc0[PX];
 #pragma unroll
-    for (int p = 0; p < P; ++p) acc0[p] = make_float2(0.0f, 0.0f);
+    for (int p = 0; p < PX; ++p) acc0[p] = make_float2(0.0f, 0.0f);
     if (active) {
         for (int j = 0; j < n0; ++j) {
+            const LT *src = reinterpret_cast<const LT *>(planes + (long long)a.epoch_of[j] * a.plane_elems + tb);
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                int x = xw + lane + 32 * p;
-                if (x < a.W) acc0[p] = S::acc(acc0[p], S::load(s_base[j] + (long long)y * a.pitch + x), s_scale[j]);
-            }
+            for (int p = 0; p < P; ++p) G::acc(acc0 + p * G::PIX, __ldg(src + 32 * p), s_scale[j]);
         }
     }
 
-    const int vchunk = min(a.V, OFF_WORDS / max(NJ, 1));
+    const int vchunk = min(a.V, TAB / max(NJ, 1));
     for (int c0 = 0; c0 < a.V; c0 += vchunk) {
         const int nc = min(vchunk, a.V - c0);
         __syncthreads();
         for (int i = threadIdx.x; i < nc; i += THREADS) s_vid[i] = a.vorder[c0 + i];
         for (int i = threadIdx.x; i < nc * NJ; i += THREADS) {
-            int vi = i / NJ, jj = i - vi * NJ;
-            int2 o = a.offs[(long long)a.vorder[c0 + vi] * N + n0 + jj];
-            int ox = max(-32767, min(32767, o.x)), oy = max(-32767, min(32767, o.y));
-            s_off[i] = ((uint32_t)oy << 16) | ((uint32_t)ox & 0xffffu);
+            const int vi = i / NJ, jj = i - vi * NJ;
+            const int j = n0 + jj;
+            const int ep = a.epoch_of[j];
+            const int2 o = a.offs[(long long)a.vorder[c0 + vi] * N + j];
+            const int ox = max(-32767, min(32767, o.x)), oy = max(-32767, min(32767, o.y));
+            int mask = 0;
+            if (xw + ox + SPAN > 0 && xw + ox < a.W) {   // the span overlaps the image's columns
+#pragma unroll
+                for (int w = 0; w < WARPS; ++w)
+                    if ((unsigned)(y0 + w + oy) < (unsigned)a.H) mask |= 1 << w;
+            }
+            long long g = (long long)ep * a.plane_elems + (long long)oy * a.pitch + ox;
+            if (STORAGE != KB_F32 && (ox & 1)) g += a.phase1 - 1;   // odd shift: the phase-1 copy
+            E e;
+            e.idx = (I)g;
+            e.info = mask | ((STORAGE == KB_F32 ? 0 : scale_exp(a.scales[ep])) << 16);
+            s_tab[i] = e;
         }
         __syncthreads();
         if (!active) continue;
         for (int vi = 0; vi < nc; ++vi) {
             const int v = s_vid[vi];
-            const uint32_t *op = s_off + vi * NJ;
-            float2 acc[P];
+            const E *tab = s_tab + vi * NJ;
+            float2 acc[PX];
 #pragma unroll
-            for (int p = 0; p < P; ++p) acc[p] = acc0[p];
+            for (int p = 0; p < PX; ++p) acc[p] = acc0[p];
             int jj = 0;
-            for (; jj + 4 <= NJ; jj += 4) gather_group<STORAGE, P, 4>(c, op + jj, n0 + jj, acc);
-            for (; jj < NJ; ++jj) gather_group<STORAGE, P, 1>(c, op + jj, n0 + jj, acc);
+            for (; jj + C <= NJ; jj += C) {
+                LT val[C][P];
+                int sx[C];
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                float F = acc[p].y;
+                for (int q = 0; q < C; ++q) {
+                    const E t = tab[jj + q];
+                    sx[q] = t.info >> 16;
+                    const LT *src = ((t.info >> warp) & 1) ? reinterpret_cast<const LT *>(planes + (t.idx + tb)) : zero;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) val[q][p] = __ldg(src + 32 * p);
+                }
+#pragma unroll
+                for (int q = 0; q < C; ++q) {
+                    const float2 sc = exp_scale(sx[q]);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[q][p], sc);
+                }
+            }
+            for (; jj < NJ; ++jj) {
+                const E t = tab[jj];
+                const LT *src = ((t.info >> warp) & 1) ? reinterpret_cast<const LT *>(planes + (t.idx + tb)) : zero;
+                LT val[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) val[p] = __ldg(src + 32 * p);
+                const float2 sc = exp_scale(t.info >> 16);
+#pragma unroll
+                for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[p], sc);
+            }
+#pragma unroll
+            for (int p = 0; p < PX; ++p) {
+                const float F = acc[p].y;
                 if (!(F > 0.0f)) continue;
-                float nu = acc[p].x * rsqrtf(F);
+                const float nu = acc[p].x * rsqrtf(F);
                 if (!(nu >= a.nu_min)) continue;
                 if (!better(nu, v, thn[p], thv[p])) continue;
                 // insertion into this lane's sorted list (rare after the first velocities)
                 float *ln = s_ln + p * THREADS + threadIdx.x;
-                int *lv = s_lv + p * THREADS + threadIdx.x;
+                uint16_t *lv = s_lv + p * THREADS + threadIdx.x;
                 int i = k - 1;
                 while (i > 0) {
-                    float pn = ln[(i - 1) * LS];
-                    int pv = lv[(i - 1) * LS];
+                    const float pn = ln[(i - 1) * LS];
+                    const int pv = lv[(i - 1) * LS];
                     if (!better(nu, v, pn, pv)) break;
                     ln[i * LS] = pn;
-                    lv[i * LS] = pv;
+                    lv[i * LS] = (uint16_t)pv;
                     --i;
                 }
                 ln[i * LS] = nu;
-                lv[i * LS] = v;
+                lv[i * LS] = (uint16_t)v;
                 thn[p] = ln[(k - 1) * LS];
                 thv[p] = lv[(k - 1) * LS];
             }
@@ -265,18 +239,19 @@ __global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
     }
     if (!active) return;
 
-    // epilogue: recompute Psi, Phi (same operation sequence) and nobs of the kept entries
+    // epilogue: recompute Psi, Phi (same operation sequence) and nobs of the kept entries;
+    // every off-image epoch added a zero in the main loop, so it adds a zero here too
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const int x = xw + lane + 32 * p;
+    for (int p = 0; p < PX; ++p) {
+        const int x = xw + (G::PIX == 1 ? lane + 32 * p : 2 * lane + 64 * (p / 2) + (p & 1));
         if (x >= a.W) continue;
         Rec *out = a.out + ((long long)y * a.W + x) * k;
         const float *ln = s_ln + p * THREADS + threadIdx.x;
-        const int *lv = s_lv + p * THREADS + threadIdx.x;
+        const uint16_t *lv = s_lv + p * THREADS + threadIdx.x;
         for (int i = 0; i < k; ++i) {
             Rec r;
             const int v = lv[i * LS];
-            if (v == INT_MAX) {
+            if (v == kNoV) {
                 r.psi = 0.0f;
                 r.phi = 0.0f;
                 r.nu = -INFINITY;
@@ -286,12 +261,15 @@ __global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
                 float2 acc = acc0[p];
                 int nobs = n0;
                 for (int j = n0; j < N; ++j) {
-                    int2 o = __ldg(ov + j);
-                    int xx = x + o.x, yy = y + o.y;
+                    const int2 o = __ldg(ov + j);
+                    const int xx = x + o.x, yy = y + o.y;
+                    T val = St::zero();
                     if ((unsigned)xx < (unsigned)a.W && (unsigned)yy < (unsigned)a.H) {
-                        acc = S::acc(acc, S::load(s_base[j] + (long long)yy * a.pitch + xx), s_scale[j]);
+                        val = St::load(planes + (long long)a.epoch_of[j] * a.plane_elems + a.origin +
+                                       (long long)yy * a.pitch + xx);
                         ++nobs;
                     }
+                    acc = St::acc(acc, val, s_scale[j]);
                 }
                 r.psi = acc.x;
                 r.phi = acc.y;
@@ -303,21 +281,46 @@ __global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
     }
 }
 
-template <int STORAGE, int P>
+template <int STORAGE, int P, int C, typename I>
 cudaError_t launch_one(const SearchArgs &a, cudaStream_t st) {
-    dim3 grid((a.W + 32 * P - 1) / (32 * P), (a.H + WARPS - 1) / WARPS);
-    size_t smem = (size_t)2 * OFF_WORDS * 4 + (size_t)2 * a.k * THREADS * P * 4;
-    cudaError_t err = cudaFuncSetAttribute(search_kernel<STORAGE, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    constexpr int SPAN = 32 * P * Gather<STORAGE>::PIX;
+    static_assert(SPAN <= kSpan, "warp span wider than the zero columns");
+    dim3 grid((a.W + SPAN - 1) / SPAN, (a.H + WARPS - 1) / WARPS);
+    size_t smem = (size_t)TAB * (sizeof(Entry<I>) + sizeof(int)) +
+                  (size_t)a.k * THREADS * P * Gather<STORAGE>::PIX * (sizeof(float) + sizeof(uint16_t));
+    cudaError_t err = cudaFuncSetAttribute(search_kernel<STORAGE, P, C, I>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    search_kernel<STORAGE, P><<<grid, THREADS, smem, st>>>(a);
+    search_kernel<STORAGE, P, C, I><<<grid, THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+template <int STORAGE, int P, int C>
+cudaError_t launch_idx(const SearchArgs &a, cudaStream_t st) {
+    // 32-bit element offsets when every plane of both phases fits
+    const long long span = (STORAGE == KB_F32 ? 1LL : 2LL) * a.N * a.plane_elems;
+    if (span < (1LL << 31) - 1) return launch_one<STORAGE, P, C, int>(a, st);
+    return launch_one<STORAGE, P, C, long long>(a, st);
+}
+
+// Shapes: (loads per lane P, epochs per load batch C); a 16-bit load is two pixels.
 template <int STORAGE>
 cudaError_t launch_storage(const SearchArgs &a, cudaStream_t st) {
-    if (a.k <= 8) return launch_one<STORAGE, 4>(a, st);
-    return launch_one<STORAGE, 2>(a, st);
+    if constexpr (STORAGE == KB_F32) {
+        switch (a.variant) {
+            case 1: return launch_idx<STORAGE, 4, 4>(a, st);
+            case 2: return launch_idx<STORAGE, 2, 4>(a, st);
+            case 3: return launch_idx<STORAGE, 4, 8>(a, st);
+            default: return launch_idx<STORAGE, 2, 8>(a, st);
+        }
+    } else {
+        switch (a.variant) {
+            case 1: return launch_idx<STORAGE, 2, 4>(a, st);
+            case 2: return launch_idx<STORAGE, 1, 4>(a, st);
+            case 3: return launch_idx<STORAGE, 2, 8>(a, st);
+            default: return launch_idx<STORAGE, 1, 8>(a, st);
+        }
+    }
 }
 
 }  // namespace

@@ -39,6 +39,7 @@ def gpu_planes(kb, ctx, st, storage="f32", bright=math.inf, mask=True):
 
 def gpu_search(kb, ctx, st, storage="f32", k=None, nu_min=-math.inf, flags=0, times=None, vx=None, vy=None,
                bright=math.inf):
+    """Search through the C ABI and return the kb_result records [H][W][k]."""
     N, H, W = st.sci.shape
     k = st.k if k is None else k
     times = st.times if times is None else times
@@ -255,3 +256,21 @@ def test_decam_full_size_sampled(kb, ctx, decam_stack):
         return P / math.sqrt(F) if F > 0 else -math.inf
     check_topk(g, ref, nu_of)
     assert np.all(g["x0"] == px[:, None]) and np.all(g["y0"] == py[:, None])
+
+
+@pytest.mark.parametrize("variant", range(0, 9))
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+def test_every_kernel_variant(kb, ctx, variant, storage):
+    """Every search kernel (register gather 0-4, TMA pipeline 5-8) in every shape gives the oracle's
+    results: ragged tile edges, masked pixels, trajectories leaving the image, odd and even shifts
+    of the 16-bit pixel pairs."""
+    st = synth.small_stack(40 + variant, 6, 45, 203, K=5, nan_frac=0.01, mask_frac=0.01, n_angles=6,
+                           n_speeds=6, s_lo=5.0, s_hi=40.0, n_sources=2, flux=60.0)
+    ctx.set_search_variant(variant)
+    try:
+        flags = kb.KB_RESCORE_FP64 if storage != "f32" else 0
+        res = gpu_search(kb, ctx, st, storage, k=5, flags=flags)
+    finally:
+        ctx.set_search_variant(0)
+    ref, nu_of = oracle_search(st, k=5)
+    check_topk(res, ref, nu_of)
