@@ -136,6 +136,28 @@ void kb_stack_free(kb_stack *s);
 int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8_t *mask, const float *psf,
                     int K, float bright_max, void *stream);
 
+/* The likelihood images of kb_make_psi_phi without allocating anything.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory where they need the planes -- code whose device
+ * memory belongs to another allocator, or loops in which cudaMalloc/cudaFree
+ * are not allowed because they can block or synchronise the device.
+ *   sci, var  device, float [N][H][W]; mask device uint8 [N][H][W] or NULL
+ *   psf       HOST, float [N][K][K], as for kb_make_psi_phi
+ *   out       device, float [N][H][W][2]: (psi, phi) per pixel, caller-owned
+ * Same arithmetic and results as kb_make_psi_phi followed by
+ * kb_stack_copy_planes(which = 0).  Works on the calling thread's current
+ * device and in stream order.  The per-epoch PSF taps it needs are kept in a
+ * static device array of 256 KB (65536 floats) that every GPU loading the
+ * library holds until exit: separable PSFs need N * 4K floats, other PSFs
+ * N * 2K^2 floats, and a call that needs more returns KB_EINVAL.  The first
+ * call on a device looks up the array's device address (set-up, once per
+ * device); make that call before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU (e.g. on different streams) race and
+ * must be ordered by the caller.  Returns KB_OK, KB_EINVAL (bad sizes or
+ * pointers, or too many taps) or KB_ECUDA. */
+int kb_make_psi_phi_static(const float *sci, const float *var, const uint8_t *mask, const float *psf, int N, int H,
+                           int W, int K, float bright_max, float *out, void *stream);
+
 /* Copy the stack's planes to dst (host or device), stream-ordered.
  *   which = 0: FP32 planes, float [N][H][W][2] = (psi, phi), dst_bytes >= N*H*W*8
  *   which = 1: 16-bit planes, uint16 [N][H][W][2] = (psi, phi) codes, dst_bytes >= N*H*W*4

@@ -59,10 +59,12 @@ _kb_search = _sig("kb_search", _i32, [_P, _P, _P, _P, _P, _i32, _i32, _f32, _i32
 _kb_results = _sig("kb_results", _i32, [_P, _P, _sz, ctypes.POINTER(_sz), _P])
 _kb_job_wait = _sig("kb_job_wait", _i32, [_P])
 _kb_job_repaired = _sig("kb_job_repaired", _i32, [_P, ctypes.POINTER(_sz)])
+_kb_make_psi_phi_static = _sig("kb_make_psi_phi_static", _i32,
+                               [_P, _P, _P, _P, _i32, _i32, _i32, _i32, _f32, _P, _P])
 
 EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_search_variant", "kb_stack_create", "kb_stack_free",
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
-            "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results"]
+            "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static"]
 
 
 class KBError(RuntimeError):
@@ -169,6 +171,18 @@ class Stack:
             self.free()
         except Exception:
             pass
+
+
+def make_psi_phi_static(sci, var, mask, psf, out, bright_max=math.inf, stream=None):
+    """psi/phi planes into the caller's device buffer `out` (float32 [N][H][W][2]) without any
+    allocation: the PSF taps go to the library's static device scratch (see include/kb.h)."""
+    psf = np.ascontiguousarray(psf, dtype=np.float32)
+    N, K = psf.shape[0], psf.shape[-1]
+    H, W = sci.shape[-2], sci.shape[-1]
+    rc = _kb_make_psi_phi_static(_ptr(sci), _ptr(var), _ptr(mask), psf.ctypes.data, N, H, W, K,
+                                 float(bright_max), _ptr(out), _stream(stream))
+    if rc != KB_OK:
+        raise KBError(rc, "kb_make_psi_phi_static failed")
 
 
 def offsets(times, vx, vy):

@@ -130,6 +130,9 @@ int quant_velocity(kb_ctx *ctx, double v, int64_t *q) {
     return KB_OK;
 }
 
+}  // namespace
+
+namespace kb {
 // ---- PSF analysis ------------------------------------------------------------
 // A K x K kernel is separable when T(i, j) = a(i) b(j); the factors are read off
 // the row and column through the largest tap and checked against every tap.
@@ -154,8 +157,7 @@ bool factor_psf(const float *T, int K, std::vector<double> &a, std::vector<doubl
             if (fabs(a[i] * b[j] - (double)T[i * K + j]) > 1e-6 * best) return false;
     return true;
 }
-
-}  // namespace
+}  // namespace kb
 
 // =============================================================================
 extern "C" {
@@ -269,7 +271,7 @@ int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8
     // analyse the PSFs: separable for every epoch -> two-pass kernel
     bool sep = true;
     std::vector<std::vector<double>> fa(N), fb(N);
-    for (int e = 0; e < N && sep; ++e) sep = factor_psf(psf + (size_t)e * K * K, K, fa[e], fb[e]);
+    for (int e = 0; e < N && sep; ++e) sep = kb::factor_psf(psf + (size_t)e * K * K, K, fa[e], fb[e]);
     size_t nt = kb::taps_floats(N, K, sep);
     if (nt > s->taps_floats) {
         if (s->taps_done) cudaEventSynchronize(s->taps_done);

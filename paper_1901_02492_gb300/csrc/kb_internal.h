@@ -7,6 +7,7 @@
 
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/kb.h"
 
@@ -131,6 +132,8 @@ cudaError_t launch_quantize(const float2 *f32, pair16 *q16, float2 *scales, cons
                             long long plane_elems, int storage, cudaStream_t st);
 // layout helper: floats needed for the taps of N epochs with kernel size K
 size_t taps_floats(int N, int K, bool separable);
+// rank-1 test and factors of a K x K PSF, T(i, j) = a(i) b(j) (host)
+bool factor_psf(const float *T, int K, std::vector<double> &a, std::vector<double> &b);
 
 // ---- stage (b) ---------------------------------------------------------------
 struct SearchArgs {
