@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, help="search kernel shape (0 = automatic)")
+    ap.add_argument("--topk", type=int, default=0, help="results per pixel (0 = the workload's k)")
+    ap.add_argument("--carveout", type=int, default=-1, help="search shared-memory carveout percent (-1 = auto)")
     return ap.parse_args()
 
 
@@ -68,7 +70,7 @@ def workload_config(args, st, world):
     name = "decam %dx%dx%d, %d velocities, k=%d" % (N, H, W, st.vx.size, st.k)
     return {"workload": name, "epochs": N, "height": H, "width": W, "velocities": int(st.vx.size),
             "topk": st.k, "psf": "17x17 Gaussian, FWHM 3.5-4.5 px", "storage": args.storage,
-            "rescore_fp64": bool(args.rescore), "search_variant": args.variant,
+            "rescore_fp64": bool(args.rescore), "search_variant": args.variant, "carveout": args.carveout,
             "evals_per_step": int(N * H * W * st.vx.size),
             "l2": "inputs larger than L2 (%.2f GB of psi/phi planes)" % (N * H * W * 8 / 1e9),
             "parallelism": "replicas%d" % world}
@@ -232,11 +234,14 @@ def run_ours(args):
     st = workload(args.size)
     N, H, W = st.sci.shape
     V = st.vx.size
+    if args.topk:
+        st.k = args.topk
     k = st.k
     evals = N * H * W * V
     flags = kb.KB_RESCORE_FP64 if args.rescore else 0
     ctx = kb.Context(dev.index)
     ctx.set_search_variant(args.variant)
+    ctx.set_search_carveout(args.carveout)
     stack = kb.Stack(ctx, N, H, W, args.storage)
     job = kb.Job(ctx, H, W, N, V, k, flags)
     sci_h = torch.from_numpy(st.sci).pin_memory()
@@ -244,7 +249,7 @@ def run_ours(args):
     sci = sci_h.to(dev)
     var = var_h.to(dev)
     stream = torch.cuda.current_stream(dev)
-    launches_per_step = 2 + (1 if args.storage != "f32" else 0) + (1 if args.rescore else 0)
+    launches_per_step = 2 + (1 if args.storage != "f32" else 0) + (2 if args.rescore else 0)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
@@ -276,6 +281,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize(dev)
     ms = t0.elapsed_time(t1)
+    repaired = job.repaired() if args.rescore else 0
     ms_psiphi = sum(t[0].elapsed_time(t[1]) for t in timers) / args.steps
     ms_search = sum(t[1].elapsed_time(t[2]) for t in timers) / args.steps
     clocks = clk.summary()
@@ -333,6 +339,10 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(sci_h.numel() * 4 + var_h.numel() * 4),
                     "d2h_bytes_per_step": int(H * W * k * kb.RESULT_DTYPE.itemsize), "ms_per_step": e2e_ms},
             "gpu_launches": launches_per_step * args.steps}
+    if args.rescore:
+        line["rescore"] = {"candidates_per_pixel": k + (max(2, k // 2) if args.storage == "bf16" else max(2, k // 4)),
+                           "repaired_pixels": repaired,
+                           "repaired_fraction": repaired / float(H * W)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         e, s, p = oracle_sample(st, args.cpu_seconds, np.random.default_rng(7))

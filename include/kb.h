@@ -108,6 +108,19 @@ size_t kb_hbm_in_use(const kb_ctx *ctx);
  * KB_EINVAL for other values. */
 int kb_set_search_variant(kb_ctx *ctx, int variant);
 
+/* Tuning hook: preferred shared-memory carveout of the register-gather search
+ * kernel, in percent of the maximum (cudaFuncAttributePreferredSharedMemoryCarveout);
+ * -1 = automatic.  It trades resident CTAs against L1 capacity, which the
+ * gathers of the early epochs reuse.  Results do not depend on it. */
+int kb_set_search_carveout(kb_ctx *ctx, int percent);
+
+/* Measurement helper (no counterpart in the paper): the L2-to-SM bandwidth, in
+ * GB/s, of the search's own access form -- warp-contiguous 8-byte loads of
+ * 256-byte spans at scattered offsets of an L2-resident 64 MB buffer, from every
+ * SM, not cached in L1.  It is the denominator of the search's roofline.  Takes
+ * about 100 ms; allocates and frees 64 MB on the context's device. */
+int kb_measure_gather_peak(kb_ctx *ctx, double *gb_per_s);
+
 /* ---- stage (a): likelihood images --------------------------------------- */
 
 /* Allocate the device planes for an N x H x W stack (1 <= N <= KB_MAX_EPOCHS,

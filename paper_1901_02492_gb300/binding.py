@@ -47,6 +47,8 @@ _kb_destroy = _sig("kb_destroy", None, [_P])
 _kb_last_error = _sig("kb_last_error", ctypes.c_char_p, [_P])
 _kb_hbm_in_use = _sig("kb_hbm_in_use", _sz, [_P])
 _kb_set_search_variant = _sig("kb_set_search_variant", _i32, [_P, _i32])
+_kb_set_search_carveout = _sig("kb_set_search_carveout", _i32, [_P, _i32])
+_kb_measure_gather_peak = _sig("kb_measure_gather_peak", _i32, [_P, ctypes.POINTER(ctypes.c_double)])
 _kb_stack_create = _sig("kb_stack_create", _i32, [_P, _i32, _i32, _i32, _i32, ctypes.POINTER(_P)])
 _kb_stack_free = _sig("kb_stack_free", None, [_P])
 _kb_make_psi_phi = _sig("kb_make_psi_phi", _i32, [_P, _P, _P, _P, _P, _i32, _f32, _P])
@@ -62,7 +64,8 @@ _kb_job_repaired = _sig("kb_job_repaired", _i32, [_P, ctypes.POINTER(_sz)])
 _kb_make_psi_phi_static = _sig("kb_make_psi_phi_static", _i32,
                                [_P, _P, _P, _P, _i32, _i32, _i32, _i32, _f32, _P, _P])
 
-EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_search_variant", "kb_stack_create", "kb_stack_free",
+EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_search_variant",
+            "kb_set_search_carveout", "kb_measure_gather_peak", "kb_stack_create", "kb_stack_free",
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
             "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static"]
 
@@ -116,6 +119,15 @@ class Context:
 
     def set_search_variant(self, variant: int):
         self.check(_kb_set_search_variant(self.h, int(variant)))
+
+    def set_search_carveout(self, percent: int):
+        self.check(_kb_set_search_carveout(self.h, int(percent)))
+
+    def measure_gather_peak(self) -> float:
+        """L2-to-SM GB/s of the search's access form on this device (roofline denominator)."""
+        v = ctypes.c_double()
+        self.check(_kb_measure_gather_peak(self.h, ctypes.byref(v)))
+        return v.value
 
     @property
     def hbm_in_use(self) -> int:

@@ -192,6 +192,13 @@ const char *kb_last_error(const kb_ctx *ctx) { return ctx ? ctx->err.c_str() : "
 
 size_t kb_hbm_in_use(const kb_ctx *ctx) { return ctx ? ctx->in_use : 0; }
 
+int kb_set_search_carveout(kb_ctx *ctx, int percent) {
+    if (!ctx) return KB_EINVAL;
+    if (percent < -1 || percent > 100) return fail(ctx, KB_EINVAL, "carveout %d not in -1..100", percent);
+    ctx->search_carveout = percent;
+    return KB_OK;
+}
+
 int kb_set_search_variant(kb_ctx *ctx, int variant) {
     if (!ctx) return KB_EINVAL;
     if (variant < 0 || variant > 8) return fail(ctx, KB_EINVAL, "search variant %d not in 0..8", variant);
@@ -406,7 +413,13 @@ int kb_offsets(const double *times, int N, const double *vx, const double *vy, i
 
 // ---- jobs --------------------------------------------------------------------
 
-static int job_kkeep(int topk, int flags) { return (flags & KB_RESCORE_FP64) ? std::min(2 * topk, 32) : topk; }
+// candidates kept by a search for FP64 rescoring: k plus a margin that grows with
+// the storage's rounding (bf16 2^-8, fp16 2^-11, fp32 2^-24); the certificate sends
+// the pixels the margin does not cover to the exhaustive FP64 repair
+static int job_kkeep(int topk, int flags, int storage) {
+    if (!(flags & KB_RESCORE_FP64)) return topk;
+    return topk + (storage == KB_BF16 ? std::max(2, topk / 2) : std::max(2, topk / 4));
+}
 
 int kb_job_create(kb_ctx *ctx, int H, int W, int N, int V, int topk, int flags, kb_job **out) {
     if (!ctx || !out) return KB_EINVAL;
@@ -424,7 +437,7 @@ int kb_job_create(kb_ctx *ctx, int H, int W, int N, int V, int topk, int flags, 
     j->Vcap = V;
     j->kcap = topk;
     j->flags = flags;
-    j->kkeep_cap = job_kkeep(topk, flags);
+    j->kkeep_cap = job_kkeep(topk, flags, KB_BF16);   // the largest margin
     size_t npix = (size_t)H * W;
     int rc = dev_alloc(ctx, (size_t)V * N * sizeof(int2), (void **)&j->offs, &j->bytes);
     if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)V * sizeof(int), (void **)&j->vorder, &j->bytes);
@@ -553,7 +566,7 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_search upload");
 
     const bool rescore = (flags & KB_RESCORE_FP64) != 0;
-    const int kkeep = rescore ? job_kkeep(topk, flags) : topk;
+    const int kkeep = rescore ? job_kkeep(topk, flags, s->q16 ? s->storage : KB_F32) : topk;
     kb::SearchArgs a;
     a.storage = s->q16 ? s->storage : KB_F32;
     a.planes = s->q16 ? (const void *)s->q16 : (const void *)s->f32;
@@ -575,6 +588,7 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     a.k = kkeep;
     a.out = job->recs;
     a.variant = ctx->search_variant;
+    a.carveout = ctx->search_carveout;
     a.ptab = job->ptab;
     a.status = job->status;
     if (a.variant >= 5)

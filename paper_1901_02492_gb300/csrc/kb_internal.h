@@ -61,6 +61,7 @@ struct kb_ctx {
     int sm_count = 0;
     size_t smem_optin = 0;
     int search_variant = 0;   // 0 = automatic
+    int search_carveout = -1; // -1 = automatic
     std::string err;
     std::mutex mu;
 };
@@ -154,6 +155,7 @@ struct SearchArgs {
     int k;                   // results kept per pixel (<= 32)
     Rec *out;                // [H*W][k]
     int variant;             // kernel shape, 0 = automatic
+    int carveout;            // preferred shared-memory carveout (percent of the maximum), -1 = automatic
     const uint32_t *ptab;    // [V][N - n0] packed (dx, dy) int16 in processing order (pipelined kernel)
     int *status;             // device status word: KB_ETIMEOUT if a bounded wait gave up
 };

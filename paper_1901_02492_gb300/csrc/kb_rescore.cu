@@ -18,17 +18,42 @@ namespace kb {
 
 namespace {
 
+// FP64 coadd of one trajectory from the FP32 planes, epochs in time order.  Four
+// epochs at a time: their offsets, then their four plane gathers, then the sums,
+// so that the scattered loads overlap instead of forming one dependent chain.
 __device__ __forceinline__ void traj64(const RescoreArgs &a, int x, int y, int v, double &P, double &F, int &nobs) {
     const int2 *ov = a.offs + (long long)v * a.N;
+    const float2 *base = a.f32 + a.origin;
     P = 0.0;
     F = 0.0;
     nobs = 0;
-    for (int j = 0; j < a.N; ++j) {
+    int j = 0;
+    for (; j + 4 <= a.N; j += 4) {
+        int2 o[4];
+        float2 pp[4];
+        bool in[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = __ldg(ov + j + q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int xx = x + o[q].x, yy = y + o[q].y;
+            in[q] = (unsigned)xx < (unsigned)a.W && (unsigned)yy < (unsigned)a.H;
+            pp[q] = in[q] ? __ldg(base + (long long)a.epoch_of[j + q] * a.plane_elems + (long long)yy * a.pitch + xx)
+                          : make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (in[q]) {
+                P += (double)pp[q].x;
+                F += (double)pp[q].y;
+                ++nobs;
+            }
+    }
+    for (; j < a.N; ++j) {
         const int2 o = __ldg(ov + j);
         const int xx = x + o.x, yy = y + o.y;
         if ((unsigned)xx < (unsigned)a.W && (unsigned)yy < (unsigned)a.H) {
-            const float2 pp = __ldg(a.f32 + (long long)a.epoch_of[j] * a.plane_elems + a.origin +
-                                    (long long)yy * a.pitch + xx);
+            const float2 pp = __ldg(base + (long long)a.epoch_of[j] * a.plane_elems + (long long)yy * a.pitch + xx);
             P += (double)pp.x;
             F += (double)pp.y;
             ++nobs;
@@ -48,49 +73,67 @@ __device__ __forceinline__ bool better64(double an, int av, double bn, int bv) {
 // than twice the largest 16-bit error seen among the pixel's own candidates
 // plus unit * (1 + |nu|).  Pixels whose candidate list was not full hold every
 // valid trajectory and are certified.  The others go to the repair list.
+// The running top-K list lives in registers (K >= k, a compile-time bound).
+template <int K>
 __global__ void rescore_kernel(RescoreArgs a) {
     const long long npix = (long long)a.H * a.W;
     for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix;
          pix += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(pix / a.W), x = (int)(pix - (long long)y * a.W);
-        double ln[32], lp[32], lf[32];
-        int lv[32], lo[32];
-        int n = 0, ncand = 0;
+        double ln[K], lp[K], lf[K];
+        int lv[K], lo[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            ln[i] = -INFINITY;
+            lp[i] = 0.0;
+            lf[i] = 0.0;
+            lv[i] = INT_MAX;
+            lo[i] = 0;
+        }
+        int ncand = 0, n = 0;
         double emax = 0.0;
         float nu16_last = -INFINITY;
         const Rec *cand = a.cand + pix * a.kc;
         for (int c = 0; c < a.kc; ++c) {
-            const uint32_t v = cand[c].meta & 0xffffu;
+            const Rec rc = cand[c];
+            const uint32_t v = rc.meta & 0xffffu;
             if (v == kEmptyVidx) break;
             ++ncand;
-            nu16_last = cand[c].nu;
+            nu16_last = rc.nu;
             double P, F;
             int nobs;
             traj64(a, x, y, (int)v, P, F, nobs);
             if (!(F > 0.0)) continue;
-            const double nu = P / sqrt(F);
-            emax = fmax(emax, fabs(nu - (double)cand[c].nu));
+            double nu = P / sqrt(F);
+            emax = fmax(emax, fabs(nu - (double)rc.nu));
             if (!(nu >= a.nu_min)) continue;
-            int i = n;
-            while (i > 0 && better64(nu, (int)v, ln[i - 1], lv[i - 1])) {
-                ln[i] = ln[i - 1];
-                lp[i] = lp[i - 1];
-                lf[i] = lf[i - 1];
-                lv[i] = lv[i - 1];
-                lo[i] = lo[i - 1];
-                --i;
-            }
-            ln[i] = nu;
-            lp[i] = P;
-            lf[i] = F;
-            lv[i] = (int)v;
-            lo[i] = nobs;
             ++n;
+            // bubble the candidate down the sorted register list (nu desc, vidx asc)
+            int cv = (int)v, co = nobs;
+            double cp = P, cf = F;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const bool sw = better64(nu, cv, ln[i], lv[i]);
+                const double tn = ln[i], tp = lp[i], tf = lf[i];
+                const int tv = lv[i], to = lo[i];
+                ln[i] = sw ? nu : tn;
+                lp[i] = sw ? cp : tp;
+                lf[i] = sw ? cf : tf;
+                lv[i] = sw ? cv : tv;
+                lo[i] = sw ? co : to;
+                nu = sw ? tn : nu;
+                cp = sw ? tp : cp;
+                cf = sw ? tf : cf;
+                cv = sw ? tv : cv;
+                co = sw ? to : co;
+            }
         }
         Rec64 *out = a.out + pix * a.k;
-        for (int i = 0; i < a.k; ++i) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            if (i >= a.k) break;
             Rec64 r;
-            if (i < n) {
+            if (lv[i] != INT_MAX) {
                 r.psi = lp[i];
                 r.phi = lf[i];
                 r.nu = ln[i];
@@ -106,7 +149,10 @@ __global__ void rescore_kernel(RescoreArgs a) {
             out[i] = r;
         }
         if (ncand == a.kc && a.ucount) {
-            const double bar = (n >= a.k) ? ln[a.k - 1] : a.nu_min;
+            double bar = a.nu_min;
+#pragma unroll
+            for (int i = 0; i < K; ++i)
+                if (i == a.k - 1 && n >= a.k) bar = ln[i];
             const double margin = 2.0 * emax + a.unit * (1.0 + fabs((double)nu16_last));
             if (!((double)nu16_last + margin < bar)) {
                 const int slot = atomicAdd(a.ucount, 1);
@@ -242,7 +288,12 @@ cudaError_t launch_rescore(const RescoreArgs &a, cudaStream_t st) {
     long long npix = (long long)a.H * a.W;
     long long blocks = (npix + 127) / 128;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    rescore_kernel<<<(int)blocks, 128, 0, st>>>(a);
+    if (a.k <= 4)
+        rescore_kernel<4><<<(int)blocks, 128, 0, st>>>(a);
+    else if (a.k <= 8)
+        rescore_kernel<8><<<(int)blocks, 128, 0, st>>>(a);
+    else
+        rescore_kernel<16><<<(int)blocks, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
