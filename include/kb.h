@@ -235,6 +235,65 @@ int kb_job_repaired(kb_job *job, size_t *n_pixels);
  * the stream.  KB_ERANGE (with *n_written = H*W*topk) if capacity is too small. */
 int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream);
 
+/* ---- batched searches (no counterpart in the paper: many stacks per launch) ----
+ *
+ * A batch runs many independent Sec. 2.2 searches, of stacks with different
+ * sizes, epoch counts, velocity grids and k, as one persistent launch per group
+ * of searches with the same storage, index width and candidate-list length.  The work list holds one
+ * item per CTA tile of every search; the resident CTAs take items off it in
+ * order of per-tile cost (largest search first).  The launches, and the FP64
+ * rescoring of the searches that ask for it, are captured once into a CUDA
+ * graph that kb_batch_run replays.  Every search gives the results that
+ * kb_search gives for the same arguments. */
+typedef struct kb_batch kb_batch;
+
+/* One search of a batch: the arguments of kb_search (same meaning and limits). */
+typedef struct kb_batch_item {
+    kb_job *job;            /* distinct per item; holds the search's tables and results */
+    const kb_stack *stack;
+    const double *times;    /* host [stack N] */
+    const double *vx, *vy;  /* host [V] */
+    int V;
+    int topk;
+    float nu_min;
+    int flags;              /* KB_RESCORE_FP64 or 0 */
+} kb_batch_item;
+
+#define KB_BATCH_AUTOTUNE 1 /* time every tile shape per group, keep the fastest */
+
+/* The plan of one group (filled by kb_batch_groups). */
+typedef struct kb_batch_group {
+    int storage;            /* KB_F32 / KB_BF16 / KB_F16 */
+    int index_bits;         /* 32 or 64: width of the element offsets */
+    int variant;            /* tile shape 1..4 (see kb_set_search_variant) */
+    int kmax;               /* candidate-list length of its searches */
+    long long n_items;      /* CTA tiles in its work list */
+    double evals;           /* trajectory-epoch evaluations of its searches */
+    float tuned_ms[5];      /* autotuner time of shapes 1..4 on its sample (0: not tuned) */
+} kb_batch_group;
+
+/* Validate every item, build and upload its tables (host arrays are read before
+ * the call returns), tune (flags & KB_BATCH_AUTOTUNE; without it the context's
+ * variant 1..4 or the default shape) and capture the graph.  Blocks until the
+ * uploads and tuning runs are done.  The jobs belong to the batch until
+ * kb_batch_free: kb_search on them fails with KB_EINVAL, and they must not be
+ * freed before the batch.  The stacks' psi/phi must be complete before each
+ * kb_batch_run (the caller orders kb_make_psi_phi before it).  Errors: KB_EINVAL
+ * (an item fails kb_search's checks, a job repeated or already in a batch; the
+ * message names the item), KB_ENOMEM, KB_ECUDA.  *out: kb_batch_free. */
+int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flags, kb_batch **out);
+
+/* Run every search of the batch on `stream` (one graph launch), then record each
+ * job's completion so that kb_job_wait / kb_results work per job.  Runs of one
+ * batch are serialised by the graph. */
+int kb_batch_run(kb_batch *b, void *stream);
+
+/* The batch's groups: *n_groups = their number; up to `capacity` written to out. */
+int kb_batch_groups(const kb_batch *b, kb_batch_group *out, int capacity, int *n_groups);
+
+/* Waits for the batch's work, releases it and its jobs (which stay valid). */
+void kb_batch_free(kb_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libkb.so")
 KB_OK, KB_EINVAL, KB_ENOMEM, KB_ECUDA, KB_ETIMEOUT, KB_ERANGE = 0, 1, 2, 3, 4, 5
 KB_F32, KB_BF16, KB_F16 = 0, 1, 2
 KB_RESCORE_FP64 = 1
+KB_BATCH_AUTOTUNE = 1
 STORAGE = {"f32": KB_F32, "bf16": KB_BF16, "f16": KB_F16}
 
 RESULT_DTYPE = np.dtype([("x0", "<i4"), ("y0", "<i4"), ("vidx", "<i4"), ("nobs", "<i4"),
@@ -64,10 +65,16 @@ _kb_job_repaired = _sig("kb_job_repaired", _i32, [_P, ctypes.POINTER(_sz)])
 _kb_make_psi_phi_static = _sig("kb_make_psi_phi_static", _i32,
                                [_P, _P, _P, _P, _i32, _i32, _i32, _i32, _f32, _P, _P])
 
+_kb_batch_create = _sig("kb_batch_create", _i32, [_P, _i32, _P, _i32, ctypes.POINTER(_P)])
+_kb_batch_run = _sig("kb_batch_run", _i32, [_P, _P])
+_kb_batch_groups = _sig("kb_batch_groups", _i32, [_P, _P, _i32, ctypes.POINTER(_i32)])
+_kb_batch_free = _sig("kb_batch_free", None, [_P])
+
 EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_search_variant",
             "kb_set_search_carveout", "kb_measure_gather_peak", "kb_stack_create", "kb_stack_free",
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
-            "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static"]
+            "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static",
+            "kb_batch_create", "kb_batch_run", "kb_batch_groups", "kb_batch_free"]
 
 
 class KBError(RuntimeError):
@@ -264,3 +271,59 @@ class Job:
         except Exception:
             pass
 
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("job", _P), ("stack", _P), ("times", _P), ("vx", _P), ("vy", _P), ("V", _i32),
+                ("topk", _i32), ("nu_min", _f32), ("flags", _i32)]
+
+
+class BatchGroup(ctypes.Structure):
+    """kb_batch_group: the plan of one persistent launch of a batch."""
+    _fields_ = [("storage", _i32), ("index_bits", _i32), ("variant", _i32), ("kmax", _i32),
+                ("n_items", ctypes.c_longlong), ("evals", ctypes.c_double), ("tuned_ms", _f32 * 5)]
+
+
+class Batch:
+    """kb_batch: many searches (job, stack, times, vx, vy, topk, nu_min, flags) as one graph-captured,
+    persistent launch per storage group.  `searches` is a list of dicts with those keys."""
+
+    def __init__(self, ctx: Context, searches, autotune=True):
+        self.ctx = ctx
+        self._keep = []
+        arr = (_BatchItem * len(searches))()
+        for i, d in enumerate(searches):
+            times, vx, vy = _f64(d["times"]), _f64(d["vx"]), _f64(d["vy"])
+            self._keep += [times, vx, vy]
+            job = d["job"]
+            topk = int(d.get("topk", job.topk))
+            arr[i] = _BatchItem(job.h, d["stack"].h, times.ctypes.data, vx.ctypes.data, vy.ctypes.data, vx.size,
+                                topk, float(d.get("nu_min", -math.inf)), int(d.get("flags", 0)))
+            job.k = topk
+        self.jobs = [d["job"] for d in searches]
+        h = _P()
+        ctx.check(_kb_batch_create(ctx.h, len(searches), ctypes.cast(arr, _P),
+                                   KB_BATCH_AUTOTUNE if autotune else 0, ctypes.byref(h)))
+        self.h = h
+        self._keep = None
+
+    def run(self, stream=None):
+        self.ctx.check(_kb_batch_run(self.h, _stream(stream)))
+
+    def groups(self):
+        n = _i32()
+        self.ctx.check(_kb_batch_groups(self.h, None, 0, ctypes.byref(n)))
+        out = (BatchGroup * n.value)()
+        self.ctx.check(_kb_batch_groups(self.h, ctypes.cast(out, _P), n.value, ctypes.byref(n)))
+        return list(out)
+
+    def free(self):
+        if self.h:
+            _kb_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -491,8 +491,12 @@ void kb_job_free(kb_job *j) {
     delete j;
 }
 
-int kb_search(kb_job *job, const kb_stack *s, const double *times, const double *vx, const double *vy, int V,
-              int topk, float nu_min, int flags, void *stream) {
+// Validation, fixed-point offset table, processing order and upload of one
+// search's tables (stream-ordered), and the kernels' argument blocks.  Shared by
+// kb_search and kb_batch_create.
+static int prepare_search(kb_job *job, const kb_stack *s, const double *times, const double *vx, const double *vy,
+                          int V, int topk, float nu_min, int flags, cudaStream_t st, kb::SearchArgs &a,
+                          kb::RescoreArgs &r, bool &rescore) {
     if (!job) return KB_EINVAL;
     kb_ctx *ctx = job->ctx;
     if (!s || !times || !vx || !vy) return fail(ctx, KB_EINVAL, "kb_search: NULL argument");
@@ -514,8 +518,6 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
         if ((rc = quant_velocity(ctx, vx[v], &qx[v])) != KB_OK) return rc;
         if ((rc = quant_velocity(ctx, vy[v], &qy[v])) != KB_OK) return rc;
     }
-    DeviceGuard g(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
 
     // host tables in the pinned staging buffer (wait until its previous upload is done)
     cudaError_t e = cudaEventSynchronize(job->stage_done);
@@ -565,9 +567,8 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     if (e == cudaSuccess) e = cudaEventRecord(job->stage_done, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_search upload");
 
-    const bool rescore = (flags & KB_RESCORE_FP64) != 0;
+    rescore = (flags & KB_RESCORE_FP64) != 0;
     const int kkeep = rescore ? job_kkeep(topk, flags, s->q16 ? s->storage : KB_F32) : topk;
-    kb::SearchArgs a;
     a.storage = s->q16 ? s->storage : KB_F32;
     a.planes = s->q16 ? (const void *)s->q16 : (const void *)s->f32;
     a.plane_elems = s->L.plane_elems;
@@ -591,13 +592,7 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     a.carveout = ctx->search_carveout;
     a.ptab = job->ptab;
     a.status = job->status;
-    if (a.variant >= 5)
-        e = kb::launch_search_tma(a, st);
-    else
-        e = kb::launch_search(a, st, ctx->sm_count);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "search kernel");
     if (rescore) {
-        kb::RescoreArgs r;
         r.f32 = s->f32;
         r.plane_elems = a.plane_elems;
         r.origin = a.origin;
@@ -616,13 +611,7 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
         r.unit = s->q16 ? (s->storage == KB_BF16 ? 0x1p-8 : 0x1p-11) : 0x1p-24;
         r.ulist = job->ulist;
         r.ucount = job->ucount;
-        e = cudaMemsetAsync(job->ucount, 0, sizeof(int), st);
-        if (e == cudaSuccess) e = kb::launch_rescore(r, st);
-        if (e == cudaSuccess) e = kb::launch_repair(r, st);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "rescore kernels");
     }
-    e = cudaEventRecord(job->done, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_search");
     job->N = N;
     job->V = V;
     job->k = topk;
@@ -630,6 +619,299 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     job->storage = a.storage;
     job->rescored = rescore;
     return KB_OK;
+}
+
+int kb_search(kb_job *job, const kb_stack *s, const double *times, const double *vx, const double *vy, int V,
+              int topk, float nu_min, int flags, void *stream) {
+    if (!job) return KB_EINVAL;
+    kb_ctx *ctx = job->ctx;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (job->owner) return fail(ctx, KB_EINVAL, "kb_search: the job belongs to a batch (kb_batch_free it first)");
+    kb::SearchArgs a;
+    kb::RescoreArgs r;
+    bool rescore = false;
+    int rc = prepare_search(job, s, times, vx, vy, V, topk, nu_min, flags, st, a, r, rescore);
+    if (rc != KB_OK) return rc;
+    cudaError_t e;
+    if (a.variant >= 5)
+        e = kb::launch_search_tma(a, st);
+    else
+        e = kb::launch_search(a, st, ctx->sm_count);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "search kernel");
+    if (rescore) {
+        e = cudaMemsetAsync(job->ucount, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = kb::launch_rescore(r, st);
+        if (e == cudaSuccess) e = kb::launch_repair(r, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "rescore kernels");
+    }
+    e = cudaEventRecord(job->done, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_search");
+    return KB_OK;
+}
+
+}  // extern "C"
+
+// ---- batched searches --------------------------------------------------------
+// Many searches (uneven stacks, epoch counts, grids, k) in one persistent launch
+// per (storage, index width) group.  The work list holds one item per CTA tile
+// of every search, {search, tile x, tile y, 0}; the persistent CTAs take items
+// off it with an atomic counter.  Searches are ordered by per-tile cost
+// (velocities x epochs), largest first, so the cheap tiles fill the tail; the
+// tiles of one search stay in row-major order, so the CTAs resident at one time
+// cover a band of rows of one stack, the L2 locality the one-search grid has.
+// The launches (and the FP64 rescoring of the searches that ask for it) are
+// captured once into a CUDA graph; kb_batch_run replays it.
+struct kb_batch {
+    kb_ctx *ctx = nullptr;
+    std::vector<kb_job *> jobs;
+    std::vector<kb::SearchArgs> args;
+    std::vector<kb::RescoreArgs> resc;       // searches with FP64 rescoring
+    std::vector<int> resc_job;
+    std::vector<kb_batch_group> groups;
+    std::vector<std::vector<int>> group_jobs;
+    std::vector<int4 *> group_items;          // device item list of each group
+    kb::SearchArgs *d_args = nullptr;
+    int *d_counters = nullptr;                // one per group
+    int4 *d_items = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    size_t bytes = 0;
+};
+
+namespace {
+
+int index_bits(const kb::SearchArgs &a) {
+    const long long span = (a.storage == KB_F32 ? 1LL : 2LL) * a.N * a.plane_elems;
+    return span < (1LL << 31) - 1 ? 32 : 64;
+}
+
+// Items of a group for one tile shape: whole searches, or (sample) a band of
+// about `frac` of each search's rows from its middle.
+void make_items(const kb_batch *b, int g, int variant, double frac, std::vector<int4> &out) {
+    out.clear();
+    const int span = kb::search_span(b->groups[g].storage, variant), R = kb::kTileRows;
+    for (int j : b->group_jobs[g]) {
+        const kb::SearchArgs &a = b->args[j];
+        const int tx = (a.W + span - 1) / span, ty = (a.H + R - 1) / R;
+        int y0 = 0, y1 = ty;
+        if (frac < 1.0) {
+            const int n = std::max(1, std::min(ty, (int)std::ceil(ty * frac)));
+            y0 = (ty - n) / 2;
+            y1 = y0 + n;
+        }
+        for (int by = y0; by < y1; ++by)
+            for (int bx = 0; bx < tx; ++bx) out.push_back(make_int4(j, bx, by, 0));
+    }
+}
+
+cudaError_t launch_group(const kb_batch *b, int g, int variant, int n_items, cudaStream_t st) {
+    const kb_batch_group &G = b->groups[g];
+    return kb::launch_search_batch(b->d_args, b->group_items[g], n_items, b->d_counters + g, G.storage, variant,
+                                   G.kmax, b->ctx->search_carveout, G.index_bits == 64, b->ctx->sm_count, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flags, kb_batch **out) {
+    if (!ctx || !out) return KB_EINVAL;
+    *out = nullptr;
+    if (count < 1 || !items) return fail(ctx, KB_EINVAL, "kb_batch_create: empty batch");
+    if (flags & ~KB_BATCH_AUTOTUNE) return fail(ctx, KB_EINVAL, "kb_batch_create: unknown flags 0x%x", flags);
+    for (int i = 0; i < count; ++i) {
+        kb_job *j = items[i].job;
+        if (!j || j->ctx != ctx) return fail(ctx, KB_EINVAL, "kb_batch_create: item %d has no job of this context", i);
+        if (j->owner) return fail(ctx, KB_EINVAL, "kb_batch_create: item %d's job belongs to another batch", i);
+        for (int k = 0; k < i; ++k)
+            if (items[k].job == j) return fail(ctx, KB_EINVAL, "kb_batch_create: items %d and %d share a job", k, i);
+    }
+    DeviceGuard dg(ctx->device);
+    kb_batch *b = new kb_batch();
+    b->ctx = ctx;
+    auto bail = [&](int rc) {
+        kb_batch_free(b);
+        return rc;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "kb_batch_create"));
+
+    // tables of every search, uploaded on the batch's stream
+    b->args.resize(count);
+    for (int i = 0; i < count; ++i) {
+        const kb_batch_item &it = items[i];
+        kb::RescoreArgs r;
+        bool rescore = false;
+        int rc = prepare_search(it.job, it.stack, it.times, it.vx, it.vy, it.V, it.topk, it.nu_min, it.flags, b->cap,
+                                b->args[i], r, rescore);
+        if (rc != KB_OK) {
+            std::string why = ctx->err;
+            return bail(fail(ctx, rc, "kb_batch_create item %d: %s", i, why.c_str()));
+        }
+        b->jobs.push_back(it.job);
+        it.job->owner = b;
+        if (rescore) {
+            b->resc.push_back(r);
+            b->resc_job.push_back(i);
+        }
+    }
+
+    // Groups by (storage, index width, list length): the lists' shared memory
+    // sets how many CTAs an SM holds, so each group's launch is sized for its
+    // own k instead of the batch's largest.  Within a group, searches by
+    // per-tile cost, largest first.
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (long long)b->args[x].V * b->args[x].N > (long long)b->args[y].V * b->args[y].N;
+    });
+    for (int i : order) {
+        const kb::SearchArgs &a = b->args[i];
+        const int bits = index_bits(a);
+        int g = 0;
+        while (g < (int)b->groups.size() && !(b->groups[g].storage == a.storage && b->groups[g].index_bits == bits &&
+                                              b->groups[g].kmax == a.k))
+            ++g;
+        if (g == (int)b->groups.size()) {
+            kb_batch_group G;
+            memset(&G, 0, sizeof G);
+            G.storage = a.storage;
+            G.index_bits = bits;
+            G.variant = 4;
+            G.kmax = a.k;
+            b->groups.push_back(G);
+            b->group_jobs.emplace_back();
+        }
+        b->group_jobs[g].push_back(i);
+        b->groups[g].evals += (double)a.V * a.N * a.H * a.W;
+    }
+    const int G = (int)b->groups.size();
+
+    // device arrays: search arguments, counters, and each group's item list at
+    // its narrowest tile shape (64 pixels: the most items any shape needs)
+    size_t n_items_max = 0;
+    std::vector<size_t> cap_items(G);
+    {
+        std::vector<int4> tmp;
+        for (int g = 0; g < G; ++g) {
+            make_items(b, g, 2, 1.0, tmp);
+            cap_items[g] = tmp.size();
+            n_items_max += tmp.size();
+        }
+    }
+    int rc = dev_alloc(ctx, (size_t)count * sizeof(kb::SearchArgs), (void **)&b->d_args, &b->bytes);
+    if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)G * sizeof(int), (void **)&b->d_counters, &b->bytes);
+    if (rc == KB_OK) rc = dev_alloc(ctx, n_items_max * sizeof(int4), (void **)&b->d_items, &b->bytes);
+    if (rc != KB_OK) return bail(rc);
+    for (int g = 0, off = 0; g < G; off += (int)cap_items[g], ++g) b->group_items.push_back(b->d_items + off);
+    e = cudaMemcpyAsync(b->d_args, b->args.data(), (size_t)count * sizeof(kb::SearchArgs), cudaMemcpyHostToDevice,
+                        b->cap);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "kb_batch_create upload"));
+
+    // Autotuner: time every tile shape of each group on a band from the middle of
+    // each search's rows (about 4e10 trajectory-epoch evaluations per group, or
+    // everything when smaller) and keep the fastest.  Without it the context's
+    // variant (1..4) or the default shape is used.
+    std::vector<int4> host;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (flags & KB_BATCH_AUTOTUNE) {
+        e = cudaEventCreate(&t0);
+        if (e == cudaSuccess) e = cudaEventCreate(&t1);
+        for (int g = 0; g < G && e == cudaSuccess; ++g) {
+            const double frac = std::min(1.0, 4e10 / std::max(1.0, b->groups[g].evals));
+            float best = INFINITY;
+            for (int v = 1; v <= 4 && e == cudaSuccess; ++v) {
+                make_items(b, g, v, frac, host);
+                e = cudaMemcpyAsync(b->group_items[g], host.data(), host.size() * sizeof(int4),
+                                    cudaMemcpyHostToDevice, b->cap);
+                float ms = 0.0f;
+                for (int rep = (v == 1 ? 0 : 1); rep < 2 && e == cudaSuccess; ++rep) {   // one warm-up run
+                    e = cudaMemsetAsync(b->d_counters + g, 0, sizeof(int), b->cap);
+                    if (e == cudaSuccess) e = cudaEventRecord(t0, b->cap);
+                    if (e == cudaSuccess) e = launch_group(b, g, v, (int)host.size(), b->cap);
+                    if (e == cudaSuccess) e = cudaEventRecord(t1, b->cap);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                }
+                b->groups[g].tuned_ms[v] = ms;
+                if (e == cudaSuccess && ms < best) {
+                    best = ms;
+                    b->groups[g].variant = v;
+                }
+            }
+        }
+        if (t0) cudaEventDestroy(t0);
+        if (t1) cudaEventDestroy(t1);
+        if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "kb_batch_create autotune"));
+    } else if (ctx->search_variant >= 1 && ctx->search_variant <= 4) {
+        for (auto &Gr : b->groups) Gr.variant = ctx->search_variant;
+    }
+
+    // final item lists, then the captured graph
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+        make_items(b, g, b->groups[g].variant, 1.0, host);
+        b->groups[g].n_items = (long long)host.size();
+        e = cudaMemcpyAsync(b->group_items[g], host.data(), host.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                            b->cap);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap);
+    }
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "kb_batch_create items"));
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "kb_batch_create capture"));
+    cudaError_t ce = cudaMemsetAsync(b->d_counters, 0, (size_t)G * sizeof(int), b->cap);
+    for (int g = 0; g < G && ce == cudaSuccess; ++g)
+        ce = launch_group(b, g, b->groups[g].variant, (int)b->groups[g].n_items, b->cap);
+    for (size_t i = 0; i < b->resc.size() && ce == cudaSuccess; ++i) {
+        ce = cudaMemsetAsync(b->resc[i].ucount, 0, sizeof(int), b->cap);
+        if (ce == cudaSuccess) ce = kb::launch_rescore(b->resc[i], b->cap);
+        if (ce == cudaSuccess) ce = kb::launch_repair(b->resc[i], b->cap);
+    }
+    e = cudaStreamEndCapture(b->cap, &b->graph);
+    if (ce != cudaSuccess) e = ce;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "kb_batch_create graph"));
+    *out = b;
+    return KB_OK;
+}
+
+int kb_batch_run(kb_batch *b, void *stream) {
+    if (!b) return KB_EINVAL;
+    kb_ctx *ctx = b->ctx;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaGraphLaunch(b->exec, st);
+    for (size_t i = 0; i < b->jobs.size() && e == cudaSuccess; ++i) e = cudaEventRecord(b->jobs[i]->done, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_batch_run");
+    return KB_OK;
+}
+
+int kb_batch_groups(const kb_batch *b, kb_batch_group *out, int capacity, int *n_groups) {
+    if (!b || !n_groups) return KB_EINVAL;
+    *n_groups = (int)b->groups.size();
+    if (out)
+        for (int g = 0; g < std::min(capacity, *n_groups); ++g) out[g] = b->groups[g];
+    return KB_OK;
+}
+
+void kb_batch_free(kb_batch *b) {
+    if (!b) return;
+    DeviceGuard dg(b->ctx->device);
+    if (b->cap) cudaStreamSynchronize(b->cap);
+    for (kb_job *j : b->jobs) {
+        if (j->done) cudaEventSynchronize(j->done);
+        j->owner = nullptr;
+    }
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->d_args);
+    cudaFree(b->d_counters);
+    cudaFree(b->d_items);
+    dev_release(b->ctx, b->bytes);
+    delete b;
 }
 
 int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream) {

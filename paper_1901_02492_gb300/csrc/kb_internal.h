@@ -110,6 +110,7 @@ struct kb_job {
     int *ucount = nullptr;       // their number (rescoring)
     int kkeep_cap = 0;
     kb_result *expand = nullptr; // device staging for host-bound kb_results (lazy)
+    kb_batch *owner = nullptr;   // the batch whose tables this job holds (kb_search refuses it)
     size_t expand_cap = 0;
     size_t bytes = 0;
 };
@@ -163,6 +164,15 @@ struct SearchArgs {
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, int sm_count);
 // TMA-pipelined kernel (variants 5..8)
 cudaError_t launch_search_tma(const SearchArgs &a, cudaStream_t st);
+// persistent batch kernel over (job, tile) items {job, tile x, tile y, 0}; all jobs of
+// one launch share storage, shape (variant 0..4) and index width; lists sized for kmax;
+// carve = shared-memory carveout percent (-1: the automatic rule)
+cudaError_t launch_search_batch(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int storage,
+                                int variant, int kmax, int carve, bool idx64, int sm_count, cudaStream_t st);
+// pixels per CTA row segment of a register-gather shape (tile width)
+int search_span(int storage, int variant);
+// rows per CTA tile of the register-gather kernel
+constexpr int kTileRows = 8;
 
 struct RescoreArgs {
     const float2 *f32;       // FP32 planes

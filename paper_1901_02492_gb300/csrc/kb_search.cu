@@ -115,8 +115,10 @@ struct Entry {
     int info;
 };
 
+// One CTA tile (rows by * 8 .. +7, columns bx * SPAN .. +SPAN-1) of one search:
+// the body of both the one-search kernel and the persistent batch kernel.
 template <int STORAGE, int P, int C, typename I>
-__global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
+__device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by, float2 *s_scale, int4 *s_dyn4) {
     typedef Store<STORAGE> St;
     typedef typename St::T T;         // one pixel's (psi, phi)
     typedef Gather<STORAGE> G;
@@ -126,9 +128,8 @@ __global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
     constexpr int SPAN = 32 * PX;     // pixels per warp row segment
     constexpr int LS = THREADS * PX;  // list stride
 
-    __shared__ float2 s_scale[KB_MAX_EPOCHS];   // per time-ordered epoch
-    // dynamic: table E [TAB] | velocity ids [TAB] | list nu float [k][LS] | list vidx u16 [k][LS]
-    extern __shared__ int4 s_dyn4[];
+    // s_scale: per time-ordered epoch.  s_dyn4: table E [TAB] | velocity ids [TAB] |
+    // list nu float [k][LS] | list vidx u16 [k][LS]
     E *s_tab = reinterpret_cast<E *>(s_dyn4);
     int *s_vid = reinterpret_cast<int *>(s_tab + TAB);
     float *s_ln = reinterpret_cast<float *>(s_vid + TAB);
@@ -143,9 +144,9 @@ __global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
     }
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int y0 = blockIdx.y * WARPS;
+    const int y0 = by * WARPS;
     const int y = y0 + warp;
-    const int xw = blockIdx.x * SPAN;
+    const int xw = bx * SPAN;
     const bool active = y < a.H;
     const T *planes = reinterpret_cast<const T *>(a.planes);
     // element index of this lane's first pixel within a plane (even for 16-bit storage)
@@ -312,6 +313,38 @@ __global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
 }
 
 template <int STORAGE, int P, int C, typename I>
+__global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
+    __shared__ float2 s_scale[KB_MAX_EPOCHS];
+    extern __shared__ int4 s_dyn4[];
+    search_tile<STORAGE, P, C, I>(a, blockIdx.x, blockIdx.y, s_scale, s_dyn4);
+}
+
+// Persistent batch search: CTAs take (job, tile) work items from an atomic
+// counter until the list is exhausted, copying the item's job descriptor into
+// shared memory first.  The item list is ordered by cost (largest first), so
+// uneven stacks, grids and epoch counts balance across the SMs.
+template <int STORAGE, int P, int C, typename I>
+__global__ void __launch_bounds__(THREADS) search_batch_kernel(const SearchArgs *jobs, const int4 *items, int n_items,
+                                                             int *counter) {
+    __shared__ float2 s_scale[KB_MAX_EPOCHS];
+    __shared__ SearchArgs s_job;
+    __shared__ int s_it;
+    extern __shared__ int4 s_dyn4[];
+    for (;;) {
+        if (threadIdx.x == 0) s_it = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_it;
+        if (it >= n_items) break;
+        const int4 w = items[it];
+        for (int i = threadIdx.x; i < (int)(sizeof(SearchArgs) / sizeof(int)); i += THREADS)
+            reinterpret_cast<int *>(&s_job)[i] = reinterpret_cast<const int *>(jobs + w.x)[i];
+        __syncthreads();
+        search_tile<STORAGE, P, C, I>(s_job, w.y, w.z, s_scale, s_dyn4);
+        __syncthreads();
+    }
+}
+
+template <int STORAGE, int P, int C, typename I>
 cudaError_t launch_one(const SearchArgs &a, cudaStream_t st) {
     constexpr int SPAN = 32 * P * Gather<STORAGE>::PIX;
     static_assert(SPAN <= kSpan, "warp span wider than the zero columns");
@@ -362,7 +395,71 @@ cudaError_t launch_storage(const SearchArgs &a, cudaStream_t st) {
     }
 }
 
+template <int STORAGE, int P, int C, typename I>
+cudaError_t launch_batch_one(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int kmax,
+                             int carve, int sm_count, cudaStream_t st) {
+    size_t smem = (size_t)TAB * (sizeof(Entry<I>) + sizeof(int)) +
+                  (size_t)kmax * THREADS * P * Gather<STORAGE>::PIX * (sizeof(float) + sizeof(uint16_t));
+    auto kern = search_batch_kernel<STORAGE, P, C, I>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (carve < 0 && kmax > 8) carve = 58;   // the rule of the one-search launch
+    if (err == cudaSuccess && carve >= 0)
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+    int per_sm = 0;
+    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+    if (err != cudaSuccess) return err;
+    // persistent grid: every SM filled with as many CTAs as it can hold
+    const int grid = sm_count * (per_sm > 0 ? per_sm : 1);
+    kern<<<grid, THREADS, smem, st>>>(jobs, items, n_items, counter);
+    return cudaGetLastError();
+}
+
+template <int STORAGE, int P, int C>
+cudaError_t launch_batch_idx(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int kmax,
+                             int carve, bool idx64, int sm_count, cudaStream_t st) {
+    if (idx64)
+        return launch_batch_one<STORAGE, P, C, long long>(jobs, items, n_items, counter, kmax, carve, sm_count, st);
+    return launch_batch_one<STORAGE, P, C, int>(jobs, items, n_items, counter, kmax, carve, sm_count, st);
+}
+
+template <int STORAGE>
+cudaError_t launch_batch_storage(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int variant,
+                                 int kmax, int carve, bool idx64, int sm_count, cudaStream_t st) {
+    if constexpr (STORAGE == KB_F32) {
+        switch (variant) {
+            case 1: return launch_batch_idx<STORAGE, 4, 4>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
+            case 2: return launch_batch_idx<STORAGE, 2, 4>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
+            case 3: return launch_batch_idx<STORAGE, 4, 8>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
+            default: return launch_batch_idx<STORAGE, 2, 8>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
+        }
+    } else {
+        switch (variant) {
+            case 1: return launch_batch_idx<STORAGE, 2, 4>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
+            case 2: return launch_batch_idx<STORAGE, 1, 4>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
+            case 3: return launch_batch_idx<STORAGE, 2, 8>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
+            default: return launch_batch_idx<STORAGE, 1, 8>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
+        }
+    }
+}
+
 }  // namespace
+
+int search_span(int storage, int variant) {
+    // loads per lane P of the shape, times 32 lanes, times pixels per load
+    static const int p32[5] = {2, 4, 2, 4, 2}, p16[5] = {1, 2, 1, 2, 1};
+    const int v = (variant >= 1 && variant <= 4) ? variant : 0;
+    return storage == KB_F32 ? 32 * p32[v] : 64 * p16[v];
+}
+
+cudaError_t launch_search_batch(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int storage,
+                                int variant, int kmax, int carve, bool idx64, int sm_count, cudaStream_t st) {
+    switch (storage) {
+        case KB_F32: return launch_batch_storage<KB_F32>(jobs, items, n_items, counter, variant, kmax, carve, idx64, sm_count, st);
+        case KB_BF16: return launch_batch_storage<KB_BF16>(jobs, items, n_items, counter, variant, kmax, carve, idx64, sm_count, st);
+        case KB_F16: return launch_batch_storage<KB_F16>(jobs, items, n_items, counter, variant, kmax, carve, idx64, sm_count, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, int /*sm_count*/) {
     switch (a.storage) {

@@ -18,7 +18,10 @@ shape: 4K x 4K warped DECam patches, 3 nights, 4 visits per night, Sec. 3.1-3.2)
               17x17 Gaussian PSF with FWHM U[3.5, 4.5] per epoch, 50 sources
               with per-epoch SNR U[1.5, 3], speeds 90-550 px/d, angles within
               +-pi/4 of +x; grid 32 angles x 32 speeds over that range, k = 8.
-  batch()     uneven stacks for the batched search (2048 x 4096, 5-20 epochs).
+  batch_specs() / batch_stack() / batch_meta()
+              64 uneven stacks for the batched search (W 2048 x H 4096, 5-20
+              epochs over 1-4 nights, PSF sigma 1.2-2.0 px, 256-2048
+              velocities, k 4-16); images_device() draws their planes on the GPU.
   serving_jobs()  the job mix of the serving loop.
 """
 from __future__ import annotations
@@ -212,6 +215,48 @@ def batch_stack(spec: dict, H: int = 4096, W: int = 2048) -> Stack:
     vx, vy = velocity_grid(spec["n_angles"], spec["n_speeds"], -math.pi / 4, math.pi / 4, 90.0, 550.0)
     return Stack("batch#%d %dx%dx%d" % (spec["index"], N, H, W), sci, var, None, psf, times, vx, vy,
                  spec["k"], [])
+
+
+def batch_meta(spec: dict):
+    """Host part of one batch stack: (times, psf [N][K][K], vx, vy, k), drawn as in batch_stack()."""
+    rng = np.random.default_rng(spec["seed"])
+    N = spec["N"]
+    times = batch_times(N, spec["nights"], rng)
+    K = 2 * int(math.ceil(4 * spec["sigma"])) + 1
+    psf = np.stack([gaussian_psf(K, spec["sigma"])] * N)
+    vx, vy = velocity_grid(spec["n_angles"], spec["n_speeds"], -math.pi / 4, math.pi / 4, 90.0, 550.0)
+    return times, psf, vx, vy, spec["k"]
+
+
+def images_device(seed: int, N: int, H: int, W: int, device, var_lo: float = 80.0, var_hi: float = 120.0,
+                  nan_frac: float = 0.01):
+    """Science and variance planes drawn on a CUDA device (torch's seeded generator), with the
+    noise and bad-pixel model of decam(): per-epoch variance U[var_lo, var_hi], N(0, var) noise,
+    disks of radius 1-3 px set to NaN covering about `nan_frac` of each epoch.  For workloads too
+    large to draw on the host in reasonable time; returns float32 tensors [N][H][W]."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    var_t = torch.empty(N, device=device).uniform_(var_lo, var_hi, generator=g)
+    sci = torch.randn((N, H, W), device=device, generator=g)
+    sci *= var_t.sqrt().view(N, 1, 1)
+    var = var_t.view(N, 1, 1).expand(N, H, W).contiguous()
+    n = max(1, int(nan_frac * H * W / 15.67))     # mean disk area of radii 1, 2, 3: (5 + 13 + 29) / 3
+    for e in range(N):
+        r = torch.randint(1, 4, (n,), device=device, generator=g)
+        cy = torch.randint(0, H, (n,), device=device, generator=g)
+        cx = torch.randint(0, W, (n,), device=device, generator=g)
+        for rad in (1, 2, 3):
+            oy, ox = torch.meshgrid(torch.arange(-rad, rad + 1, device=device),
+                                    torch.arange(-rad, rad + 1, device=device), indexing="ij")
+            sel = oy * oy + ox * ox <= rad * rad
+            oy, ox = oy[sel], ox[sel]
+            m = r == rad
+            yy = (cy[m][:, None] + oy[None, :]).reshape(-1)
+            xx = (cx[m][:, None] + ox[None, :]).reshape(-1)
+            ok = (yy >= 0) & (yy < H) & (xx >= 0) & (xx < W)
+            sci[e].view(-1)[yy[ok] * W + xx[ok]] = float("nan")
+    return sci, var
 
 
 def serving_jobs(seed: int = 4, count: int = 2000, rate_hz: float = 1.0):

@@ -52,6 +52,25 @@ def test_result_struct_layout_matches_binding(tmp_path):
     assert vals[1:] == [dt.fields[f][1] for f in dt.names]
 
 
+def test_batch_struct_layouts_match_binding(tmp_path, lib):
+    fields = {"kb_batch_item": ["job", "stack", "times", "vx", "vy", "V", "topk", "nu_min", "flags"],
+              "kb_batch_group": ["storage", "index_bits", "variant", "kmax", "n_items", "evals", "tuned_ms"]}
+    body = ""
+    for name, fs in fields.items():
+        body += 'printf("%%zu", sizeof(%s));' % name
+        body += "".join('printf(" %%zu", offsetof(%s, %s));' % (name, f) for f in fs) + 'printf("\\n");'
+    src = tmp_path / "blayout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "kb.h"\nint main(void){' + body
+                   + "return 0;}\n")
+    exe = tmp_path / "blayout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line, (name, fs), cls in zip(lines, fields.items(), [lib._BatchItem, lib.BatchGroup]):
+        vals = [int(v) for v in line.split()]
+        assert vals[0] == ctypes.sizeof(cls), name
+        assert vals[1:] == [getattr(cls, f).offset for f in fs], name
+
+
 def test_offsets_bit_exact_against_oracle(lib):
     rng = np.random.default_rng(5)
     for trial in range(5):
