@@ -49,9 +49,14 @@ def parse():
     ap.add_argument("--variant", type=int, default=0, help="search kernel shape (0 = automatic)")
     ap.add_argument("--topk", type=int, default=0, help="results per pixel (0 = the workload's k)")
     ap.add_argument("--carveout", type=int, default=-1, help="search shared-memory carveout percent (-1 = auto)")
-    ap.add_argument("--workload", default="decam", choices=["decam", "batch"],
-                    help="decam: the 12x4096^2 stack; batch: 64 uneven 2048x4096 stacks in one batched launch")
+    ap.add_argument("--workload", default="decam", choices=["decam", "batch", "serve"],
+                    help="decam: the 12x4096^2 stack; batch: 64 uneven 2048x4096 stacks in one batched launch; "
+                         "serve: a Poisson stream of search jobs through the serving loop")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--serve-load", type=float, default=0.8, help="target GPU busy fraction of the arrival rate")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     return ap.parse_args()
 
 
@@ -481,12 +486,139 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """The serving workload: Poisson arrivals of search jobs of 512^2, 4096 x 2048 and 4096^2
+    pixels, 5-15 epochs, 256-1024 velocities, k = 8, BF16 planes with FP64 rescoring, admitted
+    under an HBM budget and overlapped on `--serve-slots` streams.  The arrival rate is set to
+    `--serve-load` of the loop's measured capacity.  Beside it, the plain FP32 serial loop: each
+    job alone (upload, psi/phi, FP32 search, results to the host), its measured service times
+    queued first-come first-served on the same arrival times."""
+    import torch
+    import synth
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1901_02492_gb300 import binding as kb
+    from paper_1901_02492_gb300 import serve
+
+    budget = int(args.serve_budget_gb * 1e9)
+    ctx = kb.Context(dev.index, budget)
+    t_gen = time.perf_counter()
+    jobs = synth.serving_jobs(count=args.serve_jobs, rate_hz=1.0)
+    max_n = max(j["N"] for j in jobs)
+    pools = {}
+    for (H, W) in sorted({(j["H"], j["W"]) for j in jobs}):
+        sci, var = synth.images_device(1000 + H + W, max_n, H, W, dev)
+        pools[(H, W)] = (sci.cpu().pin_memory(), var.cpu().pin_memory())
+        del sci, var
+    torch.cuda.empty_cache()
+    metas = [synth.serving_meta(j) for j in jobs]
+
+    def requests(rate, which=None):
+        idx = range(len(jobs)) if which is None else which
+        out = []
+        for i in idx:
+            j, (times, psf, vx, vy, k) = jobs[i], metas[i]
+            sci, var = pools[(j["H"], j["W"])]
+            payload = dict(sci=sci, var=var, psf=psf, times=times, vx=vx, vy=vy)
+            arr = 0.0 if rate is None else j["arrival"] / rate
+            out.append(serve.Request(i, arr, j["N"], j["H"], j["W"], psf.shape[-1], vx.size, k, payload))
+        return out
+
+    max_npix = max(j["H"] * j["W"] for j in jobs)
+    max_planes = max_n * max_npix
+    evals = {i: jobs[i]["N"] * jobs[i]["H"] * jobs[i]["W"] * metas[i][2].size for i in range(len(jobs))}
+    t_gen = time.perf_counter() - t_gen
+
+    def backend(storage, rescore, slots):
+        return serve.CudaBackend(ctx, dev, storage=storage, rescore=rescore, slots=slots, max_npix=max_npix,
+                                 max_planes=max_planes, max_topk=8)
+
+    be = backend(args.storage if args.storage != "f32" else "bf16", True, args.serve_slots)
+    sched = serve.Scheduler(be, budget - be.fixed_bytes, args.serve_slots)
+    # warm-up and capacity: a saturated sample of the job mix (all arriving at once)
+    sample = list(range(min(len(jobs), 48)))
+    sched.run(requests(None, sample[:6]))
+    t0 = time.perf_counter()
+    sched.run(requests(None, sample))
+    cap_jobs_s = len(sample) / (time.perf_counter() - t0)
+    rate = args.serve_load * cap_jobs_s
+    be.intervals_ev.clear()
+    with ClockSampler(dev.index) as clk:
+        t0 = time.perf_counter()
+        done = sched.run(requests(rate))
+        wall = time.perf_counter() - t0
+    lat = np.array([c.latency for c in done])
+    busy = serve.busy_fraction(be.device_intervals())
+    total_evals = sum(evals[c.id] for c in done)
+    peak = sched.peak_bytes + be.fixed_bytes
+    del be, sched
+    torch.cuda.synchronize(dev)
+
+    # the serial plain-FP32 loop: one job at a time, service time measured per job
+    ser = backend("f32", False, 1)
+    reqs = requests(rate)
+    for r in reqs:
+        r.nbytes = ser.estimate(r)
+    svc = np.empty(len(reqs))
+    for idx, r in enumerate(reqs[:3] + reqs):
+        a = time.perf_counter()
+        h = ser.admit(r)
+        ser.dispatch(h, 0)
+        h["done"].synchronize()
+        ser.finish(h)
+        if idx >= 3:
+            svc[idx - 3] = time.perf_counter() - a
+    ser_lat = serve.fifo_latencies(np.array([r.arrival for r in reqs]), svc)
+    del ser
+
+    def pct(x, q):
+        return float(np.percentile(x, q))
+
+    line = {"metric": "serving: p50/p99 job latency and throughput vs a serial plain-FP32 loop",
+            "value": total_evals / wall, "unit": "evals/s", "n_gpus": world, "steps": 1, "warmup": 1,
+            "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "serving: %d Poisson-arrival jobs of 512^2, 4096x2048, 4096^2 px, 5-15 epochs, "
+                                   "256-1024 velocities, k=8, BF16 + FP64 rescoring" % len(jobs),
+                       "jobs": len(jobs), "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb,
+                       "arrival_rate_hz": rate, "capacity_jobs_s": cap_jobs_s, "target_load": args.serve_load,
+                       "inputs": "pinned host stacks per size class (drawn on the device), copied to the device "
+                                 "per job", "generate_s": round(t_gen, 1), "parallelism": "replicas%d" % world},
+            "serving": {"p50_s": pct(lat, 50), "p99_s": pct(lat, 99), "mean_s": float(lat.mean()),
+                        "jobs_per_s": len(done) / wall, "gpu_busy_fraction": busy,
+                        "peak_device_bytes": int(peak)},
+            "serial_fp32": {"p50_s": pct(ser_lat, 50), "p99_s": pct(ser_lat, 99),
+                            "jobs_per_s": len(reqs) / float(svc.sum()),
+                            "evals_per_s": sum(evals.values()) / float(svc.sum()),
+                            "mean_service_s": float(svc.mean())},
+            "clocks": clk.summary(),
+            "e2e": {"value": total_evals / wall, "unit": "evals/s",
+                    "h2d_bytes_per_step": int(sum(2 * 4 * jobs[c.id]["N"] * jobs[c.id]["H"] * jobs[c.id]["W"]
+                                                  for c in done)),
+                    "d2h_bytes_per_step": int(sum(48 * 8 * jobs[c.id]["H"] * jobs[c.id]["W"] for c in done))},
+            "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -85,7 +85,10 @@ typedef struct kb_result {
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps what the
  * context's stacks and jobs may hold on the device (0 = no cap); allocations
- * beyond it fail with KB_ENOMEM.  *ctx is owned by the caller: kb_destroy. */
+ * beyond it fail with KB_ENOMEM.  Device memory comes from a stream-ordered
+ * pool of the context, so creating and freeing stacks and jobs never waits for
+ * kernels running on other streams; freed blocks stay in the pool for reuse
+ * until kb_destroy.  *ctx is owned by the caller: kb_destroy. */
 int kb_init(kb_ctx **ctx, int device, size_t hbm_budget_bytes);
 
 /* Free the context.  Stacks and jobs made from it must be freed first. */
@@ -131,6 +134,10 @@ int kb_measure_gather_peak(kb_ctx *ctx, double *gb_per_s);
  * * 8 bytes, twice that with 16-bit storage.  *out is owned by the caller:
  * kb_stack_free. */
 int kb_stack_create(kb_ctx *ctx, int N, int H, int W, int storage, kb_stack **out);
+/* Release the stack.  Its memory is reused only after the last kb_make_psi_phi,
+ * kb_search or kb_stack_copy_planes on it has finished on the device; when the
+ * stack was searched from several streams at once, the caller waits for all of
+ * them first.  Does not block on kernels of other stacks. */
 void kb_stack_free(kb_stack *s);
 
 /* Sec. 2.1.5: fill the stack with psi_t and phi_t of every epoch.
@@ -196,6 +203,7 @@ int kb_offsets(const double *times, int N, const double *vx, const double *vy, i
  * flags may include KB_RESCORE_FP64 (reserves the candidate buffers).
  * *out is owned by the caller: kb_job_free. */
 int kb_job_create(kb_ctx *ctx, int H, int W, int N, int V, int topk, int flags, kb_job **out);
+/* Release the job; its memory is reused only after its last search finished. */
 void kb_job_free(kb_job *j);
 
 /* Sec. 2.2 exhaustive search of the stack s into job:
@@ -234,6 +242,16 @@ int kb_job_repaired(kb_job *job, size_t *n_pixels);
  * with room for `capacity` records; a host destination makes the call wait for
  * the stream.  KB_ERANGE (with *n_written = H*W*topk) if capacity is too small. */
 int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream);
+
+/* Device bytes that one search will hold, for admission under an HBM budget:
+ *   *stack  kb_stack_create(N, H, W, storage) plus kb_make_psi_phi with a K x K
+ *           PSF (an upper bound: the tap table of a non-separable PSF)
+ *   *job    kb_job_create(H, W, N, V, topk, flags)
+ * Not included: the staging that kb_results allocates on its first host-bound
+ * call (at most 2^22 records, 192 MiB).  Either pointer may be NULL.  KB_EINVAL
+ * for arguments that kb_stack_create or kb_job_create would reject. */
+int kb_estimate_bytes(int N, int H, int W, int storage, int K, int V, int topk, int flags, size_t *stack,
+                      size_t *job);
 
 /* ---- batched searches (no counterpart in the paper: many stacks per launch) ----
  *

@@ -65,6 +65,8 @@ _kb_job_repaired = _sig("kb_job_repaired", _i32, [_P, ctypes.POINTER(_sz)])
 _kb_make_psi_phi_static = _sig("kb_make_psi_phi_static", _i32,
                                [_P, _P, _P, _P, _i32, _i32, _i32, _i32, _f32, _P, _P])
 
+_kb_estimate_bytes = _sig("kb_estimate_bytes", _i32, [_i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32,
+                                                       ctypes.POINTER(_sz), ctypes.POINTER(_sz)])
 _kb_batch_create = _sig("kb_batch_create", _i32, [_P, _i32, _P, _i32, ctypes.POINTER(_P)])
 _kb_batch_run = _sig("kb_batch_run", _i32, [_P, _P])
 _kb_batch_groups = _sig("kb_batch_groups", _i32, [_P, _P, _i32, ctypes.POINTER(_i32)])
@@ -74,7 +76,7 @@ EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_s
             "kb_set_search_carveout", "kb_measure_gather_peak", "kb_stack_create", "kb_stack_free",
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
             "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static",
-            "kb_batch_create", "kb_batch_run", "kb_batch_groups", "kb_batch_free"]
+            "kb_batch_create", "kb_batch_run", "kb_batch_groups", "kb_batch_free", "kb_estimate_bytes"]
 
 
 class KBError(RuntimeError):
@@ -202,6 +204,17 @@ def make_psi_phi_static(sci, var, mask, psf, out, bright_max=math.inf, stream=No
                                  float(bright_max), _ptr(out), _stream(stream))
     if rc != KB_OK:
         raise KBError(rc, "kb_make_psi_phi_static failed")
+
+
+def estimate_bytes(N, H, W, storage, K, V, topk, flags=0):
+    """(stack bytes, job bytes) that kb_stack_create + kb_make_psi_phi and kb_job_create will hold."""
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    a, b = _sz(), _sz()
+    rc = _kb_estimate_bytes(int(N), int(H), int(W), st, int(K), int(V), int(topk), int(flags), ctypes.byref(a),
+                            ctypes.byref(b))
+    if rc != KB_OK:
+        raise KBError(rc, "kb_estimate_bytes rejected the shape")
+    return int(a.value), int(b.value)
 
 
 def offsets(times, vx, vy):

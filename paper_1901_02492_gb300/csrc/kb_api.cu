@@ -58,16 +58,61 @@ int dev_alloc(kb_ctx *ctx, size_t bytes, void **p, size_t *acct) {
                         ctx->budget);
         ctx->in_use += bytes;
     }
-    cudaError_t e = cudaMalloc(p, bytes);
+    // from the context's pool, ordered on its internal stream; synchronising that
+    // stream (not the device) makes the block usable from any stream
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->astream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->astream);
     if (e != cudaSuccess) {
         std::lock_guard<std::mutex> g(ctx->mu);
         ctx->in_use -= bytes;
         cudaGetLastError();
+        if (*p) cudaFreeAsync(*p, ctx->astream);
         *p = nullptr;
-        return fail(ctx, KB_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        return fail(ctx, KB_ENOMEM, "device allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
     }
     *acct += bytes;
     return KB_OK;
+}
+
+// Returns a block to the pool in the internal stream's order.  The caller has
+// made that stream wait for the last work that used the block.
+void dev_free(kb_ctx *ctx, void *p) {
+    if (p) cudaFreeAsync(p, ctx->astream);
+}
+
+// Pinned host staging: reuse a cached block of at least `bytes`, else allocate.
+cudaError_t host_alloc(kb_ctx *ctx, size_t bytes, void **p, size_t *cap) {
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        int best = -1;
+        for (int i = 0; i < (int)ctx->host_cache.size(); ++i)
+            if (ctx->host_cache[i].second >= bytes &&
+                (best < 0 || ctx->host_cache[i].second < ctx->host_cache[best].second))
+                best = i;
+        if (best >= 0) {
+            *p = ctx->host_cache[best].first;
+            *cap = ctx->host_cache[best].second;
+            ctx->host_cached -= *cap;
+            ctx->host_cache.erase(ctx->host_cache.begin() + best);
+            return cudaSuccess;
+        }
+    }
+    *cap = bytes;
+    return cudaMallocHost(p, bytes);
+}
+
+// Keeps up to 1 GiB of released staging for reuse (cudaFreeHost can stall the device).
+void host_release(kb_ctx *ctx, void *p, size_t cap) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (ctx->host_cached + cap <= ((size_t)1 << 30)) {
+            ctx->host_cache.emplace_back(p, cap);
+            ctx->host_cached += cap;
+            return;
+        }
+    }
+    cudaFreeHost(p);
 }
 
 void dev_release(kb_ctx *ctx, size_t bytes) {
@@ -182,11 +227,38 @@ int kb_init(kb_ctx **out, int device, size_t hbm_budget_bytes) {
     }
     ctx->sm_count = prop.multiProcessorCount;
     ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    cudaMemPoolProps pp;
+    memset(&pp, 0, sizeof pp);
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    e = cudaMemPoolCreate(&ctx->pool, &pp);
+    if (e == cudaSuccess) {
+        // freed blocks stay in the pool until the context is destroyed
+        uint64_t keep = ~0ULL;
+        e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->astream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        kb_destroy(ctx);
+        return KB_ECUDA;
+    }
     *out = ctx;
     return KB_OK;
 }
 
-void kb_destroy(kb_ctx *ctx) { delete ctx; }
+void kb_destroy(kb_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    if (ctx->astream) {
+        cudaStreamSynchronize(ctx->astream);
+        cudaStreamDestroy(ctx->astream);
+    }
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    for (auto &b : ctx->host_cache) cudaFreeHost(b.first);
+    delete ctx;
+}
 
 const char *kb_last_error(const kb_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
@@ -231,9 +303,12 @@ int kb_stack_create(kb_ctx *ctx, int N, int H, int W, int storage, kb_stack **ou
     if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)N * sizeof(float2), (void **)&s->scales, &s->bytes);
     if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)2 * N * sizeof(unsigned), (void **)&s->maxbits, &s->bytes);
     cudaError_t e = cudaSuccess;
-    if (rc == KB_OK) e = cudaMemset(s->f32, 0, (size_t)N * plane * sizeof(float2));
-    if (rc == KB_OK && e == cudaSuccess && s->q16) e = cudaMemset(s->q16, 0, (size_t)2 * N * plane * sizeof(kb::pair16));
+    if (rc == KB_OK) e = cudaMemsetAsync(s->f32, 0, (size_t)N * plane * sizeof(float2), ctx->astream);
+    if (rc == KB_OK && e == cudaSuccess && s->q16)
+        e = cudaMemsetAsync(s->q16, 0, (size_t)2 * N * plane * sizeof(kb::pair16), ctx->astream);
+    if (rc == KB_OK && e == cudaSuccess) e = cudaStreamSynchronize(ctx->astream);
     if (rc == KB_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&s->taps_done, cudaEventDisableTiming);
+    if (rc == KB_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&s->used, cudaEventDisableTiming);
     if (rc == KB_OK && e != cudaSuccess) rc = cuda_fail(ctx, e, "kb_stack_create");
     if (rc != KB_OK) {
         kb_stack_free(s);
@@ -246,17 +321,23 @@ int kb_stack_create(kb_ctx *ctx, int N, int H, int W, int storage, kb_stack **ou
 void kb_stack_free(kb_stack *s) {
     if (!s) return;
     DeviceGuard g(s->ctx->device);
+    kb_ctx *ctx = s->ctx;
     if (s->taps_done) {
         cudaEventSynchronize(s->taps_done);
+        cudaStreamWaitEvent(ctx->astream, s->taps_done, 0);
         cudaEventDestroy(s->taps_done);
     }
-    cudaFree(s->f32);
-    cudaFree(s->q16);
-    cudaFree(s->scales);
-    cudaFree(s->maxbits);
-    cudaFree(s->taps);
-    cudaFreeHost(s->taps_host);
-    dev_release(s->ctx, s->bytes);
+    if (s->used) {
+        cudaStreamWaitEvent(ctx->astream, s->used, 0);   // the last search that read the planes
+        cudaEventDestroy(s->used);
+    }
+    dev_free(ctx, s->f32);
+    dev_free(ctx, s->q16);
+    dev_free(ctx, s->scales);
+    dev_free(ctx, s->maxbits);
+    dev_free(ctx, s->taps);
+    host_release(ctx, s->taps_host, s->taps_host_cap);
+    dev_release(ctx, s->bytes);
     delete s;
 }
 
@@ -281,9 +362,12 @@ int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8
     for (int e = 0; e < N && sep; ++e) sep = kb::factor_psf(psf + (size_t)e * K * K, K, fa[e], fb[e]);
     size_t nt = kb::taps_floats(N, K, sep);
     if (nt > s->taps_floats) {
-        if (s->taps_done) cudaEventSynchronize(s->taps_done);
-        cudaFree(s->taps);
-        cudaFreeHost(s->taps_host);
+        if (s->taps_done) {
+            cudaEventSynchronize(s->taps_done);
+            cudaStreamWaitEvent(ctx->astream, s->taps_done, 0);
+        }
+        dev_free(ctx, s->taps);
+        host_release(ctx, s->taps_host, s->taps_host_cap);
         dev_release(ctx, s->taps_floats * sizeof(float));
         s->bytes -= std::min(s->bytes, s->taps_floats * sizeof(float));
         s->taps = nullptr;
@@ -291,7 +375,7 @@ int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8
         s->taps_floats = 0;
         int rc = dev_alloc(ctx, nt * sizeof(float), (void **)&s->taps, &s->bytes);
         if (rc != KB_OK) return rc;
-        cudaError_t e = cudaMallocHost((void **)&s->taps_host, nt * sizeof(float));
+        cudaError_t e = host_alloc(ctx, nt * sizeof(float), (void **)&s->taps_host, &s->taps_host_cap);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMallocHost(taps)");
         s->taps_floats = nt;
     } else {
@@ -344,6 +428,8 @@ int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8
         e = kb::launch_quantize(s->f32, s->q16, s->scales, s->maxbits, N, s->L.plane_elems, s->storage, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "quantize kernel");
     }
+    e = cudaEventRecord(s->used, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_make_psi_phi");
     s->filled = true;
     return KB_OK;
 }
@@ -367,6 +453,7 @@ int kb_stack_copy_planes(const kb_stack *s, int which, void *dst, size_t dst_byt
         e = cudaMemcpy2DAsync(to, (size_t)s->W * elem, from, (size_t)s->L.pitch * elem, (size_t)s->W * elem,
                               (size_t)s->H, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
     }
+    if (e == cudaSuccess) e = cudaEventRecord(s->used, st);
     if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_stack_copy_planes");
     return KB_OK;
@@ -421,6 +508,39 @@ static int job_kkeep(int topk, int flags, int storage) {
     return topk + (storage == KB_BF16 ? std::max(2, topk / 2) : std::max(2, topk / 4));
 }
 
+// Device bytes of kb_stack_create + kb_make_psi_phi (an upper bound: the tap
+// table is sized for the larger PSF form), and of kb_job_create: the same sums as
+// those calls' allocations.
+static size_t stack_bytes(int N, int H, int W, int storage, int K) {
+    const size_t plane = (size_t)kb::make_layout(H, W).plane_elems;
+    size_t b = (size_t)N * plane * sizeof(float2);
+    if (storage != KB_F32) b += (size_t)2 * N * plane * sizeof(kb::pair16);
+    b += (size_t)N * sizeof(float2) + (size_t)2 * N * sizeof(unsigned);
+    // the tap table of whichever PSF form is larger (the form is known only from the PSF)
+    b += std::max(kb::taps_floats(N, K, true), kb::taps_floats(N, K, false)) * sizeof(float);
+    return b;
+}
+
+static size_t job_bytes(int H, int W, int N, int V, int topk, int flags) {
+    const size_t npix = (size_t)H * W;
+    size_t b = (size_t)V * N * sizeof(int2) + (size_t)V * sizeof(int) + (size_t)V * N * sizeof(uint32_t) +
+               sizeof(int) + (size_t)N * sizeof(int) + (size_t)V * sizeof(float2) +
+               npix * job_kkeep(topk, flags, KB_BF16) * sizeof(kb::Rec);
+    if (flags & KB_RESCORE_FP64) b += npix * topk * sizeof(kb::Rec64) + npix * sizeof(int) + sizeof(int);
+    return b;
+}
+
+int kb_estimate_bytes(int N, int H, int W, int storage, int K, int V, int topk, int flags, size_t *stack,
+                      size_t *job) {
+    if (N < 1 || N > KB_MAX_EPOCHS || H < 1 || W < 1 || H > KB_MAX_SIDE || W > KB_MAX_SIDE || K < 1 ||
+        K > KB_MAX_PSF || (K % 2) == 0 || V < 1 || V > KB_MAX_VELOCITIES || topk < 1 || topk > KB_MAX_TOPK ||
+        (storage != KB_F32 && storage != KB_BF16 && storage != KB_F16) || (flags & ~KB_RESCORE_FP64))
+        return KB_EINVAL;
+    if (stack) *stack = stack_bytes(N, H, W, storage, K);
+    if (job) *job = job_bytes(H, W, N, V, topk, flags);
+    return KB_OK;
+}
+
 int kb_job_create(kb_ctx *ctx, int H, int W, int N, int V, int topk, int flags, kb_job **out) {
     if (!ctx || !out) return KB_EINVAL;
     *out = nullptr;
@@ -453,10 +573,11 @@ int kb_job_create(kb_ctx *ctx, int H, int W, int N, int V, int topk, int flags, 
     if (rc == KB_OK) {
         j->stage_bytes = (size_t)V * N * sizeof(int2) + (size_t)V * sizeof(int) + (size_t)N * sizeof(int) +
                          (size_t)V * sizeof(float2) + (size_t)V * N * sizeof(uint32_t);
-        cudaError_t e = cudaMallocHost(&j->stage, j->stage_bytes);
+        cudaError_t e = host_alloc(ctx, j->stage_bytes, &j->stage, &j->stage_cap);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->stage_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMemset(j->status, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(j->status, 0, sizeof(int), ctx->astream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->astream);
         if (e != cudaSuccess) rc = cuda_fail(ctx, e, "kb_job_create");
     }
     if (rc != KB_OK) {
@@ -470,24 +591,28 @@ int kb_job_create(kb_ctx *ctx, int H, int W, int N, int V, int topk, int flags, 
 void kb_job_free(kb_job *j) {
     if (!j) return;
     DeviceGuard g(j->ctx->device);
+    kb_ctx *ctx = j->ctx;
     if (j->stage_done) {
         cudaEventSynchronize(j->stage_done);
         cudaEventDestroy(j->stage_done);
     }
-    if (j->done) cudaEventDestroy(j->done);
-    cudaFree(j->offs);
-    cudaFree(j->vorder);
-    cudaFree(j->ptab);
-    cudaFree(j->status);
-    cudaFree(j->epoch_of);
-    cudaFree(j->vq);
-    cudaFree(j->recs);
-    cudaFree(j->recs64);
-    cudaFree(j->ulist);
-    cudaFree(j->ucount);
-    cudaFree(j->expand);
-    cudaFreeHost(j->stage);
-    dev_release(j->ctx, j->bytes);
+    if (j->done) {
+        cudaStreamWaitEvent(ctx->astream, j->done, 0);   // the last search's kernels
+        cudaEventDestroy(j->done);
+    }
+    dev_free(ctx, j->offs);
+    dev_free(ctx, j->vorder);
+    dev_free(ctx, j->ptab);
+    dev_free(ctx, j->status);
+    dev_free(ctx, j->epoch_of);
+    dev_free(ctx, j->vq);
+    dev_free(ctx, j->recs);
+    dev_free(ctx, j->recs64);
+    dev_free(ctx, j->ulist);
+    dev_free(ctx, j->ucount);
+    dev_free(ctx, j->expand);
+    host_release(ctx, j->stage, j->stage_cap);
+    dev_release(ctx, j->bytes);
     delete j;
 }
 
@@ -646,6 +771,7 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rescore kernels");
     }
     e = cudaEventRecord(job->done, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->used, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_search");
     return KB_OK;
 }
@@ -665,6 +791,7 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
 struct kb_batch {
     kb_ctx *ctx = nullptr;
     std::vector<kb_job *> jobs;
+    std::vector<const kb_stack *> stacks;
     std::vector<kb::SearchArgs> args;
     std::vector<kb::RescoreArgs> resc;       // searches with FP64 rescoring
     std::vector<int> resc_job;
@@ -751,6 +878,7 @@ int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flag
             return bail(fail(ctx, rc, "kb_batch_create item %d: %s", i, why.c_str()));
         }
         b->jobs.push_back(it.job);
+        b->stacks.push_back(it.stack);
         it.job->owner = b;
         if (rescore) {
             b->resc.push_back(r);
@@ -884,6 +1012,7 @@ int kb_batch_run(kb_batch *b, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaGraphLaunch(b->exec, st);
     for (size_t i = 0; i < b->jobs.size() && e == cudaSuccess; ++i) e = cudaEventRecord(b->jobs[i]->done, st);
+    for (size_t i = 0; i < b->stacks.size() && e == cudaSuccess; ++i) e = cudaEventRecord(b->stacks[i]->used, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_batch_run");
     return KB_OK;
 }
@@ -907,9 +1036,9 @@ void kb_batch_free(kb_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
-    cudaFree(b->d_args);
-    cudaFree(b->d_counters);
-    cudaFree(b->d_items);
+    dev_free(b->ctx, b->d_args);
+    dev_free(b->ctx, b->d_counters);
+    dev_free(b->ctx, b->d_items);
     dev_release(b->ctx, b->bytes);
     delete b;
 }
@@ -943,7 +1072,8 @@ int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, 
     }
     const size_t chunk = std::min(need, (size_t)1 << 22);
     if (job->expand_cap < chunk) {
-        cudaFree(job->expand);
+        cudaStreamWaitEvent(ctx->astream, job->done, 0);
+        dev_free(ctx, job->expand);
         dev_release(ctx, job->expand_cap * sizeof(kb_result));
         job->bytes -= std::min(job->bytes, job->expand_cap * sizeof(kb_result));
         job->expand = nullptr;

@@ -7,6 +7,7 @@
 
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/kb.h"
@@ -64,6 +65,15 @@ struct kb_ctx {
     int search_carveout = -1; // -1 = automatic
     std::string err;
     std::mutex mu;
+    // Stream-ordered device memory: a pool that keeps freed blocks for reuse and
+    // an internal stream that allocations and frees are ordered on, so creating
+    // and freeing stacks and jobs never synchronises the device (cudaMalloc /
+    // cudaFree would, stalling every other stream's kernels).
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t astream = nullptr;
+    // pinned host staging blocks returned by freed jobs and stacks, for reuse
+    std::vector<std::pair<void *, size_t>> host_cache;
+    size_t host_cached = 0;
 };
 
 struct kb_stack {
@@ -78,8 +88,10 @@ struct kb_stack {
     unsigned *maxbits = nullptr;  // device [2N] max |psi|, max phi (float bits) for the scales
     float *taps = nullptr;        // device per-epoch PSF taps (layout in kb_psiphi.cu)
     float *taps_host = nullptr;   // pinned staging of the taps
+    size_t taps_host_cap = 0;     // its capacity in bytes
     size_t taps_floats = 0;
     cudaEvent_t taps_done = nullptr;  // taps_host may be rewritten once this has completed
+    cudaEvent_t used = nullptr;       // recorded after the last kernel that read the planes
     size_t bytes = 0;
     bool filled = false;
 };
@@ -101,7 +113,7 @@ struct kb_job {
     float2 *vq = nullptr;        // [Vcap] quantised velocity (px/day) for the results
     // pinned staging for the tables
     void *stage = nullptr;
-    size_t stage_bytes = 0;
+    size_t stage_bytes = 0, stage_cap = 0;
     cudaEvent_t stage_done = nullptr;
     // results
     kb::Rec *recs = nullptr;     // [H*W][kkeep_cap]

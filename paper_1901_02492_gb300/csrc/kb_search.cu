@@ -117,7 +117,7 @@ struct Entry {
 
 // One CTA tile (rows by * 8 .. +7, columns bx * SPAN .. +SPAN-1) of one search:
 // the body of both the one-search kernel and the persistent batch kernel.
-template <int STORAGE, int P, int C, typename I>
+template <int STORAGE, int P, int C, bool PT, typename I>
 __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by, float2 *s_scale, int4 *s_dyn4) {
     typedef Store<STORAGE> St;
     typedef typename St::T T;         // one pixel's (psi, phi)
@@ -206,34 +206,65 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             float2 acc[PX];
 #pragma unroll
             for (int p = 0; p < PX; ++p) acc[p] = acc0[p];
-            int jj = 0;
-            for (; jj + C <= NJ; jj += C) {
-                LT val[C][P];
-                int sx[C];
+            if constexpr (!PT) {
+                // epochs in batches of C loads in flight, then one at a time
+                int jj = 0;
+                for (; jj + C <= NJ; jj += C) {
+                    LT val[C][P];
+                    int sx[C];
 #pragma unroll
-                for (int q = 0; q < C; ++q) {
-                    const E t = tab[jj + q];
-                    sx[q] = t.info >> 16;
-                    const LT *src = ((t.info >> warp) & 1) ? reinterpret_cast<const LT *>(planes + (t.idx + tb)) : zero;
+                    for (int q = 0; q < C; ++q) {
+                        const E t = tab[jj + q];
+                        sx[q] = t.info >> 16;
+                        const LT *src =
+                            ((t.info >> warp) & 1) ? reinterpret_cast<const LT *>(planes + (t.idx + tb)) : zero;
 #pragma unroll
-                    for (int p = 0; p < P; ++p) val[q][p] = __ldg(src + 32 * p);
+                        for (int p = 0; p < P; ++p) val[q][p] = __ldg(src + 32 * p);
+                    }
+#pragma unroll
+                    for (int q = 0; q < C; ++q) {
+                        const float2 sc = exp_scale(sx[q]);
+#pragma unroll
+                        for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[q][p], sc);
+                    }
                 }
+                for (; jj < NJ; ++jj) {
+                    const E t = tab[jj];
+                    const LT *src =
+                        ((t.info >> warp) & 1) ? reinterpret_cast<const LT *>(planes + (t.idx + tb)) : zero;
+                    LT val[P];
 #pragma unroll
-                for (int q = 0; q < C; ++q) {
-                    const float2 sc = exp_scale(sx[q]);
+                    for (int p = 0; p < P; ++p) val[p] = __ldg(src + 32 * p);
+                    const float2 sc = exp_scale(t.info >> 16);
 #pragma unroll
-                    for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[q][p], sc);
+                    for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[p], sc);
                 }
-            }
-            for (; jj < NJ; ++jj) {
-                const E t = tab[jj];
-                const LT *src = ((t.info >> warp) & 1) ? reinterpret_cast<const LT *>(planes + (t.idx + tb)) : zero;
-                LT val[P];
+            } else {
+                // every batch of C predicated (warp-uniform): the remainder costs one
+                // round trip instead of one per epoch, for more registers
+                for (int jj = 0; jj < NJ; jj += C) {
+                    LT val[C][P];
+                    int sx[C];
 #pragma unroll
-                for (int p = 0; p < P; ++p) val[p] = __ldg(src + 32 * p);
-                const float2 sc = exp_scale(t.info >> 16);
+                    for (int q = 0; q < C; ++q) {
+                        if (jj + q < NJ) {
+                            const E t = tab[jj + q];
+                            sx[q] = t.info >> 16;
+                            const LT *src =
+                                ((t.info >> warp) & 1) ? reinterpret_cast<const LT *>(planes + (t.idx + tb)) : zero;
 #pragma unroll
-                for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[p], sc);
+                            for (int p = 0; p < P; ++p) val[q][p] = __ldg(src + 32 * p);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < C; ++q) {
+                        if (jj + q < NJ) {
+                            const float2 sc = exp_scale(sx[q]);
+#pragma unroll
+                            for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[q][p], sc);
+                        }
+                    }
+                }
             }
             // scoring: one warp-uniform test gates the (divergent, rarer) list insertions
             float nu[PX];
@@ -312,19 +343,42 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     }
 }
 
-template <int STORAGE, int P, int C, typename I>
-__global__ void __launch_bounds__(THREADS) search_kernel(SearchArgs a) {
+// Resident CTAs per SM the register allocation is held to (0: no hold).  The
+// shapes with one 8-byte load per lane and epoch: with the plain remainder loop
+// (used for k <= 8, where registers decide how many CTAs an SM holds) the 16-bit
+// one is held to 5 (48 registers), which measured faster than 4 despite the L1
+// the fifth CTA displaces, and the FP32 one reaches 48 registers by itself (and
+// spills when held to it); with the predicated remainder (k > 8, where the
+// lists' shared memory limits the SM to 2-3 CTAs) they are held to 3 (85
+// registers).  The wider shapes: 2.  The batch kernel, which keeps its search's
+// arguments in shared memory rather than the parameter bank and so needs more
+// registers, is held to 3 for the narrow shapes and 2 for the wide ones.
+template <int STORAGE, int P, bool PT>
+constexpr int min_ctas() {
+    constexpr bool narrow = STORAGE == KB_F32 ? P <= 2 : P <= 1;
+    if (!narrow) return 2;
+    if (PT) return 3;
+    return STORAGE == KB_F32 ? 0 : 5;
+}
+
+template <int STORAGE, int P>
+constexpr int min_ctas_batch() {
+    return (STORAGE == KB_F32 ? P <= 2 : P <= 1) ? 3 : 2;
+}
+
+template <int STORAGE, int P, int C, bool PT, typename I>
+__global__ void __launch_bounds__(THREADS, min_ctas<STORAGE, P, PT>()) search_kernel(SearchArgs a) {
     __shared__ float2 s_scale[KB_MAX_EPOCHS];
     extern __shared__ int4 s_dyn4[];
-    search_tile<STORAGE, P, C, I>(a, blockIdx.x, blockIdx.y, s_scale, s_dyn4);
+    search_tile<STORAGE, P, C, PT, I>(a, blockIdx.x, blockIdx.y, s_scale, s_dyn4);
 }
 
 // Persistent batch search: CTAs take (job, tile) work items from an atomic
 // counter until the list is exhausted, copying the item's job descriptor into
 // shared memory first.  The item list is ordered by cost (largest first), so
 // uneven stacks, grids and epoch counts balance across the SMs.
-template <int STORAGE, int P, int C, typename I>
-__global__ void __launch_bounds__(THREADS) search_batch_kernel(const SearchArgs *jobs, const int4 *items, int n_items,
+template <int STORAGE, int P, int C, bool PT, typename I>
+__global__ void __launch_bounds__(THREADS, min_ctas_batch<STORAGE, P>()) search_batch_kernel(const SearchArgs *jobs, const int4 *items, int n_items,
                                                              int *counter) {
     __shared__ float2 s_scale[KB_MAX_EPOCHS];
     __shared__ SearchArgs s_job;
@@ -339,20 +393,20 @@ __global__ void __launch_bounds__(THREADS) search_batch_kernel(const SearchArgs 
         for (int i = threadIdx.x; i < (int)(sizeof(SearchArgs) / sizeof(int)); i += THREADS)
             reinterpret_cast<int *>(&s_job)[i] = reinterpret_cast<const int *>(jobs + w.x)[i];
         __syncthreads();
-        search_tile<STORAGE, P, C, I>(s_job, w.y, w.z, s_scale, s_dyn4);
+        search_tile<STORAGE, P, C, PT, I>(s_job, w.y, w.z, s_scale, s_dyn4);
         __syncthreads();
     }
 }
 
-template <int STORAGE, int P, int C, typename I>
-cudaError_t launch_one(const SearchArgs &a, cudaStream_t st) {
+template <int STORAGE, int P, int C, bool PT, typename I>
+cudaError_t launch_pt(const SearchArgs &a, cudaStream_t st) {
     constexpr int SPAN = 32 * P * Gather<STORAGE>::PIX;
     static_assert(SPAN <= kSpan, "warp span wider than the zero columns");
+    auto kern = search_kernel<STORAGE, P, C, PT, I>;
     dim3 grid((a.W + SPAN - 1) / SPAN, (a.H + WARPS - 1) / WARPS);
     size_t smem = (size_t)TAB * (sizeof(Entry<I>) + sizeof(int)) +
                   (size_t)a.k * THREADS * P * Gather<STORAGE>::PIX * (sizeof(float) + sizeof(uint16_t));
-    cudaError_t err = cudaFuncSetAttribute(search_kernel<STORAGE, P, C, I>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // Shared-memory carveout: it trades resident CTAs against the L1 that the early
     // epochs' gathers reuse across velocities.  Automatic: the driver's choice up to
     // k = 8; longer lists take 58 % (measured on the 12 x 4096^2 workload: k = 12
@@ -360,11 +414,17 @@ cudaError_t launch_one(const SearchArgs &a, cudaStream_t st) {
     int carve = a.carveout;
     if (carve < 0 && a.k > 8) carve = 58;
     if (err == cudaSuccess && carve >= 0)
-        err = cudaFuncSetAttribute(search_kernel<STORAGE, P, C, I>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                   carve);
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
     if (err != cudaSuccess) return err;
-    search_kernel<STORAGE, P, C, I><<<grid, THREADS, smem, st>>>(a);
+    kern<<<grid, THREADS, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// lists longer than 8 take the predicated-remainder form (see min_ctas)
+template <int STORAGE, int P, int C, typename I>
+cudaError_t launch_one(const SearchArgs &a, cudaStream_t st) {
+    if (a.k > 8) return launch_pt<STORAGE, P, C, true, I>(a, st);
+    return launch_pt<STORAGE, P, C, false, I>(a, st);
 }
 
 template <int STORAGE, int P, int C>
@@ -395,12 +455,12 @@ cudaError_t launch_storage(const SearchArgs &a, cudaStream_t st) {
     }
 }
 
-template <int STORAGE, int P, int C, typename I>
-cudaError_t launch_batch_one(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int kmax,
-                             int carve, int sm_count, cudaStream_t st) {
+template <int STORAGE, int P, int C, bool PT, typename I>
+cudaError_t launch_batch_pt(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int kmax,
+                            int carve, int sm_count, cudaStream_t st) {
     size_t smem = (size_t)TAB * (sizeof(Entry<I>) + sizeof(int)) +
                   (size_t)kmax * THREADS * P * Gather<STORAGE>::PIX * (sizeof(float) + sizeof(uint16_t));
-    auto kern = search_batch_kernel<STORAGE, P, C, I>;
+    auto kern = search_batch_kernel<STORAGE, P, C, PT, I>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (carve < 0 && kmax > 8) carve = 58;   // the rule of the one-search launch
     if (err == cudaSuccess && carve >= 0)
@@ -412,6 +472,13 @@ cudaError_t launch_batch_one(const SearchArgs *jobs, const int4 *items, int n_it
     const int grid = sm_count * (per_sm > 0 ? per_sm : 1);
     kern<<<grid, THREADS, smem, st>>>(jobs, items, n_items, counter);
     return cudaGetLastError();
+}
+
+template <int STORAGE, int P, int C, typename I>
+cudaError_t launch_batch_one(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int kmax,
+                             int carve, int sm_count, cudaStream_t st) {
+    if (kmax > 8) return launch_batch_pt<STORAGE, P, C, true, I>(jobs, items, n_items, counter, kmax, carve, sm_count, st);
+    return launch_batch_pt<STORAGE, P, C, false, I>(jobs, items, n_items, counter, kmax, carve, sm_count, st);
 }
 
 template <int STORAGE, int P, int C>

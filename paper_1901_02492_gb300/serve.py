@@ -1,0 +1,261 @@
+"""Serving loop for shift-and-stack searches: continuous admission under an HBM
+budget, device-resident psi/phi while queued, overlapping execution on streams.
+
+A request is one search job (an image stack of any size, epoch count and
+velocity grid).  Its life:
+
+  arrival -> waiting  (host FIFO)
+          -> resident (admitted: its device memory fits the budget; inputs are
+                       uploaded and its psi/phi planes computed on the upload
+                       stream; the planes stay on the device while it queues)
+          -> running  (a compute slot -- a CUDA stream -- is free: search,
+                       optional FP64 rescoring, results to the host)
+          -> done     (its memory and slot are released; waiting requests are
+                       admitted in the same pass)
+
+Admission is first-come first-served on the request's device footprint
+(kb_estimate_bytes: its psi/phi planes and search buffers), so the budget is never exceeded
+and a large request is not starved by smaller ones behind it.  Requests that
+arrive while others run are admitted as soon as memory frees up; their
+kernels overlap on the device with those already running.
+
+The scheduler core (`Scheduler`) knows nothing of CUDA: it drives a backend
+with admit / dispatch / done / finish, so its logic is tested on the CPU with a
+simulated backend; `CudaBackend` runs it through the library's C ABI.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+from typing import Any, Callable, List
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    id: int
+    arrival: float            # seconds after the start of the run
+    N: int
+    H: int
+    W: int
+    K: int                    # PSF side
+    V: int                    # velocities
+    topk: int
+    payload: Any = None       # what the backend needs (images, PSF, times, grid)
+    nbytes: int = 0           # device footprint, set by the backend's estimate
+
+
+@dataclasses.dataclass
+class Completion:
+    id: int
+    arrival: float
+    admitted: float
+    started: float
+    finished: float
+    result: Any = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class Scheduler:
+    """Continuous admission and dispatch of requests onto `slots` compute slots
+    under a device-memory budget of `budget` bytes."""
+
+    def __init__(self, backend, budget: int, slots: int = 4, poll_s: float = 2e-4):
+        self.backend = backend
+        self.budget = int(budget)
+        self.slots = int(slots)
+        self.poll_s = poll_s
+        self.peak_bytes = 0
+
+    def run(self, requests: List[Request], clock: Callable[[], float] = time.perf_counter,
+            sleep: Callable[[float], None] = time.sleep) -> List[Completion]:
+        be = self.backend
+        for r in requests:
+            r.nbytes = be.estimate(r)
+            if r.nbytes > self.budget:
+                raise ValueError("request %d needs %d bytes, more than the whole budget %d"
+                                 % (r.id, r.nbytes, self.budget))
+        pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.id)))
+        waiting: collections.deque = collections.deque()
+        resident: collections.deque = collections.deque()
+        running = {}                                   # slot -> (request, handle, admitted, started)
+        free_slots = list(range(self.slots))[::-1]
+        in_use = 0
+        out: List[Completion] = []
+        t0 = clock()
+        while pending or waiting or resident or running:
+            now = clock() - t0
+            progressed = False
+            while pending and pending[0].arrival <= now:
+                waiting.append(pending.popleft())
+                progressed = True
+            for slot in list(running):
+                r, h, t_adm, t_start = running[slot]
+                if be.done(h):
+                    res = be.finish(h)
+                    t_fin = clock() - t0
+                    out.append(Completion(r.id, r.arrival, t_adm, t_start, t_fin, res))
+                    in_use -= r.nbytes
+                    del running[slot]
+                    free_slots.append(slot)
+                    progressed = True
+            while waiting and in_use + waiting[0].nbytes <= self.budget:
+                r = waiting.popleft()
+                in_use += r.nbytes
+                self.peak_bytes = max(self.peak_bytes, in_use)
+                resident.append((r, be.admit(r), clock() - t0))
+                progressed = True
+            while resident and free_slots:
+                r, h, t_adm = resident.popleft()
+                slot = free_slots.pop()
+                be.dispatch(h, slot)
+                running[slot] = (r, h, t_adm, clock() - t0)
+                progressed = True
+            if not progressed:
+                wait = self.poll_s
+                if pending and not (waiting or resident or running):
+                    wait = max(0.0, min(0.05, pending[0].arrival - (clock() - t0)))
+                sleep(wait)
+        return out
+
+
+def fifo_latencies(arrivals: np.ndarray, service: np.ndarray) -> np.ndarray:
+    """Latencies of a single server that takes requests one at a time in arrival
+    order, each for its measured service time (the serial baseline)."""
+    lat = np.empty(len(arrivals))
+    free_at = 0.0
+    for i, (a, s) in enumerate(zip(arrivals, service)):
+        start = max(a, free_at)
+        free_at = start + s
+        lat[i] = free_at - a
+    return lat
+
+
+def busy_fraction(intervals) -> float:
+    """Fraction of [first start, last end] covered by the union of (start, end) intervals."""
+    iv = sorted(intervals)
+    if not iv:
+        return 0.0
+    total, cur_s, cur_e = 0.0, iv[0][0], iv[0][1]
+    for s, e in iv[1:]:
+        if s > cur_e:
+            total += cur_e - cur_s
+            cur_s, cur_e = s, e
+        else:
+            cur_e = max(cur_e, e)
+    total += cur_e - cur_s
+    span = max(e for _, e in iv) - iv[0][0]
+    return total / span if span > 0 else 0.0
+
+
+class CudaBackend:
+    """Runs requests through the library: kb_stack (psi/phi) on an upload stream,
+    kb_job search (+ FP64 rescoring) and results on one stream per slot.
+
+    A request's payload is a dict with host arrays `sci`, `var` ([>= N][H][W]
+    float32, pinned torch tensors; the first N epochs are used), `psf`
+    ([N][K][K]), `times` [N], `vx`, `vy` [V].  All buffers that outlive a
+    request are allocated up front, so the loop itself allocates only through
+    the library's stream-ordered pool: the device input staging (reused in
+    upload-stream order) and, per slot, a device and a pinned host buffer for
+    the results (kb_result records; returned as [H][W][topk] with keep_results).
+    """
+
+    def __init__(self, ctx, device, storage: str = "bf16", rescore: bool = True, slots: int = 4,
+                 max_npix: int = 1, max_planes: int = 1, max_topk: int = 16, keep_results: bool = False,
+                 time_device: bool = True):
+        import torch
+        from . import binding as kb
+        self.kb, self.torch = kb, torch
+        self.ctx = ctx
+        self.dev = device
+        self.storage = storage
+        self.flags = kb.KB_RESCORE_FP64 if rescore else 0
+        self.keep = keep_results
+        self.time_device = time_device
+        self.upload = torch.cuda.Stream(device)
+        self.streams = [torch.cuda.Stream(device) for _ in range(slots)]
+        self.max_planes = max_planes
+        self.stage = torch.empty(2 * max_planes, dtype=torch.float32, device=device)
+        rb = max_npix * max_topk * kb.RESULT_DTYPE.itemsize
+        self.dev_out = [torch.empty(rb, dtype=torch.uint8, device=device) for _ in range(slots)]
+        self.host_out = [torch.empty(rb, dtype=torch.uint8).pin_memory() for _ in range(slots)]
+        self.ref = torch.cuda.Event(enable_timing=True)
+        self.ref.record(self.upload)
+        self.intervals_ev = []
+        torch.cuda.synchronize(device)
+
+    @property
+    def fixed_bytes(self) -> int:
+        """Device bytes the backend holds outside any request: input staging and result buffers."""
+        return self.stage.numel() * 4 + sum(b.numel() for b in self.dev_out)
+
+    def estimate(self, r: Request) -> int:
+        s, j = self.kb.estimate_bytes(r.N, r.H, r.W, self.storage, r.K, r.V, r.topk, self.flags)
+        return s + j
+
+    def admit(self, r: Request):
+        kb, torch = self.kb, self.torch
+        p = r.payload
+        n = r.N * r.H * r.W
+        if n > self.max_planes or r.H * r.W * r.topk * kb.RESULT_DTYPE.itemsize > self.dev_out[0].numel():
+            raise ValueError("request %d is larger than the backend's staging" % r.id)
+        st = kb.Stack(self.ctx, r.N, r.H, r.W, self.storage)
+        job = kb.Job(self.ctx, r.H, r.W, r.N, r.V, r.topk, self.flags)
+        with torch.cuda.stream(self.upload):
+            sci = self.stage[:n].view(r.N, r.H, r.W)
+            var = self.stage[self.max_planes:self.max_planes + n].view(r.N, r.H, r.W)
+            sci.copy_(p["sci"][:r.N], non_blocking=True)
+            var.copy_(p["var"][:r.N], non_blocking=True)
+            st.make_psi_phi(sci, var, None, p["psf"][:r.N], stream=self.upload)
+            ready = torch.cuda.Event()
+            ready.record(self.upload)
+        return dict(r=r, stack=st, job=job, ready=ready, done=None)
+
+    def dispatch(self, h, slot: int):
+        torch = self.torch
+        r, p = h["r"], h["r"].payload
+        s = self.streams[slot]
+        nbytes = r.H * r.W * r.topk * self.kb.RESULT_DTYPE.itemsize
+        out, host = self.dev_out[slot][:nbytes], self.host_out[slot][:nbytes]
+        s.wait_event(h["ready"])
+        t0 = torch.cuda.Event(enable_timing=True) if self.time_device else None
+        t1 = torch.cuda.Event(enable_timing=True) if self.time_device else None
+        with torch.cuda.stream(s):
+            if t0 is not None:
+                t0.record(s)
+            h["job"].search(h["stack"], p["times"][:r.N], p["vx"], p["vy"], r.topk, -math.inf, self.flags, stream=s)
+            h["job"].results(out, stream=s)
+            host.copy_(out, non_blocking=True)
+            if t1 is not None:
+                t1.record(s)
+            done = torch.cuda.Event()
+            done.record(s)
+        h["done"], h["slot"], h["nbytes"] = done, slot, nbytes
+        if t0 is not None:
+            self.intervals_ev.append((t0, t1))
+
+    def done(self, h) -> bool:
+        return h["done"].query()
+
+    def finish(self, h):
+        h["job"].wait()                       # raises on a device-side status
+        res = None
+        if self.keep:
+            r = h["r"]
+            res = (self.host_out[h["slot"]][:h["nbytes"]].numpy().copy()
+                   .view(self.kb.RESULT_DTYPE).reshape(r.H, r.W, r.topk))
+        h["job"].free()
+        h["stack"].free()
+        return res
+
+    def device_intervals(self):
+        """(start, end) of every dispatched request's device work, seconds after the backend started."""
+        self.torch.cuda.synchronize(self.dev)
+        return [(self.ref.elapsed_time(a) * 1e-3, self.ref.elapsed_time(b) * 1e-3) for a, b in self.intervals_ev]

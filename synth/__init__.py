@@ -259,6 +259,22 @@ def images_device(seed: int, N: int, H: int, W: int, device, var_lo: float = 80.
     return sci, var
 
 
+def serving_meta(job: dict, n_angles: int = 16):
+    """Host part of one serving job: (times [N], psf [N][K][K], vx, vy, k).  Epochs as in the
+    uneven batch (4 visits on the first night, the rest over 1-3 more nights), PSF sigma
+    U[1.2, 2.0] px, a velocity grid of n_angles angles within +-pi/4 of +x times
+    n_velocities // n_angles speeds over 90-550 px/day."""
+    rng = np.random.default_rng(job["seed"])
+    N = job["N"]
+    times = batch_times(N, int(rng.integers(1, 5)), rng)
+    sigma = float(rng.uniform(1.2, 2.0))
+    K = 2 * int(math.ceil(4 * sigma)) + 1
+    psf = np.stack([gaussian_psf(K, sigma)] * N)
+    ns = max(1, job["n_velocities"] // n_angles)
+    vx, vy = velocity_grid(n_angles, ns, -math.pi / 4, math.pi / 4, 90.0, 550.0)
+    return times, psf, vx, vy, job["k"]
+
+
 def serving_jobs(seed: int = 4, count: int = 2000, rate_hz: float = 1.0):
     """Job descriptions for the serving loop: Poisson arrivals, mixed sizes, epochs and grids."""
     rng = np.random.default_rng(seed)

@@ -1,0 +1,129 @@
+"""The serving scheduler's host logic on a simulated backend (no GPU).
+
+The backend simulates a device whose requests each take a fixed service time
+once dispatched and run side by side on the slots; the scheduler is driven by a
+virtual clock.  Checked: the memory budget is never exceeded, admission is in
+arrival order, at most `slots` requests run at once, requests arriving while
+others run are admitted as soon as memory allows, every request completes
+once, and the serial-baseline and busy-fraction arithmetic.
+"""
+import numpy as np
+import pytest
+
+from paper_1901_02492_gb300.serve import Request, Scheduler, busy_fraction, fifo_latencies
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 1e-6)
+
+
+class SimBackend:
+    def __init__(self, clock, service):
+        self.clock, self.service = clock, service
+        self.in_use = 0
+        self.max_in_use = 0
+        self.running = 0
+        self.max_running = 0
+        self.admitted = []
+        self.events = []
+
+    def estimate(self, r):
+        return r.N * r.H * r.W
+
+    def admit(self, r):
+        self.in_use += r.nbytes
+        self.max_in_use = max(self.max_in_use, self.in_use)
+        self.admitted.append(r.id)
+        self.clock.t += 1e-4                      # host cost of an admission
+        return {"r": r}
+
+    def dispatch(self, h, slot):
+        self.running += 1
+        self.max_running = max(self.max_running, self.running)
+        h["end"] = self.clock() + self.service(h["r"])
+        h["slot"] = slot
+
+    def done(self, h):
+        return self.clock() >= h["end"]
+
+    def finish(self, h):
+        self.running -= 1
+        self.in_use -= h["r"].nbytes
+        return h["r"].id
+
+
+def _requests(n, seed=0, rate=50.0):
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    sizes = [(8, 8), (32, 64), (64, 64)]
+    out = []
+    for i in range(n):
+        H, W = sizes[int(rng.integers(0, 3))]
+        out.append(Request(i, float(t[i]), int(rng.integers(5, 16)), H, W, 7, 256, 8))
+    return out
+
+
+@pytest.mark.parametrize("slots,budget", [(1, 70000), (4, 70000), (4, 200000), (8, 61440)])
+def test_budget_slots_and_order(slots, budget):
+    clk = Clock()
+    be = SimBackend(clk, lambda r: 1e-6 * r.H * r.W * r.N / 10)
+    reqs = _requests(300)
+    out = Scheduler(be, budget, slots).run(reqs, clock=clk, sleep=clk.sleep)
+    assert sorted(c.id for c in out) == list(range(300))
+    assert be.max_in_use <= budget
+    assert be.max_running <= slots
+    assert be.admitted == sorted(be.admitted, key=lambda i: (reqs[i].arrival, i))   # FIFO admission
+    for c in out:
+        r = reqs[c.id]
+        assert c.arrival <= c.admitted <= c.started <= c.finished
+        assert c.finished - c.started >= 1e-6 * r.H * r.W * r.N / 10 - 1e-9
+    assert be.in_use == 0 and be.running == 0
+
+
+def test_requests_join_while_others_run():
+    """Continuous batching: a request arriving during a long one starts before it ends."""
+    clk = Clock()
+    long_r = Request(0, 0.0, 10, 64, 64, 7, 256, 8)
+    short = [Request(i, 0.01 * i, 5, 8, 8, 7, 256, 8) for i in range(1, 6)]
+    be = SimBackend(clk, lambda r: 1.0 if r.id == 0 else 0.002)
+    out = {c.id: c for c in Scheduler(be, 10 ** 6, 4).run([long_r] + short, clock=clk, sleep=clk.sleep)}
+    for i in range(1, 6):
+        assert out[i].started < out[0].finished
+        assert out[i].latency < 0.1
+
+
+def test_admission_waits_for_memory_and_does_not_starve_large_requests():
+    clk = Clock()
+    big = Request(1, 0.001, 10, 100, 100, 7, 256, 8)          # 100000 bytes: the whole budget
+    small = [Request(0, 0.0, 5, 10, 10, 7, 256, 8)] + [Request(i, 0.001 + 1e-4 * i, 5, 10, 10, 7, 256, 8)
+                                                        for i in range(2, 30)]
+    be = SimBackend(clk, lambda r: 0.01)
+    out = {c.id: c for c in Scheduler(be, 100000, 4).run([big] + small, clock=clk, sleep=clk.sleep)}
+    assert be.max_in_use <= 100000
+    # the big request waits only for request 0 to leave, and no later small request overtakes it
+    assert out[1].admitted >= out[0].finished
+    assert all(out[i].admitted >= out[1].finished for i in range(2, 30))
+
+
+def test_request_larger_than_budget_is_rejected():
+    clk = Clock()
+    be = SimBackend(clk, lambda r: 0.01)
+    with pytest.raises(ValueError):
+        Scheduler(be, 1000, 2).run([Request(0, 0.0, 10, 64, 64, 7, 256, 8)], clock=clk, sleep=clk.sleep)
+
+
+def test_fifo_latencies_and_busy_fraction():
+    arr = np.array([0.0, 0.5, 0.6, 5.0])
+    svc = np.array([1.0, 1.0, 1.0, 0.5])
+    # starts 0, 1, 2, 5 -> ends 1, 2, 3, 5.5
+    assert np.allclose(fifo_latencies(arr, svc), [1.0, 1.5, 2.4, 0.5])
+    assert busy_fraction([(0, 1), (0.5, 2), (3, 4)]) == pytest.approx(3.0 / 4.0)
+    assert busy_fraction([(0, 1), (1, 2)]) == pytest.approx(1.0)
+    assert busy_fraction([]) == 0.0
