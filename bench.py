@@ -451,12 +451,19 @@ def run_batch(args):
     value = world * evals * args.steps / (ms * 1e-3)
     alg_bytes = evals * BYTES_PER_EVAL[args.storage]
     achieved = alg_bytes / (ms / args.steps * 1e-3) / 1e9
+    # kernels per kb_batch_run: one per persistent group, one per search of a launch group, and the
+    # rescore + repair kernels of each rescored search (groups: searches with the same list length)
+    kkeep = [d["topk"] if not flags else None for d in searches]
+    launches_per_run = sum(1 if g.schedule == 0 else sum(1 for kk in kkeep if kk == g.kmax) for g in groups)
+    launches_per_run += 2 * len(searches) if flags else 0
     cfg = {"workload": "batch of %d uneven stacks, W %d x H %d, 5-20 epochs, 256-2048 velocities, k 4-16"
                        % (len(specs), W, H),
            "stacks": len(specs), "height": H, "width": W, "epochs_total": int(sum(sp["N"] for sp in specs)),
            "evals_per_step": int(evals), "storage": args.storage, "rescore_fp64": bool(args.rescore),
-           "groups": [{"storage": g.storage, "variant": g.variant, "index_bits": g.index_bits, "kmax": g.kmax,
-                       "items": int(g.n_items), "tuned_ms": [round(x, 3) for x in list(g.tuned_ms)[1:]]}
+           "groups": [{"storage": g.storage, "variant": g.variant, "schedule": ["persistent", "launches"][g.schedule],
+                       "index_bits": g.index_bits, "kmax": g.kmax, "items": int(g.n_items),
+                       "tuned_ms_persistent": [round(x, 3) for x in list(g.tuned_ms)[1:]],
+                       "tuned_ms_launches": [round(x, 3) for x in list(g.tuned_ms_launch)[1:]]}
                       for g in groups],
            "autotune_s": round(t_tune, 3), "generate_s": round(t_gen, 1),
            "l2": "inputs larger than L2 (%.1f GB of psi/phi planes)" % (sum(sp["N"] for sp in specs) * H * W * 8 / 1e9),
@@ -473,7 +480,7 @@ def run_batch(args):
             "clocks": clk.summary(), "e2e": None,
             "e2e_note": "inputs of the 64 stacks are drawn on the device; the end-to-end number is on the "
                         "single-stack line",
-            "gpu_launches": args.steps * (len(groups) + (2 * len(specs) if args.rescore else 0))}
+            "gpu_launches": args.steps * launches_per_run}
     if rank == 0:
         print(json.dumps(line), flush=True)
     batch.free()

@@ -256,13 +256,14 @@ int kb_estimate_bytes(int N, int H, int W, int storage, int K, int V, int topk, 
 /* ---- batched searches (no counterpart in the paper: many stacks per launch) ----
  *
  * A batch runs many independent Sec. 2.2 searches, of stacks with different
- * sizes, epoch counts, velocity grids and k, as one persistent launch per group
- * of searches with the same storage, index width and candidate-list length.  The work list holds one
- * item per CTA tile of every search; the resident CTAs take items off it in
- * order of per-tile cost (largest search first).  The launches, and the FP64
- * rescoring of the searches that ask for it, are captured once into a CUDA
- * graph that kb_batch_run replays.  Every search gives the results that
- * kb_search gives for the same arguments. */
+ * sizes, epoch counts, velocity grids and k, grouped by storage, index width and
+ * candidate-list length.  Each group runs with one of two schedules: one
+ * persistent launch whose CTAs take items off a work list (one item per CTA tile
+ * of every search, in order of per-tile cost, largest search first), or one
+ * launch per search.  The launches, and the FP64 rescoring of the searches that
+ * ask for it, are captured once into a CUDA graph that kb_batch_run replays.
+ * Every search gives the results that kb_search gives for the same arguments
+ * and tile shape. */
 typedef struct kb_batch kb_batch;
 
 /* One search of a batch: the arguments of kb_search (same meaning and limits). */
@@ -277,7 +278,7 @@ typedef struct kb_batch_item {
     int flags;              /* KB_RESCORE_FP64 or 0 */
 } kb_batch_item;
 
-#define KB_BATCH_AUTOTUNE 1 /* time every tile shape per group, keep the fastest */
+#define KB_BATCH_AUTOTUNE 1 /* time every tile shape and schedule per group, keep the fastest */
 
 /* The plan of one group (filled by kb_batch_groups). */
 typedef struct kb_batch_group {
@@ -287,7 +288,9 @@ typedef struct kb_batch_group {
     int kmax;               /* candidate-list length of its searches */
     long long n_items;      /* CTA tiles in its work list */
     double evals;           /* trajectory-epoch evaluations of its searches */
-    float tuned_ms[5];      /* autotuner time of shapes 1..4 on its sample (0: not tuned) */
+    float tuned_ms[5];      /* autotuner time of shapes 1..4, persistent schedule, on its sample (0: not tuned) */
+    int schedule;           /* 0: one persistent launch over the group's work list; 1: one launch per search */
+    float tuned_ms_launch[5]; /* autotuner time of shapes 1..4 with one launch per search (0: not tuned) */
 } kb_batch_group;
 
 /* Validate every item, build and upload its tables (host arrays are read before

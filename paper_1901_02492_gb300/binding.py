@@ -294,7 +294,8 @@ class _BatchItem(ctypes.Structure):
 class BatchGroup(ctypes.Structure):
     """kb_batch_group: the plan of one persistent launch of a batch."""
     _fields_ = [("storage", _i32), ("index_bits", _i32), ("variant", _i32), ("kmax", _i32),
-                ("n_items", ctypes.c_longlong), ("evals", ctypes.c_double), ("tuned_ms", _f32 * 5)]
+                ("n_items", ctypes.c_longlong), ("evals", ctypes.c_double), ("tuned_ms", _f32 * 5),
+                ("schedule", _i32), ("tuned_ms_launch", _f32 * 5)]
 
 
 class Batch:

@@ -717,6 +717,8 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
     a.carveout = ctx->search_carveout;
     a.ptab = job->ptab;
     a.status = job->status;
+    a.by0 = 0;
+    a.nby = 0;
     if (rescore) {
         r.f32 = s->f32;
         r.plane_elems = a.plane_elems;
@@ -833,10 +835,29 @@ void make_items(const kb_batch *b, int g, int variant, double frac, std::vector<
     }
 }
 
-cudaError_t launch_group(const kb_batch *b, int g, int variant, int n_items, cudaStream_t st) {
+// One group's searches with tile shape `variant`: schedule 0 runs the persistent
+// kernel over the group's work list (n_items items), schedule 1 launches the
+// one-search kernel per search, over the middle `frac` of its row tiles (the
+// rows make_items takes for the same frac).
+cudaError_t launch_group(const kb_batch *b, int g, int variant, int schedule, int n_items, double frac,
+                         cudaStream_t st) {
     const kb_batch_group &G = b->groups[g];
-    return kb::launch_search_batch(b->d_args, b->group_items[g], n_items, b->d_counters + g, G.storage, variant,
-                                   G.kmax, b->ctx->search_carveout, G.index_bits == 64, b->ctx->sm_count, st);
+    if (schedule == 0)
+        return kb::launch_search_batch(b->d_args, b->group_items[g], n_items, b->d_counters + g, G.storage, variant,
+                                       G.kmax, b->ctx->search_carveout, G.index_bits == 64, b->ctx->sm_count, st);
+    cudaError_t e = cudaSuccess;
+    for (int j : b->group_jobs[g]) {
+        kb::SearchArgs a = b->args[j];
+        a.variant = variant;
+        if (frac < 1.0) {
+            const int ty = (a.H + kb::kTileRows - 1) / kb::kTileRows;
+            a.nby = std::max(1, std::min(ty, (int)std::ceil(ty * frac)));
+            a.by0 = (ty - a.nby) / 2;
+        }
+        e = kb::launch_search(a, st, b->ctx->sm_count);
+        if (e != cudaSuccess) break;
+    }
+    return e;
 }
 
 }  // namespace
@@ -939,10 +960,11 @@ int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flag
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "kb_batch_create upload"));
 
-    // Autotuner: time every tile shape of each group on a band from the middle of
-    // each search's rows (about 4e10 trajectory-epoch evaluations per group, or
-    // everything when smaller) and keep the fastest.  Without it the context's
-    // variant (1..4) or the default shape is used.
+    // Autotuner: time every tile shape, with both schedules (the persistent
+    // work-list kernel and one launch per search), of each group on a band from
+    // the middle of each search's rows (about 4e10 trajectory-epoch evaluations
+    // per group, or everything when smaller) and keep the fastest.  Without it
+    // the context's variant (1..4) or the default shape runs persistent.
     std::vector<int4> host;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (flags & KB_BATCH_AUTOTUNE) {
@@ -955,19 +977,22 @@ int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flag
                 make_items(b, g, v, frac, host);
                 e = cudaMemcpyAsync(b->group_items[g], host.data(), host.size() * sizeof(int4),
                                     cudaMemcpyHostToDevice, b->cap);
-                float ms = 0.0f;
-                for (int rep = (v == 1 ? 0 : 1); rep < 2 && e == cudaSuccess; ++rep) {   // one warm-up run
-                    e = cudaMemsetAsync(b->d_counters + g, 0, sizeof(int), b->cap);
-                    if (e == cudaSuccess) e = cudaEventRecord(t0, b->cap);
-                    if (e == cudaSuccess) e = launch_group(b, g, v, (int)host.size(), b->cap);
-                    if (e == cudaSuccess) e = cudaEventRecord(t1, b->cap);
-                    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-                }
-                b->groups[g].tuned_ms[v] = ms;
-                if (e == cudaSuccess && ms < best) {
-                    best = ms;
-                    b->groups[g].variant = v;
+                for (int sched = 0; sched < 2 && e == cudaSuccess; ++sched) {
+                    float ms = 0.0f;
+                    for (int rep = (v == 1 && sched == 0 ? 0 : 1); rep < 2 && e == cudaSuccess; ++rep) {
+                        e = cudaMemsetAsync(b->d_counters + g, 0, sizeof(int), b->cap);   // rep 0: warm-up
+                        if (e == cudaSuccess) e = cudaEventRecord(t0, b->cap);
+                        if (e == cudaSuccess) e = launch_group(b, g, v, sched, (int)host.size(), frac, b->cap);
+                        if (e == cudaSuccess) e = cudaEventRecord(t1, b->cap);
+                        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                    }
+                    (sched == 0 ? b->groups[g].tuned_ms : b->groups[g].tuned_ms_launch)[v] = ms;
+                    if (e == cudaSuccess && ms < best) {
+                        best = ms;
+                        b->groups[g].variant = v;
+                        b->groups[g].schedule = sched;
+                    }
                 }
             }
         }
@@ -991,7 +1016,7 @@ int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flag
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "kb_batch_create capture"));
     cudaError_t ce = cudaMemsetAsync(b->d_counters, 0, (size_t)G * sizeof(int), b->cap);
     for (int g = 0; g < G && ce == cudaSuccess; ++g)
-        ce = launch_group(b, g, b->groups[g].variant, (int)b->groups[g].n_items, b->cap);
+        ce = launch_group(b, g, b->groups[g].variant, b->groups[g].schedule, (int)b->groups[g].n_items, 1.0, b->cap);
     for (size_t i = 0; i < b->resc.size() && ce == cudaSuccess; ++i) {
         ce = cudaMemsetAsync(b->resc[i].ucount, 0, sizeof(int), b->cap);
         if (ce == cudaSuccess) ce = kb::launch_rescore(b->resc[i], b->cap);

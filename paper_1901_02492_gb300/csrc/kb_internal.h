@@ -171,6 +171,7 @@ struct SearchArgs {
     int carveout;            // preferred shared-memory carveout (percent of the maximum), -1 = automatic
     const uint32_t *ptab;    // [V][N - n0] packed (dx, dy) int16 in processing order (pipelined kernel)
     int *status;             // device status word: KB_ETIMEOUT if a bounded wait gave up
+    int by0, nby;            // register-gather kernel: row tiles by0 .. by0 + nby - 1 (nby 0: all)
 };
 // register-gather kernel (variant 0 = its default shape, 1..4)
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, int sm_count);

@@ -115,6 +115,26 @@ struct Entry {
     int info;
 };
 
+// two consecutive table entries (the first at an even index) in one 16-byte load
+template <typename E>
+__device__ __forceinline__ void load_pair(const E *t, E &a, E &b) {
+    if constexpr (sizeof(E) == 8) {
+        const int4 w = *reinterpret_cast<const int4 *>(t);
+        a.idx = w.x;
+        a.info = w.y;
+        b.idx = w.z;
+        b.info = w.w;
+    } else {
+        a = t[0];
+        b = t[1];
+    }
+}
+
+// with k > 8, a warp's list insertions for one pixel slot are done cooperatively
+// (the whole warp per candidate) when at most this many of its lanes insert, else
+// by each lane alone
+constexpr int kCoopMax = 3;
+
 // One CTA tile (rows by * 8 .. +7, columns bx * SPAN .. +SPAN-1) of one search:
 // the body of both the one-search kernel and the persistent batch kernel.
 template <int STORAGE, int P, int C, bool PT, typename I>
@@ -126,19 +146,27 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     typedef Entry<I> E;
     constexpr int PX = P * G::PIX;    // pixels per lane
     constexpr int SPAN = 32 * PX;     // pixels per warp row segment
-    constexpr int LS = THREADS * PX;  // list stride
+    constexpr int LS = THREADS * PX;  // list columns (pixels) of the CTA
 
     // s_scale: per time-ordered epoch.  s_dyn4: table E [TAB] | velocity ids [TAB] |
-    // list nu float [k][LS] | list vidx u16 [k][LS]
+    // list nu float [KP * LS] | list vidx u16 [KP * LS].  Column c = p * THREADS +
+    // thread holds one pixel's list, best first; slot i of column c is at c * CS + i * IS.
+    //   k <= 8 (PT false): slot-major, CS = 1, IS = LS, KP = k: each lane walks its
+    //     own lists, consecutive lanes in consecutive banks.
+    //   k > 8 (PT true): column-major with an odd stride, CS = KP = k | 1, IS = 1: a
+    //     pixel's slots are contiguous for the warp-cooperative insertion, and lanes
+    //     walking their own lists still hit distinct banks.
     E *s_tab = reinterpret_cast<E *>(s_dyn4);
     int *s_vid = reinterpret_cast<int *>(s_tab + TAB);
-    float *s_ln = reinterpret_cast<float *>(s_vid + TAB);
-    uint16_t *s_lv = reinterpret_cast<uint16_t *>(s_ln + a.k * LS);
-
     const int N = a.N, n0 = a.n0, NJ = N - n0, k = a.k;
+    const int KP = PT ? (a.k | 1) : a.k, CS = PT ? KP : 1, IS = PT ? 1 : LS;
+    const int NJP = PT ? (NJ + 1) & ~1 : NJ;   // table row stride (even where entries are loaded in pairs)
+    float *s_ln = reinterpret_cast<float *>(s_vid + TAB);
+    uint16_t *s_lv = reinterpret_cast<uint16_t *>(s_ln + KP * LS);
+
     for (int j = threadIdx.x; j < N; j += THREADS)
         s_scale[j] = (STORAGE == KB_F32) ? make_float2(1.0f, 1.0f) : exp_scale(scale_exp(a.scales[a.epoch_of[j]]));
-    for (int i = threadIdx.x; i < k * LS; i += THREADS) {
+    for (int i = threadIdx.x; i < KP * LS; i += THREADS) {
         s_ln[i] = -INFINITY;
         s_lv[i] = kNoV;
     }
@@ -174,13 +202,13 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
         }
     }
 
-    const int vchunk = min(a.V, TAB / max(NJ, 1));
+    const int vchunk = min(a.V, TAB / max(NJP, 1));
     for (int c0 = 0; c0 < a.V; c0 += vchunk) {
         const int nc = min(vchunk, a.V - c0);
         __syncthreads();
         for (int i = threadIdx.x; i < nc; i += THREADS) s_vid[i] = a.vorder[c0 + i];
         for (int i = threadIdx.x; i < nc * NJ; i += THREADS) {
-            const int vi = i / NJ, jj = i - vi * NJ;
+            const int vi = i / NJ, jj = i - vi * NJ;   // entry (vi, jj) at vi * NJP + jj
             const int j = n0 + jj;
             const int ep = a.epoch_of[j];
             const int2 o = a.offs[(long long)a.vorder[c0 + vi] * N + j];
@@ -196,13 +224,13 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             E e;
             e.idx = (I)g;
             e.info = mask | ((STORAGE == KB_F32 ? 0 : scale_exp(a.scales[ep])) << 16);
-            s_tab[i] = e;
+            s_tab[vi * NJP + jj] = e;
         }
         __syncthreads();
         if (!active) continue;
         for (int vi = 0; vi < nc; ++vi) {
             const int v = s_vid[vi];
-            const E *tab = s_tab + vi * NJ;
+            const E *tab = s_tab + vi * NJP;
             float2 acc[PX];
 #pragma unroll
             for (int p = 0; p < PX; ++p) acc[p] = acc0[p];
@@ -246,14 +274,21 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
                     LT val[C][P];
                     int sx[C];
 #pragma unroll
-                    for (int q = 0; q < C; ++q) {
+                    for (int q = 0; q < C; q += 2) {
                         if (jj + q < NJ) {
-                            const E t = tab[jj + q];
-                            sx[q] = t.info >> 16;
-                            const LT *src =
-                                ((t.info >> warp) & 1) ? reinterpret_cast<const LT *>(planes + (t.idx + tb)) : zero;
+                            E t[2];
+                            load_pair(tab + jj + q, t[0], t[1]);   // the second may be row padding
 #pragma unroll
-                            for (int p = 0; p < P; ++p) val[q][p] = __ldg(src + 32 * p);
+                            for (int h = 0; h < 2; ++h) {
+                                if (jj + q + h < NJ) {
+                                    sx[q + h] = t[h].info >> 16;
+                                    const LT *src = ((t[h].info >> warp) & 1)
+                                                        ? reinterpret_cast<const LT *>(planes + (t[h].idx + tb))
+                                                        : zero;
+#pragma unroll
+                                    for (int p = 0; p < P; ++p) val[q + h][p] = __ldg(src + 32 * p);
+                                }
+                            }
                         }
                     }
 #pragma unroll
@@ -280,22 +315,66 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             if (!__any_sync(0xffffffffu, any)) continue;
 #pragma unroll
             for (int p = 0; p < PX; ++p) {
-                if (!cand[p]) continue;
-                float *ln = s_ln + p * THREADS + threadIdx.x;
-                uint16_t *lv = s_lv + p * THREADS + threadIdx.x;
-                int i = k - 1;
-                while (i > 0) {
-                    const float pn = ln[(i - 1) * LS];
-                    const int pv = lv[(i - 1) * LS];
-                    if (!better(nu[p], v, pn, pv)) break;
-                    ln[i * LS] = pn;
-                    lv[i * LS] = (uint16_t)pv;
-                    --i;
+                unsigned m = 0;
+                if constexpr (PT) {
+                    m = __ballot_sync(0xffffffffu, cand[p]);
+                    if (m == 0) continue;
                 }
-                ln[i * LS] = nu[p];
-                lv[i * LS] = (uint16_t)v;
-                thn[p] = ln[(k - 1) * LS];
-                thv[p] = lv[(k - 1) * LS];
+                if (!PT || __popc(m) > kCoopMax) {
+                    // each lane inserts into its own list, walking up from the last slot
+                    if (cand[p]) {
+                        float *ln = s_ln + (p * THREADS + threadIdx.x) * CS;
+                        uint16_t *lv = s_lv + (p * THREADS + threadIdx.x) * CS;
+                        int i = k - 1;
+                        while (i > 0) {
+                            const float pn = ln[(i - 1) * IS];
+                            const int pv = lv[(i - 1) * IS];
+                            if (!better(nu[p], v, pn, pv)) break;
+                            ln[i * IS] = pn;
+                            lv[i * IS] = (uint16_t)pv;
+                            --i;
+                        }
+                        ln[i * IS] = nu[p];
+                        lv[i * IS] = (uint16_t)v;
+                        thn[p] = ln[(k - 1) * IS];
+                        thv[p] = lv[(k - 1) * IS];
+                    }
+                } else {
+                    // few lanes: the warp inserts their candidates one at a time, lane j
+                    // holding slot j of the list (one load, one ballot, one store)
+                    do {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1;
+                        const float nn = __shfl_sync(0xffffffffu, nu[p], src);
+                        const int col = p * THREADS + warp * 32 + src;
+                        float *ln = s_ln + col * KP;
+                        uint16_t *lv = s_lv + col * KP;
+                        float en = -INFINITY;
+                        int ev = kNoV;
+                        if (lane < k) {
+                            en = ln[lane];
+                            ev = lv[lane];
+                        }
+                        // first slot the candidate beats (exists: it beats the last slot)
+                        const unsigned bm = __ballot_sync(0xffffffffu, lane < k && better(nn, v, en, ev));
+                        const int pos = __ffs(bm) - 1;
+                        const float upn = __shfl_up_sync(0xffffffffu, en, 1);
+                        const int upv = __shfl_up_sync(0xffffffffu, ev, 1);
+                        const float wn = lane == pos ? nn : (lane > pos ? upn : en);
+                        const int wv = lane == pos ? v : (lane > pos ? upv : ev);
+                        if (lane >= pos && lane < k) {
+                            ln[lane] = wn;
+                            lv[lane] = (uint16_t)wv;
+                        }
+                        const float tn = __shfl_sync(0xffffffffu, wn, k - 1);
+                        const int tv = __shfl_sync(0xffffffffu, wv, k - 1);
+                        if (lane == src) {
+                            thn[p] = tn;
+                            thv[p] = tv;
+                        }
+                    } while (m);
+                }
+                if constexpr (PT) __syncwarp();   // lists written above are read by other lanes later
             }
         }
     }
@@ -308,11 +387,11 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
         const int x = xw + (G::PIX == 1 ? lane + 32 * p : 2 * lane + 64 * (p / 2) + (p & 1));
         if (x >= a.W) continue;
         Rec *out = a.out + ((long long)y * a.W + x) * k;
-        const float *ln = s_ln + p * THREADS + threadIdx.x;
-        const uint16_t *lv = s_lv + p * THREADS + threadIdx.x;
+        const float *ln = s_ln + (p * THREADS + threadIdx.x) * CS;
+        const uint16_t *lv = s_lv + (p * THREADS + threadIdx.x) * CS;
         for (int i = 0; i < k; ++i) {
             Rec r;
-            const int v = lv[i * LS];
+            const int v = lv[i * IS];
             if (v == kNoV) {
                 r.psi = 0.0f;
                 r.phi = 0.0f;
@@ -335,7 +414,7 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
                 }
                 r.psi = acc.x;
                 r.phi = acc.y;
-                r.nu = ln[i * LS];
+                r.nu = ln[i * IS];
                 r.meta = (uint32_t)v | ((uint32_t)nobs << 16);
             }
             reinterpret_cast<uint4 *>(out)[i] = *reinterpret_cast<uint4 *>(&r);
@@ -344,15 +423,15 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
 }
 
 // Resident CTAs per SM the register allocation is held to (0: no hold).  The
-// shapes with one 8-byte load per lane and epoch: with the plain remainder loop
-// (used for k <= 8, where registers decide how many CTAs an SM holds) the 16-bit
-// one is held to 5 (48 registers), which measured faster than 4 despite the L1
-// the fifth CTA displaces, and the FP32 one reaches 48 registers by itself (and
-// spills when held to it); with the predicated remainder (k > 8, where the
-// lists' shared memory limits the SM to 2-3 CTAs) they are held to 3 (85
-// registers).  The wider shapes: 2.  The batch kernel, which keeps its search's
-// arguments in shared memory rather than the parameter bank and so needs more
-// registers, is held to 3 for the narrow shapes and 2 for the wide ones.
+// shapes with one 8-byte load per lane and epoch, with the plain remainder loop
+// (used for k <= 8, where registers decide how many CTAs an SM holds): the
+// 16-bit one is held to 5 (48 registers), which measured faster than 4 despite
+// the L1 the fifth CTA displaces; the FP32 one reaches 48 registers by itself
+// and spills when held to it.  With the predicated remainder (k > 8, where the
+// lists' shared memory limits the SM to 2-3 CTAs): 3 (85 registers).  The wider
+// shapes: 2.  The batch kernel, which keeps its search's arguments in shared
+// memory rather than the parameter bank and so needs more registers, is held to
+// 3 for the narrow shapes and 2 for the wide ones.
 template <int STORAGE, int P, bool PT>
 constexpr int min_ctas() {
     constexpr bool narrow = STORAGE == KB_F32 ? P <= 2 : P <= 1;
@@ -370,7 +449,7 @@ template <int STORAGE, int P, int C, bool PT, typename I>
 __global__ void __launch_bounds__(THREADS, min_ctas<STORAGE, P, PT>()) search_kernel(SearchArgs a) {
     __shared__ float2 s_scale[KB_MAX_EPOCHS];
     extern __shared__ int4 s_dyn4[];
-    search_tile<STORAGE, P, C, PT, I>(a, blockIdx.x, blockIdx.y, s_scale, s_dyn4);
+    search_tile<STORAGE, P, C, PT, I>(a, blockIdx.x, a.by0 + blockIdx.y, s_scale, s_dyn4);
 }
 
 // Persistent batch search: CTAs take (job, tile) work items from an atomic
@@ -403,9 +482,9 @@ cudaError_t launch_pt(const SearchArgs &a, cudaStream_t st) {
     constexpr int SPAN = 32 * P * Gather<STORAGE>::PIX;
     static_assert(SPAN <= kSpan, "warp span wider than the zero columns");
     auto kern = search_kernel<STORAGE, P, C, PT, I>;
-    dim3 grid((a.W + SPAN - 1) / SPAN, (a.H + WARPS - 1) / WARPS);
+    dim3 grid((a.W + SPAN - 1) / SPAN, a.nby > 0 ? a.nby : (a.H + WARPS - 1) / WARPS);
     size_t smem = (size_t)TAB * (sizeof(Entry<I>) + sizeof(int)) +
-                  (size_t)a.k * THREADS * P * Gather<STORAGE>::PIX * (sizeof(float) + sizeof(uint16_t));
+                  (size_t)(PT ? (a.k | 1) : a.k) * THREADS * P * Gather<STORAGE>::PIX * (sizeof(float) + sizeof(uint16_t));
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // Shared-memory carveout: it trades resident CTAs against the L1 that the early
     // epochs' gathers reuse across velocities.  Automatic: the driver's choice up to
@@ -459,7 +538,7 @@ template <int STORAGE, int P, int C, bool PT, typename I>
 cudaError_t launch_batch_pt(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int kmax,
                             int carve, int sm_count, cudaStream_t st) {
     size_t smem = (size_t)TAB * (sizeof(Entry<I>) + sizeof(int)) +
-                  (size_t)kmax * THREADS * P * Gather<STORAGE>::PIX * (sizeof(float) + sizeof(uint16_t));
+                  (size_t)(PT ? (kmax | 1) : kmax) * THREADS * P * Gather<STORAGE>::PIX * (sizeof(float) + sizeof(uint16_t));
     auto kern = search_batch_kernel<STORAGE, P, C, PT, I>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (carve < 0 && kmax > 8) carve = 58;   // the rule of the one-search launch

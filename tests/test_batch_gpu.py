@@ -109,9 +109,10 @@ def test_autotuned_batch_matches_single_searches_and_oracle(kb, ctx, uneven):
     cases, stacks = uneven
     got, groups = _batched(kb, ctx, stacks, cases, autotune=True)
     for g in groups:
-        assert 1 <= g.variant <= 4
-        assert all(g.tuned_ms[v] > 0 for v in range(1, 5))
-        assert g.tuned_ms[g.variant] == min(g.tuned_ms[1:5])
+        assert 1 <= g.variant <= 4 and g.schedule in (0, 1)
+        assert all(g.tuned_ms[v] > 0 and g.tuned_ms_launch[v] > 0 for v in range(1, 5))
+        chosen = (g.tuned_ms_launch if g.schedule else g.tuned_ms)[g.variant]
+        assert chosen == min(min(g.tuned_ms[1:5]), min(g.tuned_ms_launch[1:5]))
         assert g.n_items > 0 and g.evals > 0
     shape_of = {(g.storage, g.kmax): g.variant for g in groups}
     names = {"f32": 0, "bf16": 1, "f16": 2}

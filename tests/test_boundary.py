@@ -54,7 +54,8 @@ def test_result_struct_layout_matches_binding(tmp_path):
 
 def test_batch_struct_layouts_match_binding(tmp_path, lib):
     fields = {"kb_batch_item": ["job", "stack", "times", "vx", "vy", "V", "topk", "nu_min", "flags"],
-              "kb_batch_group": ["storage", "index_bits", "variant", "kmax", "n_items", "evals", "tuned_ms"]}
+              "kb_batch_group": ["storage", "index_bits", "variant", "kmax", "n_items", "evals", "tuned_ms",
+                                 "schedule", "tuned_ms_launch"]}
     body = ""
     for name, fs in fields.items():
         body += 'printf("%%zu", sizeof(%s));' % name
