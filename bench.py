@@ -61,10 +61,20 @@ def parse():
 
 
 def dist_info():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1901_02492_gb300 import replicas
+    return replicas.dist_info()
+
+
+def setup_device(world, local):
+    """One process per GPU: bind this rank's device and join the (NCCL) group when N > 1."""
+    import torch
+    from paper_1901_02492_gb300 import replicas
+    if world > 1:
+        torch.cuda.set_device(local)
+        replicas.init("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    return dev
 
 
 def workload(size):
@@ -228,13 +238,9 @@ def run_reference(args):
 
 def run_ours(args):
     import torch
+    from paper_1901_02492_gb300 import replicas
     rank, world, local = dist_info()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
+    dev = setup_device(world, local)
     import __graft_entry__
     __graft_entry__.build()
     from paper_1901_02492_gb300 import binding as kb
@@ -275,8 +281,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize(dev)
     timers = [[ev(), ev(), ev()] for _ in range(args.steps)]
     with ClockSampler(dev.index) as clk:
@@ -286,8 +291,7 @@ def run_ours(args):
             step(timers[i])
         t1.record(stream)
         torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize(dev)
     ms = t0.elapsed_time(t1)
     repaired = job.repaired() if args.rescore else 0
@@ -309,13 +313,10 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         if i > 0:
             e2e_ms.append(1e3 * (time.perf_counter() - a))
-    e2e_ms = float(np.mean(e2e_ms))
+    e2e_ms = float(np.mean(e2e_ms)) if e2e_ms else float("nan")
 
-    # max over ranks
-    if world > 1:
-        t = torch.tensor([ms, e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = t.tolist()
+    # the slowest rank's times (replicas: every rank searched its own copy of the stack)
+    ms, e2e_ms = replicas.max_over_ranks([ms, e2e_ms], device=dev)
     value = world * evals * args.steps / (ms * 1e-3)
     peaks = measured_peaks()
 
@@ -363,8 +364,7 @@ def run_ours(args):
     job.free()
     stack.free()
     ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finish()
 
 
 def run_batch(args):
@@ -374,13 +374,9 @@ def run_batch(args):
     Beside it: the same searches as a loop of single kb_search calls."""
     import torch
     import synth
+    from paper_1901_02492_gb300 import replicas
     rank, world, local = dist_info()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
+    dev = setup_device(world, local)
     import __graft_entry__
     __graft_entry__.build()
     from paper_1901_02492_gb300 import binding as kb
@@ -430,8 +426,7 @@ def run_batch(args):
     for _ in range(args.warmup):
         batch.run(stream)
     torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(dev.index) as clk:
         t0, t1 = ev(), ev()
@@ -440,14 +435,10 @@ def run_batch(args):
             batch.run(stream)
         t1.record(stream)
         torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize(dev)
     ms = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = replicas.max_over_ranks([ms], device=dev)[0]
     value = world * evals * args.steps / (ms * 1e-3)
     alg_bytes = evals * BYTES_PER_EVAL[args.storage]
     achieved = alg_bytes / (ms / args.steps * 1e-3) / 1e9
@@ -489,8 +480,7 @@ def run_batch(args):
     for s in stacks:
         s.free()
     ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finish()
 
 
 def run_serve(args):
@@ -502,13 +492,9 @@ def run_serve(args):
     queued first-come first-served on the same arrival times."""
     import torch
     import synth
+    from paper_1901_02492_gb300 import replicas
     rank, world, local = dist_info()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
+    dev = setup_device(world, local)
     import __graft_entry__
     __graft_entry__.build()
     from paper_1901_02492_gb300 import binding as kb
@@ -614,8 +600,7 @@ def run_serve(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finish()
 
 
 def main():

@@ -49,86 +49,198 @@ __device__ __forceinline__ float2 weighted(float n, float v, uint8_t m, float br
     return make_float2(nw, w);
 }
 
-template <bool SEP>
+// Stages the CTA's input tile plus halo as (n w, w) pairs, zero outside the
+// image: warps take rows (two at a time), lanes run along a row in chunks of 32
+// (coalesced, no index division).  All loads of the two rows are issued before
+// any is used, so up to 2 x 4 image/variance pairs per lane are in flight.
+__device__ __forceinline__ void stage_tile(const PsiPhiArgs &a, int e, int x0, int y0, int r, int AW, int AH,
+                                           float2 *A) {
+    constexpr int WARPS = THREADS / 32, CH = 4;     // AW = TX + 2r <= 64 + 62 < 32 * CH
+    const size_t npix = (size_t)a.H * a.W;
+    const float *sci = a.sci + e * npix;
+    const float *var = a.var + e * npix;
+    const uint8_t *msk = a.mask ? a.mask + e * npix : nullptr;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int ty0 = warp; ty0 < AH; ty0 += 2 * WARPS) {
+        float n[2][CH], v[2][CH];
+        uint8_t m[2][CH];
+        bool in[2][CH];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ty = ty0 + h * WARPS, y = y0 - r + ty;
+            const bool rowin = ty < AH && y >= 0 && y < a.H;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int tx = lane + 32 * c, x = x0 - r + tx;
+                in[h][c] = rowin && tx < AW && x >= 0 && x < a.W;
+                n[h][c] = 0.0f;
+                v[h][c] = 0.0f;
+                m[h][c] = 0;
+                if (in[h][c]) {
+                    const size_t gi = (size_t)y * a.W + x;
+                    n[h][c] = __ldg(sci + gi);
+                    v[h][c] = __ldg(var + gi);
+                    if (msk) m[h][c] = __ldg(msk + gi);
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ty = ty0 + h * WARPS;
+            if (ty >= AH) continue;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int tx = lane + 32 * c;
+                if (tx < AW)
+                    A[ty * AW + tx] = in[h][c] ? weighted(n[h][c], v[h][c], m[h][c], a.bright_max)
+                                               : make_float2(0.0f, 0.0f);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void track_max(const PsiPhiArgs &a, float2 o, float &mpsi, float &mphi) {
+    mpsi = fmaxf(mpsi, fabsf(o.x));
+    mphi = fmaxf(mphi, o.y);
+}
+
+// Separable PSF T(dy, dx) = a(dy) b(dx), KT taps (KT = 0: the runtime K).  The
+// horizontal pass writes B (AH x TX); the vertical pass gives each thread one
+// column and VR consecutive output rows, so one shared load of B feeds up to VR
+// outputs.  Every output sums its taps in tap order with one packed FMA each,
+// whatever KT, so all instantiations give identical results.
+constexpr int VR = 8;
+template <int KT>
+__global__ void __launch_bounds__(THREADS) psi_phi_sep_kernel(PsiPhiArgs a) {
+    extern __shared__ float4 smem_raw[];
+    const int K = KT > 0 ? KT : a.K, r = K / 2;
+    const int e = blockIdx.z;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int AW = TX + 2 * r, AH = TY + 2 * r;
+
+    // shared layout: taps (a, a^2)[K] vertical, then (b, b^2)[K] horizontal | A (AH x AW) | B (AH x TX)
+    float *s_taps = reinterpret_cast<float *>(smem_raw);
+    const int ntaps = 4 * K;
+    float2 *A = reinterpret_cast<float2 *>(s_taps + ((ntaps + 3) & ~3));
+    float2 *B = A + AH * AW;
+    const float *taps = a.taps + (size_t)e * ntaps;
+    for (int i = threadIdx.x; i < ntaps; i += THREADS) s_taps[i] = taps[i];
+    stage_tile(a, e, x0, y0, r, AW, AH, A);
+    __syncthreads();
+
+    const float2 *ta = reinterpret_cast<const float2 *>(s_taps), *tb = ta + K;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (KT > 0) {
+        // one warp per row, each lane two adjacent outputs c, c + 1 from the K + 1 inputs
+        // A[c .. c + K], read as (K + 1) / 2 aligned 16-byte loads (AW and c are even)
+        static_assert(TX == 64, "a warp covers one row of TX outputs in pairs");
+        for (int ty = warp; ty < AH; ty += THREADS / 32) {
+            const int c = 2 * lane;
+            const float4 *row = reinterpret_cast<const float4 *>(A + ty * AW + c);
+            float2 in[KT + 1];
+#pragma unroll
+            for (int j = 0; j < (KT + 1) / 2; ++j) {
+                const float4 q = row[j];
+                in[2 * j] = make_float2(q.x, q.y);
+                in[2 * j + 1] = make_float2(q.z, q.w);
+            }
+            float2 h0 = make_float2(0.0f, 0.0f), h1 = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int d = 0; d < KT; ++d) {
+                h0 = fma2(in[d], tb[d], h0);
+                h1 = fma2(in[d + 1], tb[d], h1);
+            }
+            reinterpret_cast<float4 *>(B + ty * TX + c)[0] = make_float4(h0.x, h0.y, h1.x, h1.y);
+        }
+    } else {
+        for (int ty = warp; ty < AH; ty += THREADS / 32) {
+            for (int c = lane; c < TX; c += 32) {
+                const float2 *row = A + ty * AW + c;
+                float2 h = make_float2(0.0f, 0.0f);
+                for (int d = 0; d < K; ++d) h = fma2(row[d], tb[d], h);
+                B[ty * TX + c] = h;
+            }
+        }
+    }
+    __syncthreads();
+
+    float2 *out = a.out + e * a.plane_elems + a.origin;
+    float mpsi = 0.0f, mphi = 0.0f;
+    constexpr int GROUPS = THREADS / TX;            // row groups of VR rows, one column per thread
+    const int c = threadIdx.x % TX, g = threadIdx.x / TX;
+    const int x = x0 + c;
+    for (int row0 = g * VR; row0 < TY; row0 += GROUPS * VR) {
+        float2 o[VR];
+#pragma unroll
+        for (int q = 0; q < VR; ++q) o[q] = make_float2(0.0f, 0.0f);
+        if constexpr (KT > 0) {
+            // input row row0 + d feeds output q with tap d - q
+#pragma unroll
+            for (int d = 0; d < KT + VR - 1; ++d) {
+                const float2 v = B[(row0 + d) * TX + c];
+#pragma unroll
+                for (int q = 0; q < VR; ++q)
+                    if (d - q >= 0 && d - q < KT) o[q] = fma2(v, ta[d - q], o[q]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < VR; ++q)
+                for (int d = 0; d < K; ++d) o[q] = fma2(B[(row0 + q + d) * TX + c], ta[d], o[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < VR; ++q) {
+            const int y = y0 + row0 + q;
+            if (y < a.H && x < a.W) {
+                out[(long long)y * a.pitch + x] = o[q];
+                track_max(a, o[q], mpsi, mphi);
+            }
+        }
+    }
+    if (a.maxbits) {
+        // non-negative floats order like their bit patterns
+        unsigned bp = __reduce_max_sync(0xffffffffu, __float_as_uint(mpsi));
+        unsigned bf = __reduce_max_sync(0xffffffffu, __float_as_uint(mphi));
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(a.maxbits + 2 * e, bp);
+            atomicMax(a.maxbits + 2 * e + 1, bf);
+        }
+    }
+}
+
+// General PSF: one pass over the K x K taps (the single-pass form of Sec. 2.3).
 __global__ void __launch_bounds__(THREADS) psi_phi_kernel(PsiPhiArgs a) {
     extern __shared__ float4 smem_raw[];
     const int K = a.K, r = K / 2;
     const int e = blockIdx.z;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int AW = TX + 2 * r, AH = TY + 2 * r;
-    const size_t npix = (size_t)a.H * a.W;
-
-    // shared layout: taps | A (AH x AW pairs) | B (AH x TX pairs, separable only)
+    // shared layout: taps (T, T^2)[K*K] row-major (dy, dx) | A (AH x AW)
     float *s_taps = reinterpret_cast<float *>(smem_raw);
-    const int ntaps = SEP ? 4 * K : 2 * K * K;
-    const int taps_pad = (ntaps + 3) & ~3;
-    float2 *A = reinterpret_cast<float2 *>(s_taps + taps_pad);
-    float2 *B = A + AH * AW;
-
+    const int ntaps = 2 * K * K;
+    float2 *A = reinterpret_cast<float2 *>(s_taps + ((ntaps + 3) & ~3));
     const float *taps = a.taps + (size_t)e * ntaps;
     for (int i = threadIdx.x; i < ntaps; i += THREADS) s_taps[i] = taps[i];
-
-    const float *sci = a.sci + e * npix;
-    const float *var = a.var + e * npix;
-    const uint8_t *msk = a.mask ? a.mask + e * npix : nullptr;
-    for (int i = threadIdx.x; i < AH * AW; i += THREADS) {
-        int ty = i / AW, tx = i - ty * AW;
-        int y = y0 - r + ty, x = x0 - r + tx;
-        float2 v = make_float2(0.0f, 0.0f);
-        if (y >= 0 && y < a.H && x >= 0 && x < a.W) {
-            size_t gi = (size_t)y * a.W + x;
-            v = weighted(__ldg(sci + gi), __ldg(var + gi), msk ? __ldg(msk + gi) : (uint8_t)0, a.bright_max);
-        }
-        A[i] = v;
-    }
+    stage_tile(a, e, x0, y0, r, AW, AH, A);
     __syncthreads();
 
     float2 *out = a.out + e * a.plane_elems + a.origin;
     float mpsi = 0.0f, mphi = 0.0f;
-    if (SEP) {
-        // taps: (a, a^2)[K] vertical, then (b, b^2)[K] horizontal, as float pairs
-        const float2 *ta = reinterpret_cast<const float2 *>(s_taps), *tb = ta + K;
-        for (int i = threadIdx.x; i < AH * TX; i += THREADS) {
-            int ty = i / TX, c = i - ty * TX;
-            const float2 *row = A + ty * AW + c;
-            float2 h = make_float2(0.0f, 0.0f);
-            for (int d = 0; d < K; ++d) h = fma2(row[d], tb[d], h);
-            B[i] = h;
+    const float2 *t = reinterpret_cast<const float2 *>(s_taps);
+    for (int i = threadIdx.x; i < TY * TX; i += THREADS) {
+        int ty = i / TX, c = i - ty * TX;
+        int y = y0 + ty, x = x0 + c;
+        float2 o = make_float2(0.0f, 0.0f);
+        for (int dy = 0; dy < K; ++dy) {
+            const float2 *row = A + (ty + dy) * AW + c;
+            const float2 *k = t + dy * K;
+            for (int dx = 0; dx < K; ++dx) o = fma2(row[dx], k[dx], o);
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < TY * TX; i += THREADS) {
-            int ty = i / TX, c = i - ty * TX;
-            int y = y0 + ty, x = x0 + c;
-            const float2 *col = B + ty * TX + c;
-            float2 o = make_float2(0.0f, 0.0f);
-            for (int d = 0; d < K; ++d) o = fma2(col[d * TX], ta[d], o);
-            if (y < a.H && x < a.W) {
-                out[(long long)y * a.pitch + x] = o;
-                mpsi = fmaxf(mpsi, fabsf(o.x));
-                mphi = fmaxf(mphi, o.y);
-            }
-        }
-    } else {
-        // taps: (T, T^2)[K*K] as float pairs, row-major (dy, dx)
-        const float2 *t = reinterpret_cast<const float2 *>(s_taps);
-        for (int i = threadIdx.x; i < TY * TX; i += THREADS) {
-            int ty = i / TX, c = i - ty * TX;
-            int y = y0 + ty, x = x0 + c;
-            float2 o = make_float2(0.0f, 0.0f);
-            for (int dy = 0; dy < K; ++dy) {
-                const float2 *row = A + (ty + dy) * AW + c;
-                const float2 *k = t + dy * K;
-                for (int dx = 0; dx < K; ++dx) o = fma2(row[dx], k[dx], o);
-            }
-            if (y < a.H && x < a.W) {
-                out[(long long)y * a.pitch + x] = o;
-                mpsi = fmaxf(mpsi, fabsf(o.x));
-                mphi = fmaxf(mphi, o.y);
-            }
+        if (y < a.H && x < a.W) {
+            out[(long long)y * a.pitch + x] = o;
+            track_max(a, o, mpsi, mphi);
         }
     }
     if (a.maxbits) {
-        // non-negative floats order like their bit patterns
         unsigned bp = __reduce_max_sync(0xffffffffu, __float_as_uint(mpsi));
         unsigned bf = __reduce_max_sync(0xffffffffu, __float_as_uint(mphi));
         if ((threadIdx.x & 31) == 0) {
@@ -201,19 +313,36 @@ static size_t psi_phi_smem(int K, bool sep) {
     return taps + A + B;
 }
 
+template <int KT>
+cudaError_t launch_sep(const PsiPhiArgs &a, dim3 grid, size_t smem, cudaStream_t st) {
+    cudaError_t err = cudaFuncSetAttribute(psi_phi_sep_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    psi_phi_sep_kernel<KT><<<grid, THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_psi_phi(const PsiPhiArgs &a, cudaStream_t st) {
     dim3 grid((a.W + TX - 1) / TX, (a.H + TY - 1) / TY, a.N);
     size_t smem = psi_phi_smem(a.K, a.separable);
-    cudaError_t err;
     if (a.separable) {
-        err = cudaFuncSetAttribute(psi_phi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        psi_phi_kernel<true><<<grid, THREADS, smem, st>>>(a);
-    } else {
-        err = cudaFuncSetAttribute(psi_phi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        psi_phi_kernel<false><<<grid, THREADS, smem, st>>>(a);
+        switch (a.K) {   // the PSF sides of the workloads get fully unrolled taps
+            case 3: return launch_sep<3>(a, grid, smem, st);
+            case 5: return launch_sep<5>(a, grid, smem, st);
+            case 7: return launch_sep<7>(a, grid, smem, st);
+            case 9: return launch_sep<9>(a, grid, smem, st);
+            case 11: return launch_sep<11>(a, grid, smem, st);
+            case 13: return launch_sep<13>(a, grid, smem, st);
+            case 15: return launch_sep<15>(a, grid, smem, st);
+            case 17: return launch_sep<17>(a, grid, smem, st);
+            case 19: return launch_sep<19>(a, grid, smem, st);
+            case 21: return launch_sep<21>(a, grid, smem, st);
+            default: return launch_sep<0>(a, grid, smem, st);
+        }
     }
+    cudaError_t err = cudaFuncSetAttribute(psi_phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    psi_phi_kernel<<<grid, THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }
 

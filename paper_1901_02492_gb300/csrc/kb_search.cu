@@ -160,7 +160,7 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     int *s_vid = reinterpret_cast<int *>(s_tab + TAB);
     const int N = a.N, n0 = a.n0, NJ = N - n0, k = a.k;
     const int KP = PT ? (a.k | 1) : a.k, CS = PT ? KP : 1, IS = PT ? 1 : LS;
-    const int NJP = PT ? (NJ + 1) & ~1 : NJ;   // table row stride (even where entries are loaded in pairs)
+    const int NJP = (NJ + 1) & ~1;   // table row stride: even, so entries pair into 16-byte loads
     float *s_ln = reinterpret_cast<float *>(s_vid + TAB);
     uint16_t *s_lv = reinterpret_cast<uint16_t *>(s_ln + KP * LS);
 
@@ -241,13 +241,24 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
                     LT val[C][P];
                     int sx[C];
 #pragma unroll
-                    for (int q = 0; q < C; ++q) {
-                        const E t = tab[jj + q];
-                        sx[q] = t.info >> 16;
-                        const LT *src =
-                            ((t.info >> warp) & 1) ? reinterpret_cast<const LT *>(planes + (t.idx + tb)) : zero;
+                    for (int q = 0; q < C; q += 2) {
+                        // entries in pairs (one 16-byte shared load) for FP32; the 16-bit
+                        // kernels, held to 48 registers, spill with the pair live and load singly
+                        E t[2];
+                        if constexpr (STORAGE == KB_F32) {
+                            load_pair(tab + jj + q, t[0], t[1]);
+                        } else {
+                            t[0] = tab[jj + q];
+                            t[1] = tab[jj + q + 1];
+                        }
 #pragma unroll
-                        for (int p = 0; p < P; ++p) val[q][p] = __ldg(src + 32 * p);
+                        for (int h = 0; h < 2; ++h) {
+                            sx[q + h] = t[h].info >> 16;
+                            const LT *src = ((t[h].info >> warp) & 1)
+                                                ? reinterpret_cast<const LT *>(planes + (t[h].idx + tb)) : zero;
+#pragma unroll
+                            for (int p = 0; p < P; ++p) val[q + h][p] = __ldg(src + 32 * p);
+                        }
                     }
 #pragma unroll
                     for (int q = 0; q < C; ++q) {

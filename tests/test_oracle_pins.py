@@ -6,6 +6,7 @@ rational arithmetic, a distributional law, a different formulation (numpy
 slicing) or brute-force enumeration.
 """
 import math
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -362,3 +363,66 @@ def test_search_from_images_matches_planes():
     b = oracle.search_pixels_from_images(st.sci, st.var, st.mask, st.psf, st.times, dx, dy, 6, px, py)
     assert np.array_equal(a["vidx"], b["vidx"]) and np.array_equal(a["nobs"], b["nobs"])
     np.testing.assert_allclose(a["nu"][a["vidx"] >= 0], b["nu"][b["vidx"] >= 0], rtol=1e-12)
+
+
+def _read_golden(name):
+    """Parse a hand-worked fixture of tests/golden (format described in the file)."""
+    from fractions import Fraction
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    d = dict(images=[], mask=[], velocities=[], trajectories=[], topk=[])
+    cur = None
+    for raw in open(path):
+        line = raw.split("#")[0].strip()
+        if not line:
+            continue
+        tok = line.split()
+        if tok[0] == "times":
+            d["times"] = [float(t) for t in tok[1:]]
+        elif tok[0] == "variance":
+            d["variance"] = [float(t) for t in tok[1:]]
+        elif tok[0] == "psf":
+            d["psf"] = float(tok[1])
+        elif tok[0] == "image":
+            cur = []
+            d["images"].append(cur)
+        elif tok[0] == "mask":
+            d["mask"].append(tuple(int(t) for t in tok[1:]))
+        elif tok[0] == "velocity":
+            d["velocities"].append((float(tok[2]), float(tok[3])))
+        elif tok[0] == "trajectory":
+            d["trajectories"].append((int(tok[1]), int(tok[2]), int(tok[3]), Fraction(tok[4]), Fraction(tok[5]),
+                                      int(tok[6])))
+        elif tok[0] == "topk":
+            d["topk"].append((int(tok[1]), int(tok[2]), [int(t) for t in tok[3:]]))
+        else:
+            cur.append([float(t) for t in tok])
+    return d
+
+
+def test_hand_worked_coadd_example():
+    """Sec. 2.1.5 / 2.2 on a hand-worked 3-epoch stack (tests/golden/coadd_hand_example.txt):
+    exact Psi, Phi and nobs of ten trajectories (masked pixel, trajectories leaving the
+    image, half-pixel offsets in both directions) and the top-k order of one start pixel."""
+    d = _read_golden("coadd_hand_example.txt")
+    sci = np.array(d["images"], np.float32)
+    N, H, W = sci.shape
+    var = np.stack([np.full((H, W), v, np.float32) for v in d["variance"]])
+    mask = np.zeros((N, H, W), np.uint8)
+    for e, x, y in d["mask"]:
+        mask[e, y, x] = 1
+    psf = np.full((N, 1, 1), d["psf"], np.float32)
+    vx = np.array([v[0] for v in d["velocities"]])
+    vy = np.array([v[1] for v in d["velocities"]])
+    times = np.array(d["times"])
+    psi, phi = oracle.psi_phi(sci, var, mask, psf)
+    dx, dy = oracle.offsets(times, vx, vy)
+    for x0, y0, v, P, F, nobs in d["trajectories"]:
+        Pg, Fg, Ng = oracle.sums_one_velocity(psi, phi, times, dx[v], dy[v])
+        assert Pg[y0, x0] == float(P) and Fg[y0, x0] == float(F) and Ng[y0, x0] == nobs, (x0, y0, v)
+    for x0, y0, order in d["topk"]:
+        rec = oracle.search_pixels(psi, phi, times, dx, dy, len(order), np.array([x0]), np.array([y0]))[0]
+        assert list(rec["vidx"]) == order
+        for r in rec:
+            P, F = [(t[3], t[4]) for t in d["trajectories"] if (t[0], t[1], t[2]) == (x0, y0, r["vidx"])][0]
+            assert r["nu"] == pytest.approx(float(P) / math.sqrt(float(F)), rel=1e-15)
+            assert r["alpha"] == pytest.approx(float(P / F), rel=1e-15)
