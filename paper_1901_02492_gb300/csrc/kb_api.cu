@@ -264,6 +264,13 @@ const char *kb_last_error(const kb_ctx *ctx) { return ctx ? ctx->err.c_str() : "
 
 size_t kb_hbm_in_use(const kb_ctx *ctx) { return ctx ? ctx->in_use : 0; }
 
+int kb_set_search_waves(kb_ctx *ctx, int waves) {
+    if (!ctx) return KB_EINVAL;
+    if (waves < -1 || waves > 1024) return fail(ctx, KB_EINVAL, "waves %d not in -1..1024", waves);
+    ctx->search_waves = waves;
+    return KB_OK;
+}
+
 int kb_set_search_carveout(kb_ctx *ctx, int percent) {
     if (!ctx) return KB_EINVAL;
     if (percent < -1 || percent > 100) return fail(ctx, KB_EINVAL, "carveout %d not in -1..100", percent);
@@ -719,6 +726,7 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
     a.status = job->status;
     a.by0 = 0;
     a.nby = 0;
+    a.waves = ctx->search_waves < 0 ? 0 : ctx->search_waves;
     if (rescore) {
         r.f32 = s->f32;
         r.plane_elems = a.plane_elems;

@@ -66,6 +66,26 @@ __device__ __forceinline__ bool better64(double an, int av, double bn, int bv) {
     return an > bn || (an == bn && av < bv);
 }
 
+// FP64 nu of a coadd, Psi / sqrt(Phi) as Psi * rsqrt(Phi) (CUDA's double rsqrt):
+// one reciprocal square root instead of a correctly rounded square root and a
+// division, which on this GPU's narrow FP64 pipe cost several times more.  Equal
+// sums still give equal nu, so exact ties keep breaking by velocity index.
+__device__ __forceinline__ double nu64(double P, double F) { return P * rsqrt(F); }
+
+// Order-preserving integer key of a double (-inf < ... < +inf; NaN never occurs
+// here): comparisons of the running lists run on the integer pipe, not the FP64 one.
+__device__ __forceinline__ unsigned long long okey(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+__device__ __forceinline__ double okey_value(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffULL) : ~k));
+}
+// (key desc, vidx asc): the same order as better64 on the doubles the keys encode
+__device__ __forceinline__ bool betterk(unsigned long long ak, int av, unsigned long long bk, int bv) {
+    return ak > bk || (ak == bk && av < bv);
+}
+
 // One thread per start pixel: FP64 sums of the kc candidates, re-ranking, and the
 // certificate.  A trajectory outside the candidate list had a 16-bit score at
 // most nu16 of the last candidate; the pixel is certified when the k-th
@@ -80,11 +100,12 @@ __global__ void rescore_kernel(RescoreArgs a) {
     for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix;
          pix += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(pix / a.W), x = (int)(pix - (long long)y * a.W);
-        double ln[K], lp[K], lf[K];
+        double lp[K], lf[K];
+        unsigned long long lk[K];   // nu as its order key
         int lv[K], lo[K];
 #pragma unroll
         for (int i = 0; i < K; ++i) {
-            ln[i] = -INFINITY;
+            lk[i] = okey(-INFINITY);
             lp[i] = 0.0;
             lf[i] = 0.0;
             lv[i] = INT_MAX;
@@ -104,24 +125,28 @@ __global__ void rescore_kernel(RescoreArgs a) {
             int nobs;
             traj64(a, x, y, (int)v, P, F, nobs);
             if (!(F > 0.0)) continue;
-            double nu = P / sqrt(F);
+            const double nu = nu64(P, F);
             emax = fmax(emax, fabs(nu - (double)rc.nu));
             if (!(nu >= a.nu_min)) continue;
             ++n;
-            // bubble the candidate down the sorted register list (nu desc, vidx asc)
+            // bubble the candidate down the sorted register list (nu desc, vidx asc),
+            // comparing integer keys; skipped when it does not beat the last entry
+            unsigned long long ck = okey(nu);
             int cv = (int)v, co = nobs;
+            if (!betterk(ck, cv, lk[K - 1], lv[K - 1])) continue;
             double cp = P, cf = F;
 #pragma unroll
             for (int i = 0; i < K; ++i) {
-                const bool sw = better64(nu, cv, ln[i], lv[i]);
-                const double tn = ln[i], tp = lp[i], tf = lf[i];
+                const bool sw = betterk(ck, cv, lk[i], lv[i]);
+                const double tp = lp[i], tf = lf[i];
+                const unsigned long long tk = lk[i];
                 const int tv = lv[i], to = lo[i];
-                ln[i] = sw ? nu : tn;
+                lk[i] = sw ? ck : tk;
                 lp[i] = sw ? cp : tp;
                 lf[i] = sw ? cf : tf;
                 lv[i] = sw ? cv : tv;
                 lo[i] = sw ? co : to;
-                nu = sw ? tn : nu;
+                ck = sw ? tk : ck;
                 cp = sw ? tp : cp;
                 cf = sw ? tf : cf;
                 cv = sw ? tv : cv;
@@ -136,7 +161,7 @@ __global__ void rescore_kernel(RescoreArgs a) {
             if (lv[i] != INT_MAX) {
                 r.psi = lp[i];
                 r.phi = lf[i];
-                r.nu = ln[i];
+                r.nu = okey_value(lk[i]);
                 r.vidx = (uint32_t)lv[i];
                 r.nobs = (uint32_t)lo[i];
             } else {
@@ -152,7 +177,7 @@ __global__ void rescore_kernel(RescoreArgs a) {
             double bar = a.nu_min;
 #pragma unroll
             for (int i = 0; i < K; ++i)
-                if (i == a.k - 1 && n >= a.k) bar = ln[i];
+                if (i == a.k - 1 && n >= a.k) bar = okey_value(lk[i]);
             const double margin = 2.0 * emax + a.unit * (1.0 + fabs((double)nu16_last));
             if (!((double)nu16_last + margin < bar)) {
                 const int slot = atomicAdd(a.ucount, 1);
@@ -181,7 +206,7 @@ __global__ void repair_kernel(RescoreArgs a) {
             int nobs;
             traj64(a, x, y, v, P, F, nobs);
             if (!(F > 0.0)) continue;
-            const double nu = P / sqrt(F);
+            const double nu = nu64(P, F);
             if (!(nu >= a.nu_min)) continue;
             if (n == a.k && !better64(nu, v, ln[n - 1], lv[n - 1])) continue;
             int i = (n < a.k) ? n++ : a.k - 1;

@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(THREADS, min_ctas_batch<STORAGE, P>()) search_
 }
 
 template <int STORAGE, int P, int C, bool PT, typename I>
-cudaError_t launch_pt(const SearchArgs &a, cudaStream_t st) {
+cudaError_t launch_pt(const SearchArgs &a, cudaStream_t st, int sm_count) {
     constexpr int SPAN = 32 * P * Gather<STORAGE>::PIX;
     static_assert(SPAN <= kSpan, "warp span wider than the zero columns");
     auto kern = search_kernel<STORAGE, P, C, PT, I>;
@@ -506,41 +506,54 @@ cudaError_t launch_pt(const SearchArgs &a, cudaStream_t st) {
     if (err == cudaSuccess && carve >= 0)
         err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
     if (err != cudaSuccess) return err;
-    kern<<<grid, THREADS, smem, st>>>(a);
-    return cudaGetLastError();
+    int per_sm = 0;
+    if (a.waves > 0) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+    if (err != cudaSuccess) return err;
+    // bands of `waves` resident waves of CTAs, one launch each (see kb_set_search_waves)
+    const int band = per_sm > 0 ? max(1, (int)((long long)a.waves * per_sm * sm_count / grid.x)) : (int)grid.y;
+    const int by_end = a.by0 + (int)grid.y;
+    for (int b0 = a.by0; b0 < by_end; b0 += band) {
+        SearchArgs ab = a;
+        ab.by0 = b0;
+        ab.nby = min(band, by_end - b0);
+        kern<<<dim3(grid.x, ab.nby), THREADS, smem, st>>>(ab);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
 }
 
 // lists longer than 8 take the predicated-remainder form (see min_ctas)
 template <int STORAGE, int P, int C, typename I>
-cudaError_t launch_one(const SearchArgs &a, cudaStream_t st) {
-    if (a.k > 8) return launch_pt<STORAGE, P, C, true, I>(a, st);
-    return launch_pt<STORAGE, P, C, false, I>(a, st);
+cudaError_t launch_one(const SearchArgs &a, cudaStream_t st, int sm_count) {
+    if (a.k > 8) return launch_pt<STORAGE, P, C, true, I>(a, st, sm_count);
+    return launch_pt<STORAGE, P, C, false, I>(a, st, sm_count);
 }
 
 template <int STORAGE, int P, int C>
-cudaError_t launch_idx(const SearchArgs &a, cudaStream_t st) {
+cudaError_t launch_idx(const SearchArgs &a, cudaStream_t st, int sm_count) {
     // 32-bit element offsets when every plane of both phases fits
     const long long span = (STORAGE == KB_F32 ? 1LL : 2LL) * a.N * a.plane_elems;
-    if (span < (1LL << 31) - 1) return launch_one<STORAGE, P, C, int>(a, st);
-    return launch_one<STORAGE, P, C, long long>(a, st);
+    if (span < (1LL << 31) - 1) return launch_one<STORAGE, P, C, int>(a, st, sm_count);
+    return launch_one<STORAGE, P, C, long long>(a, st, sm_count);
 }
 
 // Shapes: (loads per lane P, epochs per load batch C); a 16-bit load is two pixels.
 template <int STORAGE>
-cudaError_t launch_storage(const SearchArgs &a, cudaStream_t st) {
+cudaError_t launch_storage(const SearchArgs &a, cudaStream_t st, int sm_count) {
     if constexpr (STORAGE == KB_F32) {
         switch (a.variant) {
-            case 1: return launch_idx<STORAGE, 4, 4>(a, st);
-            case 2: return launch_idx<STORAGE, 2, 4>(a, st);
-            case 3: return launch_idx<STORAGE, 4, 8>(a, st);
-            default: return launch_idx<STORAGE, 2, 8>(a, st);
+            case 1: return launch_idx<STORAGE, 4, 4>(a, st, sm_count);
+            case 2: return launch_idx<STORAGE, 2, 4>(a, st, sm_count);
+            case 3: return launch_idx<STORAGE, 4, 8>(a, st, sm_count);
+            default: return launch_idx<STORAGE, 2, 8>(a, st, sm_count);
         }
     } else {
         switch (a.variant) {
-            case 1: return launch_idx<STORAGE, 2, 4>(a, st);
-            case 2: return launch_idx<STORAGE, 1, 4>(a, st);
-            case 3: return launch_idx<STORAGE, 2, 8>(a, st);
-            default: return launch_idx<STORAGE, 1, 8>(a, st);
+            case 1: return launch_idx<STORAGE, 2, 4>(a, st, sm_count);
+            case 2: return launch_idx<STORAGE, 1, 4>(a, st, sm_count);
+            case 3: return launch_idx<STORAGE, 2, 8>(a, st, sm_count);
+            default: return launch_idx<STORAGE, 1, 8>(a, st, sm_count);
         }
     }
 }
@@ -618,11 +631,11 @@ cudaError_t launch_search_batch(const SearchArgs *jobs, const int4 *items, int n
     }
 }
 
-cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, int /*sm_count*/) {
+cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, int sm_count) {
     switch (a.storage) {
-        case KB_F32: return launch_storage<KB_F32>(a, st);
-        case KB_BF16: return launch_storage<KB_BF16>(a, st);
-        case KB_F16: return launch_storage<KB_F16>(a, st);
+        case KB_F32: return launch_storage<KB_F32>(a, st, sm_count);
+        case KB_BF16: return launch_storage<KB_BF16>(a, st, sm_count);
+        case KB_F16: return launch_storage<KB_F16>(a, st, sm_count);
         default: return cudaErrorInvalidValue;
     }
 }
