@@ -249,7 +249,8 @@ int kb_job_repaired(kb_job *job, size_t *n_pixels);
 /* Write the job's results as kb_result records, [H][W][topk] in start-pixel
  * row-major order, best first within a pixel.  out is a host or device pointer
  * with room for `capacity` records; a host destination makes the call wait for
- * the stream.  KB_ERANGE (with *n_written = H*W*topk) if capacity is too small. */
+ * the stream (host records go through device staging in chunks of 2^22 and
+ * copies).  KB_ERANGE (with *n_written = H*W*topk) if capacity is too small. */
 int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream);
 
 /* Device bytes that one search will hold, for admission under an HBM budget:

@@ -129,6 +129,7 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+
 // ---- fixed-point trajectory offsets (see include/kb.h) ----------------------
 constexpr int64_t kVelOne = 1LL << 16;    // v_q units per px/day
 constexpr int64_t kTimeOne = 1LL << 20;   // t_q units per day
@@ -812,6 +813,8 @@ struct kb_batch {
     int *d_counters = nullptr;                // one per group
     int4 *d_items = nullptr;
     cudaStream_t cap = nullptr;
+    cudaStream_t cap2 = nullptr;              // second branch of the launch schedule
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     size_t bytes = 0;
@@ -844,16 +847,19 @@ void make_items(const kb_batch *b, int g, int variant, double frac, std::vector<
 }
 
 // One group's searches with tile shape `variant`: schedule 0 runs the persistent
-// kernel over the group's work list (n_items items), schedule 1 launches the
-// one-search kernel per search, over the middle `frac` of its row tiles (the
-// rows make_items takes for the same frac).
+// kernel over the group's work list (n_items items) on `st`; schedule 1 launches
+// the one-search kernel per search, over the middle `frac` of its row tiles (the
+// rows make_items takes for the same frac), alternating between `st` and `st2`
+// so that one search's CTAs start while the previous one drains.  The caller
+// orders st2 after st before and joins it back after.
 cudaError_t launch_group(const kb_batch *b, int g, int variant, int schedule, int n_items, double frac,
-                         cudaStream_t st) {
+                         cudaStream_t st, cudaStream_t st2) {
     const kb_batch_group &G = b->groups[g];
     if (schedule == 0)
         return kb::launch_search_batch(b->d_args, b->group_items[g], n_items, b->d_counters + g, G.storage, variant,
                                        G.kmax, b->ctx->search_carveout, G.index_bits == 64, b->ctx->sm_count, st);
     cudaError_t e = cudaSuccess;
+    int n = 0;
     for (int j : b->group_jobs[g]) {
         kb::SearchArgs a = b->args[j];
         a.variant = variant;
@@ -862,10 +868,16 @@ cudaError_t launch_group(const kb_batch *b, int g, int variant, int schedule, in
             a.nby = std::max(1, std::min(ty, (int)std::ceil(ty * frac)));
             a.by0 = (ty - a.nby) / 2;
         }
-        e = kb::launch_search(a, st, b->ctx->sm_count);
+        e = kb::launch_search(a, (n++ & 1) ? st2 : st, b->ctx->sm_count);
         if (e != cudaSuccess) break;
     }
     return e;
+}
+
+// st2 waits for everything issued to st so far (fork), or st for st2 (join)
+cudaError_t order_after(cudaStream_t waiter, cudaStream_t on, cudaEvent_t ev) {
+    cudaError_t e = cudaEventRecord(ev, on);
+    return e == cudaSuccess ? cudaStreamWaitEvent(waiter, ev, 0) : e;
 }
 
 }  // namespace
@@ -892,6 +904,9 @@ int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flag
         return rc;
     };
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "kb_batch_create"));
 
     // tables of every search, uploaded on the batch's stream
@@ -990,7 +1005,10 @@ int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flag
                     for (int rep = (v == 1 && sched == 0 ? 0 : 1); rep < 2 && e == cudaSuccess; ++rep) {
                         e = cudaMemsetAsync(b->d_counters + g, 0, sizeof(int), b->cap);   // rep 0: warm-up
                         if (e == cudaSuccess) e = cudaEventRecord(t0, b->cap);
-                        if (e == cudaSuccess) e = launch_group(b, g, v, sched, (int)host.size(), frac, b->cap);
+                        if (e == cudaSuccess) e = order_after(b->cap2, b->cap, b->fork);
+                        if (e == cudaSuccess)
+                            e = launch_group(b, g, v, sched, (int)host.size(), frac, b->cap, b->cap2);
+                        if (e == cudaSuccess) e = order_after(b->cap, b->cap2, b->join);
                         if (e == cudaSuccess) e = cudaEventRecord(t1, b->cap);
                         if (e == cudaSuccess) e = cudaEventSynchronize(t1);
                         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
@@ -1023,8 +1041,11 @@ int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flag
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "kb_batch_create capture"));
     cudaError_t ce = cudaMemsetAsync(b->d_counters, 0, (size_t)G * sizeof(int), b->cap);
+    if (ce == cudaSuccess) ce = order_after(b->cap2, b->cap, b->fork);
     for (int g = 0; g < G && ce == cudaSuccess; ++g)
-        ce = launch_group(b, g, b->groups[g].variant, b->groups[g].schedule, (int)b->groups[g].n_items, 1.0, b->cap);
+        ce = launch_group(b, g, b->groups[g].variant, b->groups[g].schedule, (int)b->groups[g].n_items, 1.0, b->cap,
+                          b->cap2);
+    if (ce == cudaSuccess) ce = order_after(b->cap, b->cap2, b->join);
     for (size_t i = 0; i < b->resc.size() && ce == cudaSuccess; ++i) {
         ce = cudaMemsetAsync(b->resc[i].ucount, 0, sizeof(int), b->cap);
         if (ce == cudaSuccess) ce = kb::launch_rescore(b->resc[i], b->cap);
@@ -1066,9 +1087,13 @@ void kb_batch_free(kb_batch *b) {
         if (j->done) cudaEventSynchronize(j->done);
         j->owner = nullptr;
     }
+    if (b->cap2) cudaStreamSynchronize(b->cap2);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->cap2) cudaStreamDestroy(b->cap2);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     dev_free(b->ctx, b->d_args);
     dev_free(b->ctx, b->d_counters);
     dev_free(b->ctx, b->d_items);

@@ -179,6 +179,11 @@ def test_results_to_device_buffer(kb, ctx):
     torch.cuda.synchronize()
     devh = dev.cpu().numpy().view(kb.RESULT_DTYPE).reshape(H, W, 4)
     assert np.array_equal(host, devh)
+    # page-locked host memory is written by the GPU directly: the same records
+    pinned = torch.zeros(H * W * 4 * kb.RESULT_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    pin_np = pinned.numpy().view(kb.RESULT_DTYPE)
+    job.results(pin_np)
+    assert np.array_equal(host.ravel(), pin_np)
     # re-running the same job with a different k and grid reuses its buffers
     job.search(s, st.times, st.vx[:10], st.vy[:10], 2)
     again = job.results()
