@@ -103,9 +103,10 @@ def workload_config(args, st, world):
 
 class ClockSampler:
     def __init__(self, gpu_index):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                 ".bench_clocks_%d.csv" % os.getpid())
+        fd, self.path = tempfile.mkstemp(prefix="bench_clocks_", suffix=".csv")
+        os.close(fd)
         self.gpu = gpu_index
 
     def __enter__(self):
@@ -602,7 +603,8 @@ def run_serve(args):
                     "h2d_bytes_per_step": int(sum(2 * 4 * jobs[c.id]["N"] * jobs[c.id]["H"] * jobs[c.id]["W"]
                                                   for c in done)),
                     "d2h_bytes_per_step": int(sum(48 * 8 * jobs[c.id]["H"] * jobs[c.id]["W"] for c in done))},
-            "gpu_launches": None}
+            # per job: psi/phi, quantize, search, rescore, repair, expand (results to the device buffer)
+            "gpu_launches": 6 * len(done)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -17,7 +17,7 @@
  *   scores             Sec. 2.1.5: alpha_ML = Psi / Phi, nu = Psi / sqrt(Phi)
  *   search             Sec. 2.2: evaluate nu for every start pixel and velocity
  *
- * Readings of points the paper leaves open (all listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - a pixel is masked when its mask byte is non-zero, when n or sigma^2 is not
  *     finite, when sigma^2 <= 0, or when n exceeds the optional bright-pixel
  *     limit (Sec. 5.2); masked pixels get weight 0 and contribute exactly 0;

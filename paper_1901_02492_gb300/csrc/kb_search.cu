@@ -8,12 +8,18 @@
 // Work decomposition (GB300-first, not the paper's 32x16 thread blocks):
 //   - a CTA owns 8 rows x SPAN columns of start pixels, one warp per row; a lane
 //     owns P loads' worth of pixels (FP32: pixel lane + 32 p; 16-bit: the pixel
-//     pair 2 lane + 64 p, + 1) and runs the whole velocity loop for them, so the
-//     per-pixel top-k is private to a lane (threshold in registers, list of
-//     (nu, 16-bit velocity index) in shared memory) and no cross-thread merge is
-//     needed.  Shared memory per CTA is kept small: the kernel is latency-bound
-//     (resident warps set its throughput) and the SRAM left to L1 serves the
-//     early epochs' gathers, which neighbouring velocities share;
+//     pair 2 lane + 64 p, + 1) and runs the whole velocity loop for them.  The
+//     admission threshold of each pixel's top-k (its k-th (nu, vidx)) is in
+//     registers, the list of (nu, 16-bit velocity index) in shared memory.
+//     Shared memory per CTA is kept small: the kernel is latency-bound (resident
+//     warps set its throughput) and the SRAM left to L1 serves the early epochs'
+//     gathers, which neighbouring velocities share;
+//   - k <= 8: slot-major lists, each lane inserting into its own pixels' lists.
+//     k > 8: pixel-major lists with an odd stride (k | 1), and when at most
+//     kCoopMax lanes of a warp have a candidate for one pixel slot the warp
+//     inserts each cooperatively (lane j holds slot j: one load, one ballot, one
+//     shifted store) instead of one lane walking a long list while the others
+//     wait; the epochs' last, partial load batch is predicated (one round trip);
 //   - for one (velocity, epoch) a warp's loads cover SPAN consecutive pixels of
 //     one plane row: fully coalesced 8-byte loads.  16-bit pairs are 8-byte
 //     aligned because the planes also exist shifted by one pixel (the "phase 1"
@@ -22,8 +28,9 @@
 //     there once: each entry holds the element offset of the shifted row start
 //     (epoch plane and phase included), a mask of the CTA's warps whose shifted
 //     span overlaps the image, and the epoch's power-of-two scale exponents.
-//     The inner loop is one broadcast load, one bit test, a select, the
-//     gathers and one packed f32x2 accumulate per pixel;
+//     The inner loop is one broadcast load (a 16-byte pair of entries for FP32
+//     and k > 8), one bit test, a select, the gathers and one packed f32x2
+//     accumulate per pixel (16-bit: one mixed-precision FMA per value);
 //   - spans that overlap the image only partly read the zero columns the planes
 //     carry left and right of every row (kSpan wide); spans that miss it read a
 //     small zero block that stays in L1, so off-image steps cost no memory
