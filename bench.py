@@ -347,7 +347,7 @@ def run_ours(args):
                          "peak_source": "measured in this run by kb_measure_gather_peak: L2-resident 256-byte "
                                         "warp-span loads (the search's access form), no HBM or L1 term",
                          "ms_per_launch": ms_search, "alg_bytes_per_launch": alg_bytes},
-            "roofline_psi_phi": {"bound": "hbm", "kernel": "psi_phi_kernel", "ms_per_launch": ms_psiphi,
+            "roofline_psi_phi": {"bound": "hbm", "kernel": "psi_phi_sep_kernel", "ms_per_launch": ms_psiphi,
                                  "achieved": psiphi_bytes / (ms_psiphi * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                                  "frac": psiphi_bytes / (ms_psiphi * 1e-3) / 1e9 / hbm,
                                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
