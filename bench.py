@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--serve-load", type=float, default=0.8, help="target GPU busy fraction of the arrival rate")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-policy", default="sjf", choices=["fifo", "sjf"],
+                    help="dispatch order of resident jobs: arrival order, or least work first with aging")
     return ap.parse_args()
 
 
@@ -541,7 +543,7 @@ def run_serve(args):
                                  max_planes=max_planes, max_topk=8)
 
     be = backend(args.storage if args.storage != "f32" else "bf16", True, args.serve_slots)
-    sched = serve.Scheduler(be, budget - be.fixed_bytes, args.serve_slots)
+    sched = serve.Scheduler(be, budget - be.fixed_bytes, args.serve_slots, policy=args.serve_policy)
     # warm-up and capacity: a saturated sample of the job mix (all arriving at once)
     sample = list(range(min(len(jobs), 48)))
     sched.run(requests(None, sample[:6]))
@@ -588,6 +590,7 @@ def run_serve(args):
             "config": {"workload": "serving: %d Poisson-arrival jobs of 512^2, 4096x2048, 4096^2 px, 5-15 epochs, "
                                    "256-1024 velocities, k=8, BF16 + FP64 rescoring" % len(jobs),
                        "jobs": len(jobs), "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb,
+                       "dispatch_policy": args.serve_policy,
                        "arrival_rate_hz": rate, "capacity_jobs_s": cap_jobs_s, "target_load": args.serve_load,
                        "inputs": "pinned host stacks per size class (drawn on the device), copied to the device "
                                  "per job", "generate_s": round(t_gen, 1), "parallelism": "replicas%d" % world},

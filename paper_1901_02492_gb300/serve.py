@@ -64,14 +64,36 @@ class Completion:
 
 class Scheduler:
     """Continuous admission and dispatch of requests onto `slots` compute slots
-    under a device-memory budget of `budget` bytes."""
+    under a device-memory budget of `budget` bytes.
 
-    def __init__(self, backend, budget: int, slots: int = 4, poll_s: float = 2e-4):
+    Admission to device memory is first-come first-served.  Dispatch of resident
+    requests to a free slot follows `policy`:
+      "fifo"  in admission order;
+      "sjf"   least work first (trajectory-epoch evaluations N H W V), except that
+              a request resident for longer than `max_wait` seconds goes first
+              (oldest first), so large requests are delayed, never starved."""
+
+    def __init__(self, backend, budget: int, slots: int = 4, poll_s: float = 2e-4, policy: str = "fifo",
+                 max_wait: float = 2.0):
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("unknown policy %r" % policy)
         self.backend = backend
         self.budget = int(budget)
         self.slots = int(slots)
         self.poll_s = poll_s
+        self.policy = policy
+        self.max_wait = float(max_wait)
         self.peak_bytes = 0
+
+    def _next(self, resident, now):
+        """Index in `resident` of the request to dispatch next."""
+        if self.policy == "fifo":
+            return 0
+        overdue = [i for i, (r, h, t_adm) in enumerate(resident) if now - t_adm > self.max_wait]
+        if overdue:
+            return overdue[0]
+        return min(range(len(resident)), key=lambda i: (work(resident[i][0]), resident[i][0].arrival,
+                                                         resident[i][0].id))
 
     def run(self, requests: List[Request], clock: Callable[[], float] = time.perf_counter,
             sleep: Callable[[float], None] = time.sleep) -> List[Completion]:
@@ -112,7 +134,9 @@ class Scheduler:
                 resident.append((r, be.admit(r), clock() - t0))
                 progressed = True
             while resident and free_slots:
-                r, h, t_adm = resident.popleft()
+                i = self._next(resident, clock() - t0)
+                r, h, t_adm = resident[i]
+                del resident[i]
                 slot = free_slots.pop()
                 be.dispatch(h, slot)
                 running[slot] = (r, h, t_adm, clock() - t0)
@@ -123,6 +147,11 @@ class Scheduler:
                     wait = max(0.0, min(0.05, pending[0].arrival - (clock() - t0)))
                 sleep(wait)
         return out
+
+
+def work(r: Request) -> int:
+    """Trajectory-epoch evaluations of a request's search."""
+    return r.N * r.H * r.W * r.V
 
 
 def fifo_latencies(arrivals: np.ndarray, service: np.ndarray) -> np.ndarray:
