@@ -59,11 +59,13 @@ def parse():
                          "serve: a Poisson stream of search jobs through the serving loop")
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--serve-jobs", type=int, default=2000)
-    ap.add_argument("--serve-load", type=float, default=0.8, help="target GPU busy fraction of the arrival rate")
+    ap.add_argument("--serve-load", type=float, default=0.75,
+                    help="arrival rate as a fraction of the capacity measured on a saturated sample")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
-    ap.add_argument("--serve-policy", default="sjf", choices=["fifo", "sjf"],
-                    help="dispatch order of resident jobs: arrival order, or least work first with aging")
+    ap.add_argument("--serve-policy", default="both", choices=["fifo", "sjf", "both"],
+                    help="dispatch order of resident jobs: arrival order, least work first with aging, or "
+                         "both in turn on the same arrivals (the line reports the last, sjf)")
     return ap.parse_args()
 
 
@@ -543,24 +545,34 @@ def run_serve(args):
                                  max_planes=max_planes, max_topk=8)
 
     be = backend(args.storage if args.storage != "f32" else "bf16", True, args.serve_slots)
-    sched = serve.Scheduler(be, budget - be.fixed_bytes, args.serve_slots, policy=args.serve_policy)
-    # warm-up and capacity: a saturated sample of the job mix (all arriving at once)
-    sample = list(range(min(len(jobs), 48)))
-    sched.run(requests(None, sample[:6]))
+    # warm-up, then capacity: a saturated sample of the job mix (all arriving at once), dispatched in
+    # arrival order whatever the policy under test, so that every policy sees the same arrival rate
+    calib = serve.Scheduler(be, budget - be.fixed_bytes, args.serve_slots, policy="fifo")
+    sample = list(range(min(len(jobs), 300)))
+    calib.run(requests(None, sample[:6]))
     t0 = time.perf_counter()
-    sched.run(requests(None, sample))
-    cap_jobs_s = len(sample) / (time.perf_counter() - t0)
+    calib.run(requests(None, sample))
+    # capacity in evaluations per second (the sample's job mix need not match the stream's), turned
+    # into jobs per second with the whole stream's mean work per job
+    cap_evals_s = sum(evals[i] for i in sample) / (time.perf_counter() - t0)
+    cap_jobs_s = cap_evals_s / (sum(evals.values()) / len(jobs))
     rate = args.serve_load * cap_jobs_s
-    be.intervals_ev.clear()
-    with ClockSampler(dev.index) as clk:
-        t0 = time.perf_counter()
-        done = sched.run(requests(rate))
-        wall = time.perf_counter() - t0
-    lat = np.array([c.latency for c in done])
-    busy = serve.busy_fraction(be.device_intervals())
+    policies = ["fifo", "sjf"] if args.serve_policy == "both" else [args.serve_policy]
+    served = {}
+    for pol in policies:
+        sched = serve.Scheduler(be, budget - be.fixed_bytes, args.serve_slots, policy=pol)
+        be.intervals_ev.clear()
+        with ClockSampler(dev.index) as clk:
+            t0 = time.perf_counter()
+            done = sched.run(requests(rate))
+            wall = time.perf_counter() - t0
+        lat = np.array([c.latency for c in done])
+        served[pol] = dict(done=done, wall=wall, lat=lat, busy=serve.busy_fraction(be.device_intervals()),
+                           peak=sched.peak_bytes + be.fixed_bytes, clocks=clk.summary())
+    main = served[policies[-1]]
+    done, wall, lat = main["done"], main["wall"], main["lat"]
     total_evals = sum(evals[c.id] for c in done)
-    peak = sched.peak_bytes + be.fixed_bytes
-    del be, sched
+    del be
     torch.cuda.synchronize(dev)
 
     # the serial plain-FP32 loop: one job at a time, service time measured per job
@@ -590,18 +602,21 @@ def run_serve(args):
             "config": {"workload": "serving: %d Poisson-arrival jobs of 512^2, 4096x2048, 4096^2 px, 5-15 epochs, "
                                    "256-1024 velocities, k=8, BF16 + FP64 rescoring" % len(jobs),
                        "jobs": len(jobs), "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb,
-                       "dispatch_policy": args.serve_policy,
+                       "dispatch_policy": policies[-1],
                        "arrival_rate_hz": rate, "capacity_jobs_s": cap_jobs_s, "target_load": args.serve_load,
                        "inputs": "pinned host stacks per size class (drawn on the device), copied to the device "
                                  "per job", "generate_s": round(t_gen, 1), "parallelism": "replicas%d" % world},
             "serving": {"p50_s": pct(lat, 50), "p99_s": pct(lat, 99), "mean_s": float(lat.mean()),
-                        "jobs_per_s": len(done) / wall, "gpu_busy_fraction": busy,
-                        "peak_device_bytes": int(peak)},
+                        "jobs_per_s": len(done) / wall, "gpu_busy_fraction": main["busy"],
+                        "peak_device_bytes": int(main["peak"])},
+            "serving_by_policy": {pol: {"p50_s": pct(v["lat"], 50), "p99_s": pct(v["lat"], 99),
+                                        "mean_s": float(v["lat"].mean()), "jobs_per_s": len(v["done"]) / v["wall"],
+                                        "gpu_busy_fraction": v["busy"]} for pol, v in served.items()},
             "serial_fp32": {"p50_s": pct(ser_lat, 50), "p99_s": pct(ser_lat, 99),
                             "jobs_per_s": len(reqs) / float(svc.sum()),
                             "evals_per_s": sum(evals.values()) / float(svc.sum()),
                             "mean_service_s": float(svc.mean())},
-            "clocks": clk.summary(),
+            "clocks": main["clocks"],
             "e2e": {"value": total_evals / wall, "unit": "evals/s",
                     "h2d_bytes_per_step": int(sum(2 * 4 * jobs[c.id]["N"] * jobs[c.id]["H"] * jobs[c.id]["W"]
                                                   for c in done)),

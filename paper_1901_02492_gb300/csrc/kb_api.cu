@@ -310,12 +310,11 @@ int kb_stack_create(kb_ctx *ctx, int N, int H, int W, int storage, kb_stack **ou
         rc = dev_alloc(ctx, (size_t)2 * N * plane * sizeof(kb::pair16), (void **)&s->q16, &s->bytes);
     if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)N * sizeof(float2), (void **)&s->scales, &s->bytes);
     if (rc == KB_OK) rc = dev_alloc(ctx, (size_t)2 * N * sizeof(unsigned), (void **)&s->maxbits, &s->bytes);
+    // The planes are cleared by the first kb_make_psi_phi, on its stream: a memset
+    // here would run on the library's internal stream and queue behind whatever
+    // kernels other streams have on the device.
     cudaError_t e = cudaSuccess;
-    if (rc == KB_OK) e = cudaMemsetAsync(s->f32, 0, (size_t)N * plane * sizeof(float2), ctx->astream);
-    if (rc == KB_OK && e == cudaSuccess && s->q16)
-        e = cudaMemsetAsync(s->q16, 0, (size_t)2 * N * plane * sizeof(kb::pair16), ctx->astream);
-    if (rc == KB_OK && e == cudaSuccess) e = cudaStreamSynchronize(ctx->astream);
-    if (rc == KB_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&s->taps_done, cudaEventDisableTiming);
+    if (rc == KB_OK) e = cudaEventCreateWithFlags(&s->taps_done, cudaEventDisableTiming);
     if (rc == KB_OK && e == cudaSuccess) e = cudaEventCreateWithFlags(&s->used, cudaEventDisableTiming);
     if (rc == KB_OK && e != cudaSuccess) rc = cuda_fail(ctx, e, "kb_stack_create");
     if (rc != KB_OK) {
@@ -408,7 +407,14 @@ int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8
             }
         }
     }
-    cudaError_t e = cudaMemcpyAsync(s->taps, th, nt * sizeof(float), cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaSuccess;
+    if (!s->zeroed) {
+        // once per stack: the zero borders (psi/phi only write the image's pixels); the
+        // 16-bit copies are written whole by the quantize kernel
+        e = cudaMemsetAsync(s->f32, 0, (size_t)N * s->L.plane_elems * sizeof(float2), st);
+        if (e == cudaSuccess) s->zeroed = true;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->taps, th, nt * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(s->taps_done, st);
     bool q = s->q16 != nullptr;
     if (e == cudaSuccess && q) e = cudaMemsetAsync(s->maxbits, 0, 2 * N * sizeof(unsigned), st);
@@ -446,6 +452,7 @@ int kb_stack_copy_planes(const kb_stack *s, int which, void *dst, size_t dst_byt
     if (!s) return KB_EINVAL;
     kb_ctx *ctx = s->ctx;
     if (!dst) return fail(ctx, KB_EINVAL, "kb_stack_copy_planes: dst is NULL");
+    if (!s->filled) return fail(ctx, KB_EINVAL, "kb_stack_copy_planes: the stack has no psi/phi yet");
     const void *src = which == 0 ? (const void *)s->f32 : (const void *)s->q16;
     size_t elem = which == 0 ? sizeof(float2) : sizeof(kb::pair16);
     if ((which != 0 && which != 1) || !src) return fail(ctx, KB_EINVAL, "stack has no planes of kind %d", which);
@@ -579,13 +586,20 @@ int kb_job_create(kb_ctx *ctx, int H, int W, int N, int V, int topk, int flags, 
     if (rc == KB_OK && (flags & KB_RESCORE_FP64)) rc = dev_alloc(ctx, npix * sizeof(int), (void **)&j->ulist, &j->bytes);
     if (rc == KB_OK && (flags & KB_RESCORE_FP64)) rc = dev_alloc(ctx, sizeof(int), (void **)&j->ucount, &j->bytes);
     if (rc == KB_OK) {
-        j->stage_bytes = (size_t)V * N * sizeof(int2) + (size_t)V * sizeof(int) + (size_t)N * sizeof(int) +
-                         (size_t)V * sizeof(float2) + (size_t)V * N * sizeof(uint32_t);
+        // pinned staging: the tables of a search, then (16-byte aligned) the host copies of
+        // the status word and the repaired-pixel count, written after each search
+        const size_t tables = (size_t)V * N * sizeof(int2) + (size_t)V * sizeof(int) + (size_t)N * sizeof(int) +
+                              (size_t)V * sizeof(float2) + (size_t)V * N * sizeof(uint32_t);
+        const size_t hstat_off = (tables + 15) & ~(size_t)15;
+        j->stage_bytes = hstat_off + 16;
         cudaError_t e = host_alloc(ctx, j->stage_bytes, &j->stage, &j->stage_cap);
+        if (e == cudaSuccess) {
+            j->hstat = reinterpret_cast<int *>(static_cast<char *>(j->stage) + hstat_off);
+            j->hstat[0] = 0;
+            j->hstat[1] = 0;
+        }
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->stage_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMemsetAsync(j->status, 0, sizeof(int), ctx->astream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->astream);
         if (e != cudaSuccess) rc = cuda_fail(ctx, e, "kb_job_create");
     }
     if (rc != KB_OK) {
@@ -622,6 +636,16 @@ void kb_job_free(kb_job *j) {
     host_release(ctx, j->stage, j->stage_cap);
     dev_release(ctx, j->bytes);
     delete j;
+}
+
+// Stream-ordered copies of the status word and the repaired-pixel count into the
+// job's pinned host words, read by kb_job_wait / kb_job_repaired once job->done
+// has completed (a synchronous read would wait behind other streams' work).
+static cudaError_t readback_status(kb_job *job, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(job->hstat, job->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && job->rescored)
+        e = cudaMemcpyAsync(job->hstat + 1, job->ucount, sizeof(int), cudaMemcpyDeviceToHost, st);
+    return e;
 }
 
 // Validation, fixed-point offset table, processing order and upload of one
@@ -781,7 +805,8 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
         if (e == cudaSuccess) e = kb::launch_repair(r, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "rescore kernels");
     }
-    e = cudaEventRecord(job->done, st);
+    e = readback_status(job, st);
+    if (e == cudaSuccess) e = cudaEventRecord(job->done, st);
     if (e == cudaSuccess) e = cudaEventRecord(s->used, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_search");
     return KB_OK;
@@ -1051,6 +1076,7 @@ int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flag
         if (ce == cudaSuccess) ce = kb::launch_rescore(b->resc[i], b->cap);
         if (ce == cudaSuccess) ce = kb::launch_repair(b->resc[i], b->cap);
     }
+    for (size_t i = 0; i < b->jobs.size() && ce == cudaSuccess; ++i) ce = readback_status(b->jobs[i], b->cap);
     e = cudaStreamEndCapture(b->cap, &b->graph);
     if (ce != cudaSuccess) e = ce;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -1160,11 +1186,7 @@ int kb_job_repaired(kb_job *job, size_t *n_pixels) {
     *n_pixels = 0;
     int rc = kb_job_wait(job);
     if (rc != KB_OK || !job->rescored) return rc;
-    DeviceGuard g(job->ctx->device);
-    int n = 0;
-    cudaError_t e = cudaMemcpy(&n, job->ucount, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(job->ctx, e, "kb_job_repaired");
-    *n_pixels = (size_t)n;
+    *n_pixels = (size_t)job->hstat[1];   // copied after the search's kernels (see readback_status)
     return KB_OK;
 }
 
@@ -1173,10 +1195,9 @@ int kb_job_wait(kb_job *job) {
     kb_ctx *ctx = job->ctx;
     DeviceGuard g(ctx->device);
     cudaError_t e = cudaEventSynchronize(job->done);
-    int st = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&st, job->status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_job_wait");
-    if (st != 0) return fail(ctx, KB_ETIMEOUT, "a bounded device-side wait of the search gave up; results are invalid");
+    if (job->hstat[0] != 0)
+        return fail(ctx, KB_ETIMEOUT, "a bounded device-side wait of the search gave up; results are invalid");
     return KB_OK;
 }
 

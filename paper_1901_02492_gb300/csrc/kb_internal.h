@@ -95,6 +95,7 @@ struct kb_stack {
     cudaEvent_t used = nullptr;       // recorded after the last kernel that read the planes
     size_t bytes = 0;
     bool filled = false;
+    bool zeroed = false;          // the FP32 planes (borders included) were cleared on a stream
 };
 
 struct kb_job {
@@ -109,6 +110,7 @@ struct kb_job {
     int *vorder = nullptr;       // [Vcap] processing order -> caller vidx
     uint32_t *ptab = nullptr;    // [Vcap][Ncap] producer table, processing order
     int *status = nullptr;       // device status word of the last search
+    int *hstat = nullptr;        // pinned host copies, written after the last search: [0] status, [1] repaired
     cudaEvent_t done = nullptr;  // recorded after the last search's kernels
     int *epoch_of = nullptr;     // [Ncap] time-order position -> stack epoch
     float2 *vq = nullptr;        // [Vcap] quantised velocity (px/day) for the results
