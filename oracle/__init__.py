@@ -65,6 +65,7 @@ def _load():
             lib.kbo_offset.argtypes = [i64, i64]
             lib.kbo_offset.restype = i64
             lib.kbo_sums_one_velocity.argtypes = [P, P, P, i32, i32, i32, P, P, P, P, P]
+            lib.kbo_filter_lightcurve.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64, P, P, P, P, P]
             lib.kbo_search_pixels.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64, P, P, i64, P]
             lib.kbo_search_region.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64,
                                               i32, i32, i32, i32, P]
@@ -172,6 +173,25 @@ def sums_one_velocity(psi, phi, times, dx_v, dy_v):
     lib.kbo_sums_one_velocity(_ptr(psi), _ptr(phi), _ptr(times), N, H, W, _ptr(dx_v), _ptr(dy_v),
                               _ptr(P), _ptr(F), _ptr(n))
     return P, F, n
+
+
+def filter_lightcurve(psi, phi, times, dx_v, dy_v, x0, y0, nsigma=5.0):
+    """Sec. 3.3 outlier filter of one trajectory: (Psi, Phi, nkept, nrejected, rejected[N] bool)
+    over the kept epochs (see kbo_filter_lightcurve for the reading)."""
+    lib = _load()
+    psi = _c(psi, np.float64)
+    phi = _c(phi, np.float64)
+    times = _c(times, np.float64)
+    dx_v = _c(dx_v, np.int32)
+    dy_v = _c(dy_v, np.int32)
+    N, H, W = psi.shape
+    P, F = ctypes.c_double(), ctypes.c_double()
+    nk, nr = ctypes.c_int32(), ctypes.c_int32()
+    rej = np.zeros(N, np.uint8)
+    lib.kbo_filter_lightcurve(_ptr(psi), _ptr(phi), _ptr(times), N, H, W, _ptr(dx_v), _ptr(dy_v), int(x0), int(y0),
+                              float(nsigma), ctypes.byref(P), ctypes.byref(F), ctypes.byref(nk), ctypes.byref(nr),
+                              _ptr(rej))
+    return P.value, F.value, nk.value, nr.value, rej.astype(bool)
 
 
 def search_region(psi, phi, times, dx, dy, k, nu_min=-np.inf, region=None):

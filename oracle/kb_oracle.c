@@ -16,6 +16,8 @@
  *   coadd              Sec. 2.1.5: Psi = sum_i Psi_i(y_i), Phi = sum_i Phi_i(y_i)
  *   scores             Sec. 2.1.5: alpha_ML = Psi / Phi, nu = Psi / sqrt(Phi)
  *   search             Sec. 2.2: evaluate nu for every start pixel and velocity
+ *   light-curve filter Sec. 3.3: reject observations far from the best-fit flux
+ *                      of the others, recompute the likelihood (reading below)
  *
  * Readings of points the paper leaves open:
  *   - a pixel is masked when its mask byte is non-zero, when n or sigma^2 is not
@@ -381,4 +383,68 @@ void kbo_search_pixels_from_images(const float *sci, const float *var, const uin
             offer(P, F, nobs, v, k, nu_min, o);
         }
     }
+}
+
+/* ---- light-curve outlier filter (Sec. 3.3) ------------------------------ */
+
+/*
+ * Sec. 3.3: reject the observations of a kept trajectory that lie more than
+ * nsigma standard deviations from the best-fit (Kalman) flux at that
+ * observation, then recompute the likelihood from the remaining ones.
+ *
+ * Reading of the unspecified filter: the object's flux is constant (the model
+ * of Sec. 2.1), so the Kalman estimate from a set of observations is their
+ * inverse-variance weighted mean.  Epoch e's own flux estimate is
+ * alpha_e = psi_e / phi_e with variance 1 / phi_e (Sec. 2.1.5 for one image);
+ * the estimate from all the other epochs is alpha_rest = (Psi - psi_e) /
+ * (Phi - phi_e) with variance 1 / (Phi - phi_e).  Epoch e is rejected when
+ *     |alpha_e - alpha_rest| > nsigma * sqrt(1 / phi_e + 1 / (Phi - phi_e)).
+ * All decisions use the unfiltered sums (one pass); epochs with phi_e == 0 or
+ * with no information in the others (Phi - phi_e == 0) are never rejected.
+ * Only epochs whose trajectory pixel is inside the image take part.
+ *
+ * Outputs: the sums over the kept epochs (time order), the number of kept and
+ * of rejected epochs, and rejected[e] = 1 for each rejected epoch e.
+ */
+void kbo_filter_lightcurve(const double *psi, const double *phi, const double *times, int N, int H, int W,
+                           const int32_t *dx, const int32_t *dy, int x0, int y0, double nsigma, double *P_out,
+                           double *F_out, int32_t *nkept, int32_t *nrej, uint8_t *rejected) {
+    size_t npix = (size_t)H * W;
+    int order[4096];
+    time_order(times, N, order);
+    double P = 0.0, F = 0.0;
+    for (int e = 0; e < N; ++e) rejected[e] = 0;
+    for (int j = 0; j < N; ++j) { /* the unfiltered coadd */
+        int e = order[j], x = x0 + dx[e], y = y0 + dy[e];
+        if (x < 0 || x >= W || y < 0 || y >= H) continue;
+        size_t i = (size_t)e * npix + (size_t)y * W + x;
+        P += psi[i];
+        F += phi[i];
+    }
+    double Pk = 0.0, Fk = 0.0;
+    int kept = 0, rej = 0;
+    for (int j = 0; j < N; ++j) {
+        int e = order[j], x = x0 + dx[e], y = y0 + dy[e];
+        if (x < 0 || x >= W || y < 0 || y >= H) continue;
+        size_t i = (size_t)e * npix + (size_t)y * W + x;
+        double pe = psi[i], fe = phi[i], rest = F - fe;
+        int out = 0;
+        if (fe > 0.0 && rest > 0.0) {
+            double a_e = pe / fe, a_rest = (P - pe) / rest;
+            double sigma = sqrt(1.0 / fe + 1.0 / rest);
+            out = fabs(a_e - a_rest) > nsigma * sigma;
+        }
+        if (out) {
+            rejected[e] = 1;
+            ++rej;
+        } else {
+            Pk += pe;
+            Fk += fe;
+            ++kept;
+        }
+    }
+    *P_out = Pk;
+    *F_out = Fk;
+    *nkept = kept;
+    *nrej = rej;
 }

@@ -426,3 +426,101 @@ def test_hand_worked_coadd_example():
             P, F = [(t[3], t[4]) for t in d["trajectories"] if (t[0], t[1], t[2]) == (x0, y0, r["vidx"])][0]
             assert r["nu"] == pytest.approx(float(P) / math.sqrt(float(F)), rel=1e-15)
             assert r["alpha"] == pytest.approx(float(P / F), rel=1e-15)
+
+
+# ------------------------------------------------------------ Sec. 3.3 light-curve filter
+
+def _flat_stack(N, H, W, flux_map):
+    """1 x 1 PSF, unit variance: psi_t = n_t, phi_t = 1 at every pixel (Sec. 2.1.5 with T = 1)."""
+    sci = np.asarray(flux_map, np.float32)
+    var = np.ones((N, H, W), np.float32)
+    psf = np.ones((N, 1, 1), np.float32)
+    return sci, var, psf
+
+
+def test_filter_rejects_exactly_the_interloper_epoch():
+    """Constant flux 2 on a stationary trajectory in 8 epochs, one epoch with flux 32 (a bright
+    interloper, Sec. 3.3).  With unit variances that epoch is 28 sigma from the other seven's
+    flux and each other epoch 4 sigma from the rest: only the interloper goes, and the kept
+    epochs give Psi = 14, Phi = 7, nu = 14 / sqrt(7), alpha = 2."""
+    N, H, W = 8, 5, 5
+    img = np.zeros((N, H, W), np.float32)
+    img[:, 2, 2] = 2.0
+    img[3, 2, 2] = 32.0
+    sci, var, psf = _flat_stack(N, H, W, img)
+    times = np.arange(N, dtype=np.float64) * 0.1
+    psi, phi = oracle.psi_phi(sci, var, None, psf)
+    dx = np.zeros(N, np.int32)
+    dy = np.zeros(N, np.int32)
+    P, F, nk, nr, rej = oracle.filter_lightcurve(psi, phi, times, dx, dy, 2, 2, 5.0)
+    assert (P, F, nk, nr) == (14.0, 7.0, 7, 1)
+    assert list(np.nonzero(rej)[0]) == [3]
+    # a lower threshold also takes the 4-sigma epochs: nothing then survives but the outlier's test
+    P, F, nk, nr, rej = oracle.filter_lightcurve(psi, phi, times, dx, dy, 2, 2, 3.5)
+    assert nr == N and nk == 0 and (P, F) == (0.0, 0.0)
+
+
+def test_filter_keeps_a_clean_noiseless_source():
+    """A noiseless point source on its exact trajectory: every epoch's flux equals the others',
+    so nothing is rejected and the sums equal the unfiltered coadd."""
+    rng = np.random.default_rng(31)
+    N, H, W, K = 6, 40, 60, 7
+    times = np.array([0.0, 0.3, 0.7, 1.2, 1.6, 2.0])
+    psf1 = synth.gaussian_psf(K, 1.2)
+    psf = np.stack([psf1] * N)
+    var = np.stack([np.full((H, W), v, np.float32) for v in rng.uniform(2.0, 5.0, N)])
+    sci = np.zeros((N, H, W), np.float32)
+    v = (7.0, -4.0)
+    for e, t in enumerate(times):
+        sci[e, 25 + int(round(v[1] * t)) - K // 2: 25 + int(round(v[1] * t)) + K // 2 + 1,
+            12 + int(round(v[0] * t)) - K // 2: 12 + int(round(v[0] * t)) + K // 2 + 1] = 8.0 * psf1
+    psi, phi = oracle.psi_phi(sci, var, None, psf)
+    dx, dy = oracle.offsets(times, np.array([v[0]]), np.array([v[1]]))
+    P, F, nk, nr, rej = oracle.filter_lightcurve(psi, phi, times, dx[0], dy[0], 12, 25, 5.0)
+    P0, F0, n0 = oracle.sums_one_velocity(psi, phi, times, dx[0], dy[0])
+    assert nr == 0 and nk == N and not rej.any()
+    assert P == P0[25, 12] and F == F0[25, 12]
+    assert P / F == pytest.approx(8.0, rel=1e-9)
+
+
+def test_filter_rarely_rejects_pure_noise():
+    """N(0, 1) noise, unit variance, no source: alpha_e - alpha_rest then has variance exactly
+    1 / phi_e + 1 / (Phi - phi_e), so the statistic is N(0, 1).  A 5-sigma rejection has
+    probability ~6e-7 per epoch (essentially none over ~48000 epochs); beyond 2 sigma lie
+    4.55 % of them."""
+    rng = np.random.default_rng(32)
+    N, H, W = 8, 60, 100
+    sci, var, psf = _flat_stack(N, H, W, rng.standard_normal((N, H, W)))
+    times = np.arange(N) * 0.25
+    psi, phi = oracle.psi_phi(sci, var, None, psf)
+    dx = np.zeros(N, np.int32)
+    dy = np.zeros(N, np.int32)
+    rej5 = rej2 = 0
+    for y in range(H):
+        for x in range(W):
+            rej5 += oracle.filter_lightcurve(psi, phi, times, dx, dy, x, y, 5.0)[3]
+            rej2 += oracle.filter_lightcurve(psi, phi, times, dx, dy, x, y, 2.0)[3]
+    n = N * H * W
+    assert rej5 <= 2
+    # under the null, (alpha_e - alpha_rest) / sigma is exactly N(0, 1): 4.55 % beyond 2 sigma
+    assert abs(rej2 / n - 0.0455) < 5 * math.sqrt(0.0455 * 0.9545 / n)
+
+
+def test_filter_masked_epoch_and_permutation_invariance():
+    """An epoch masked at the trajectory pixel (phi = 0 there with a 1 x 1 PSF) carries no
+    information and is never rejected; permuting (epoch, time) pairs changes nothing."""
+    N, H, W = 7, 4, 4
+    img = np.zeros((N, H, W), np.float32)
+    img[:, 1, 1] = 3.0
+    img[5, 1, 1] = 300.0
+    sci, var, psf = _flat_stack(N, H, W, img)
+    mask = np.zeros((N, H, W), np.uint8)
+    mask[5, 1, 1] = 1
+    times = np.array([0.0, 0.5, 0.2, 0.9, 0.4, 0.7, 1.0])
+    psi, phi = oracle.psi_phi(sci, var, mask, psf)
+    z = np.zeros(N, np.int32)
+    P, F, nk, nr, rej = oracle.filter_lightcurve(psi, phi, times, z, z, 1, 1, 5.0)
+    assert nr == 0 and nk == N and (P, F) == (18.0, 6.0)
+    perm = np.array([3, 0, 6, 1, 5, 2, 4])
+    r2 = oracle.filter_lightcurve(psi[perm], phi[perm], times[perm], z, z, 1, 1, 5.0)
+    assert r2[:4] == (P, F, nk, nr)
