@@ -58,6 +58,8 @@ def parse():
                     help="decam: the 12x4096^2 stack; batch: 64 uneven 2048x4096 stacks in one batched launch; "
                          "serve: a Poisson stream of search jobs through the serving loop")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--filter", action="store_true",
+                    help="also time the Sec. 3.3 light-curve outlier filter on the kept trajectories")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-load", type=float, default=0.75,
                     help="arrival rate as a fraction of the capacity measured on a saturated sample")
@@ -360,6 +362,22 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(sci_h.numel() * 4 + var_h.numel() * 4),
                     "d2h_bytes_per_step": int(H * W * k * kb.RESULT_DTYPE.itemsize), "ms_per_step": e2e_ms},
             "gpu_launches": launches_per_step * args.steps}
+    if args.filter:
+        # the Sec. 3.3 outlier filter of every kept trajectory (two FP64 passes over its epochs)
+        fout = torch.empty(H * W * k * kb.FILTERED_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        job.filter_lightcurves(stack, 5.0, fout, stream=stream)
+        f0, f1 = ev(), ev()
+        f0.record(stream)
+        for _ in range(3):
+            job.filter_lightcurves(stack, 5.0, fout, stream=stream)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        fms = f0.elapsed_time(f1) / 3
+        nrej = int(fout.view(torch.int32).view(H * W * k, kb.FILTERED_DTYPE.itemsize // 4)[:, 4].sum().item())
+        line["filter"] = {"kernel": "filter_kernel", "nsigma": 5.0, "ms_per_launch": fms,
+                          "trajectories_per_s": H * W * k / (fms * 1e-3), "rejected_epochs": nrej,
+                          "trajectories": H * W * k}
+        del fout
     if args.rescore:
         line["rescore"] = {"candidates_per_pixel": k + (max(2, k // 2) if args.storage == "bf16" else max(2, k // 4)),
                            "repaired_pixels": repaired,

@@ -253,6 +253,37 @@ int kb_job_repaired(kb_job *job, size_t *n_pixels);
  * copies).  KB_ERANGE (with *n_written = H*W*topk) if capacity is too small. */
 int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream);
 
+/* ---- light-curve outlier filter of kept trajectories (Sec. 3.3) ---------- */
+
+/* One filtered trajectory (72 bytes). */
+typedef struct kb_filtered {
+    int32_t x0, y0;        /* start pixel */
+    int32_t vidx;          /* velocity index as in kb_results; -1 = empty slot */
+    int32_t nobs;          /* epochs kept: trajectory pixel in the image, not rejected */
+    int32_t nrejected;     /* epochs rejected as outliers */
+    int32_t reserved;
+    uint32_t rejected[4];  /* bit e % 32 of word e / 32: stack epoch e rejected */
+    double psi, phi;       /* coadd over the kept epochs, FP64 sums of the FP32 planes */
+    double nu, alpha;      /* psi / sqrt(phi), psi / phi; -inf and 0 when phi == 0 or empty */
+} kb_filtered;
+
+/* Sec. 3.3: for every kept trajectory of the job's last search (H*W*topk of
+ * them, the records kb_results would write), reject the observations that lie
+ * more than `nsigma` standard deviations from the best-fit flux of the others
+ * and recompute the likelihood from the rest.  Reading of the paper's Kalman
+ * variant: the flux is constant, so the estimate from a set of observations is
+ * their inverse-variance weighted mean; epoch e (pixel in the image, phi_e > 0)
+ * with flux psi_e / phi_e is rejected when it differs from the others' estimate
+ * (Psi - psi_e) / (Phi - phi_e) by more than nsigma sqrt(1 / phi_e + 1 / (Phi -
+ * phi_e)), all decisions on the unfiltered sums, in FP64.
+ *   s      the stack that was searched (its FP32 planes are read)
+ *   out    DEVICE pointer, room for `capacity` records, written [H][W][topk]
+ * KB_EINVAL (no search yet, stack shape differs, nsigma <= 0, out not device
+ * memory), KB_ERANGE (capacity < H*W*topk; *n_written says how many).  Runs in
+ * stream order after the search. */
+int kb_filter_lightcurves(kb_job *job, const kb_stack *s, double nsigma, kb_filtered *out, size_t capacity,
+                          size_t *n_written, void *stream);
+
 /* Device bytes that one search will hold, for admission under an HBM budget:
  *   *stack  kb_stack_create(N, H, W, storage) plus kb_make_psi_phi with a K x K
  *           PSF (an upper bound: the tap table of a non-separable PSF)

@@ -27,6 +27,11 @@ RESULT_DTYPE = np.dtype([("x0", "<i4"), ("y0", "<i4"), ("vidx", "<i4"), ("nobs",
                          ("nu", "<f8"), ("alpha", "<f8")])
 assert RESULT_DTYPE.itemsize == 48
 
+FILTERED_DTYPE = np.dtype([("x0", "<i4"), ("y0", "<i4"), ("vidx", "<i4"), ("nobs", "<i4"), ("nrejected", "<i4"),
+                           ("reserved", "<i4"), ("rejected", "<u4", (4,)), ("psi", "<f8"), ("phi", "<f8"),
+                           ("nu", "<f8"), ("alpha", "<f8")])
+assert FILTERED_DTYPE.itemsize == 72
+
 if not os.path.exists(LIB_PATH):
     raise ImportError("libkb.so is not built (run paper_1901_02492_gb300.build.build() or "
                       "__graft_entry__.build()); there is no fallback path")
@@ -68,6 +73,7 @@ _kb_make_psi_phi_static = _sig("kb_make_psi_phi_static", _i32,
 
 _kb_estimate_bytes = _sig("kb_estimate_bytes", _i32, [_i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32,
                                                        ctypes.POINTER(_sz), ctypes.POINTER(_sz)])
+_kb_filter_lightcurves = _sig("kb_filter_lightcurves", _i32, [_P, _P, ctypes.c_double, _P, _sz, ctypes.POINTER(_sz), _P])
 _kb_batch_create = _sig("kb_batch_create", _i32, [_P, _i32, _P, _i32, ctypes.POINTER(_P)])
 _kb_batch_run = _sig("kb_batch_run", _i32, [_P, _P])
 _kb_batch_groups = _sig("kb_batch_groups", _i32, [_P, _P, _i32, ctypes.POINTER(_i32)])
@@ -77,7 +83,8 @@ EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_s
             "kb_set_search_carveout", "kb_set_search_waves", "kb_measure_gather_peak", "kb_stack_create", "kb_stack_free",
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
             "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static",
-            "kb_batch_create", "kb_batch_run", "kb_batch_groups", "kb_batch_free", "kb_estimate_bytes"]
+            "kb_batch_create", "kb_batch_run", "kb_batch_groups", "kb_batch_free", "kb_estimate_bytes",
+            "kb_filter_lightcurves"]
 
 
 class KBError(RuntimeError):
@@ -276,6 +283,22 @@ class Job:
         self.ctx.check(_kb_results(self.h, _ptr(out), cap, ctypes.byref(written), _stream(stream)))
         if isinstance(out, np.ndarray):
             return out.reshape(self.H, self.W, self.k)
+        return out
+
+    def filter_lightcurves(self, stack: Stack, nsigma=5.0, out=None, stream=None):
+        """Sec. 3.3 outlier filter of the kept trajectories: FILTERED_DTYPE records [H][W][k].
+        out: None (returned as numpy, through a temporary device buffer) or a CUDA uint8 tensor."""
+        import torch
+        n = self.H * self.W * (self.k or self.topk)
+        dev = out
+        if dev is None:
+            dev = torch.empty(n * FILTERED_DTYPE.itemsize, dtype=torch.uint8, device="cuda:%d" % self.ctx.device)
+        cap = dev.numel() * dev.element_size() // FILTERED_DTYPE.itemsize
+        written = _sz()
+        self.ctx.check(_kb_filter_lightcurves(self.h, stack.h, float(nsigma), _ptr(dev), cap, ctypes.byref(written),
+                                              _stream(stream)))
+        if out is None:
+            return dev.cpu().numpy().view(FILTERED_DTYPE).reshape(self.H, self.W, self.k or self.topk)
         return out
 
     def free(self):

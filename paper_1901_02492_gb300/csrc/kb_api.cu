@@ -1181,6 +1181,43 @@ int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, 
     return kb_job_wait(job);
 }
 
+int kb_filter_lightcurves(kb_job *job, const kb_stack *s, double nsigma, kb_filtered *out, size_t capacity,
+                          size_t *n_written, void *stream) {
+    if (!job) return KB_EINVAL;
+    kb_ctx *ctx = job->ctx;
+    if (job->k == 0) return fail(ctx, KB_EINVAL, "kb_filter_lightcurves: no search has run on this job");
+    if (!s || !s->filled || s->H != job->H || s->W != job->W || s->N != job->N)
+        return fail(ctx, KB_EINVAL, "kb_filter_lightcurves: the stack is not the searched one (shape or psi/phi)");
+    if (!(nsigma > 0.0) || !std::isfinite(nsigma))
+        return fail(ctx, KB_EINVAL, "kb_filter_lightcurves: nsigma %g is not positive", nsigma);
+    const size_t need = (size_t)job->H * job->W * job->k;
+    if (n_written) *n_written = need;
+    if (!out || !is_device_ptr(out)) return fail(ctx, KB_EINVAL, "kb_filter_lightcurves: out must be device memory");
+    if (capacity < need) return fail(ctx, KB_ERANGE, "kb_filter_lightcurves: capacity %zu < %zu", capacity, need);
+    DeviceGuard g(ctx->device);
+    kb::FilterArgs a;
+    a.f32 = s->f32;
+    a.plane_elems = s->L.plane_elems;
+    a.origin = s->L.origin;
+    a.H = s->H;
+    a.W = s->W;
+    a.pitch = s->L.pitch;
+    a.N = s->N;
+    a.epoch_of = job->epoch_of;
+    a.offs = job->offs;
+    a.recs = job->rescored ? nullptr : job->recs;
+    a.recs64 = job->rescored ? job->recs64 : nullptr;
+    a.krec = job->kkeep;
+    a.k = job->k;
+    a.nsigma2 = nsigma * nsigma;
+    a.out = out;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = kb::launch_filter(a, st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->used, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_filter_lightcurves");
+    return KB_OK;
+}
+
 int kb_job_repaired(kb_job *job, size_t *n_pixels) {
     if (!job || !n_pixels) return KB_EINVAL;
     *n_pixels = 0;

@@ -222,4 +222,19 @@ struct ExpandArgs {
 };
 cudaError_t launch_expand(const ExpandArgs &a, cudaStream_t st);
 
+// Sec. 3.3 light-curve filter of kept trajectories
+struct FilterArgs {
+    const float2 *f32;       // FP32 planes (phase 0)
+    long long plane_elems, origin;
+    int H, W, pitch, N;
+    const int *epoch_of;     // [N] time order -> stack epoch
+    const int2 *offs;        // [V][N] time order
+    const Rec *recs;         // [H*W][krec] or null
+    const Rec64 *recs64;     // [H*W][k] or null
+    int krec, k;
+    double nsigma2;          // nsigma^2
+    kb_filtered *out;        // device [H*W][k]
+};
+cudaError_t launch_filter(const FilterArgs &a, cudaStream_t st);
+
 }  // namespace kb

@@ -327,6 +327,92 @@ cudaError_t launch_repair(const RescoreArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Sec. 3.3 light-curve filter, one thread per kept trajectory: pass 1 sums the
+// coadd in FP64 (epochs in time order), pass 2 re-gathers each in-image epoch
+// and rejects it when its flux psi_e / phi_e differs from the other epochs'
+// weighted mean (Psi - psi_e) / (Phi - phi_e) by more than nsigma sigma, with
+// sigma^2 = 1 / phi_e + 1 / (Phi - phi_e).  Multiplying through by
+// phi_e (Phi - phi_e) > 0 gives the division-free test
+//     (psi_e Phi - Psi phi_e)^2 > nsigma^2 Phi phi_e (Phi - phi_e),
+// which spares the narrow FP64 pipe two divisions and a square root per epoch.
+__global__ void filter_kernel(FilterArgs a) {
+    const long long total = (long long)a.H * a.W * a.k;
+    const float2 *base = a.f32 + a.origin;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long pix = g / a.k;
+        const int slot = (int)(g - pix * a.k);
+        const int y = (int)(pix / a.W), x = (int)(pix - (long long)y * a.W);
+        const uint32_t v = a.recs64 ? a.recs64[pix * a.k + slot].vidx : (a.recs[pix * a.krec + slot].meta & 0xffffu);
+        kb_filtered o;
+        o.x0 = x;
+        o.y0 = y;
+        o.reserved = 0;
+        o.rejected[0] = o.rejected[1] = o.rejected[2] = o.rejected[3] = 0u;
+        if (v == kEmptyVidx) {
+            o.vidx = -1;
+            o.nobs = 0;
+            o.nrejected = 0;
+            o.psi = o.phi = 0.0;
+            o.nu = -INFINITY;
+            o.alpha = 0.0;
+            a.out[g] = o;
+            continue;
+        }
+        const int2 *ov = a.offs + (long long)v * a.N;
+        double P = 0.0, F = 0.0;
+        for (int j = 0; j < a.N; ++j) {
+            const int2 d = __ldg(ov + j);
+            const int xx = x + d.x, yy = y + d.y;
+            if ((unsigned)xx < (unsigned)a.W && (unsigned)yy < (unsigned)a.H) {
+                const float2 q = __ldg(base + (long long)a.epoch_of[j] * a.plane_elems + (long long)yy * a.pitch + xx);
+                P += (double)q.x;
+                F += (double)q.y;
+            }
+        }
+        double Pk = 0.0, Fk = 0.0;
+        int kept = 0, rej = 0;
+        for (int j = 0; j < a.N; ++j) {
+            const int2 d = __ldg(ov + j);
+            const int xx = x + d.x, yy = y + d.y;
+            if (!((unsigned)xx < (unsigned)a.W && (unsigned)yy < (unsigned)a.H)) continue;
+            const int e = a.epoch_of[j];
+            const float2 q = __ldg(base + (long long)e * a.plane_elems + (long long)yy * a.pitch + xx);
+            const double pe = (double)q.x, fe = (double)q.y, rest = F - fe;
+            bool out = false;
+            if (fe > 0.0 && rest > 0.0) {
+                const double dev = pe * F - P * fe;
+                out = dev * dev > a.nsigma2 * F * fe * rest;
+            }
+            if (out) {
+                o.rejected[e >> 5] |= 1u << (e & 31);
+                ++rej;
+            } else {
+                Pk += pe;
+                Fk += fe;
+                ++kept;
+            }
+        }
+        o.vidx = (int)v;
+        o.nobs = kept;
+        o.nrejected = rej;
+        o.psi = Pk;
+        o.phi = Fk;
+        o.nu = Fk > 0.0 ? Pk / sqrt(Fk) : -INFINITY;
+        o.alpha = Fk > 0.0 ? Pk / Fk : 0.0;
+        a.out[g] = o;
+    }
+}
+
+cudaError_t launch_filter(const FilterArgs &a, cudaStream_t st) {
+    const long long total = (long long)a.H * a.W * a.k;
+    if (total <= 0) return cudaSuccess;
+    long long blocks = (total + 127) / 128;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    filter_kernel<<<(int)blocks, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_expand(const ExpandArgs &a, cudaStream_t st) {
     if (a.count <= 0) return cudaSuccess;
     long long blocks = (a.count + 255) / 256;

@@ -72,6 +72,19 @@ def test_batch_struct_layouts_match_binding(tmp_path, lib):
         assert vals[1:] == [getattr(cls, f).offset for f in fs], name
 
 
+def test_filtered_record_layout_matches_binding(tmp_path, lib):
+    names = list(lib.FILTERED_DTYPE.names)
+    src = tmp_path / "flayout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "kb.h"\nint main(void){'
+                   'printf("%zu", sizeof(kb_filtered));'
+                   + "".join('printf(" %%zu", offsetof(kb_filtered, %s));' % f for f in names) + "return 0;}\n")
+    exe = tmp_path / "flayout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals[0] == lib.FILTERED_DTYPE.itemsize
+    assert vals[1:] == [lib.FILTERED_DTYPE.fields[f][1] for f in names]
+
+
 def test_offsets_bit_exact_against_oracle(lib):
     rng = np.random.default_rng(5)
     for trial in range(5):
