@@ -66,6 +66,8 @@ def _load():
             lib.kbo_offset.restype = i64
             lib.kbo_sums_one_velocity.argtypes = [P, P, P, i32, i32, i32, P, P, P, P, P]
             lib.kbo_filter_lightcurve.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64, P, P, P, P, P]
+            lib.kbo_stamp.argtypes = [P, P, i32, i32, i32, P, P, i32, i32, i32, i32, P]
+            lib.kbo_moments.argtypes = [P, i32, P, P, P, P, P, P]
             lib.kbo_search_pixels.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64, P, P, i64, P]
             lib.kbo_search_region.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64,
                                               i32, i32, i32, i32, P]
@@ -192,6 +194,31 @@ def filter_lightcurve(psi, phi, times, dx_v, dy_v, x0, y0, nsigma=5.0):
                               float(nsigma), ctypes.byref(P), ctypes.byref(F), ctypes.byref(nk), ctypes.byref(nr),
                               _ptr(rej))
     return P.value, F.value, nk.value, nr.value, rej.astype(bool)
+
+
+def stamp(sci, mask, dx_v, dy_v, x0, y0, r, median=False):
+    """Sec. 3.3 coadded postage stamp [2r+1][2r+1] (float32) of one trajectory: the mean or
+    median over epochs of the finite, unmasked, in-image science pixels."""
+    lib = _load()
+    sci = _c(sci, np.float32)
+    mask = None if mask is None else _c(mask, np.uint8)
+    dx_v = _c(dx_v, np.int32)
+    dy_v = _c(dy_v, np.int32)
+    N, H, W = sci.shape
+    out = np.empty((2 * r + 1, 2 * r + 1), np.float32)
+    lib.kbo_stamp(_ptr(sci), None if mask is None else _ptr(mask), N, H, W, _ptr(dx_v), _ptr(dy_v), int(x0), int(y0),
+                  int(r), 1 if median else 0, _ptr(out))
+    return out
+
+
+def moments(st):
+    """(m00, mx, my, mu20, mu02, mu11) of a stamp, coordinates relative to its centre."""
+    lib = _load()
+    st = _c(st, np.float32)
+    r = (st.shape[0] - 1) // 2
+    vals = [ctypes.c_double() for _ in range(6)]
+    lib.kbo_moments(_ptr(st), r, *[ctypes.byref(v) for v in vals])
+    return tuple(v.value for v in vals)
 
 
 def search_region(psi, phi, times, dx, dy, k, nu_min=-np.inf, region=None):

@@ -18,6 +18,8 @@
  *   search             Sec. 2.2: evaluate nu for every start pixel and velocity
  *   light-curve filter Sec. 3.3: reject observations far from the best-fit flux
  *                      of the others, recompute the likelihood (reading below)
+ *   postage stamps     Sec. 3.3: mean / median coadd of science-image stamps along
+ *                      a trajectory, and the stamp's central moments
  *
  * Readings of points the paper leaves open:
  *   - a pixel is masked when its mask byte is non-zero, when n or sigma^2 is not
@@ -447,4 +449,85 @@ void kbo_filter_lightcurve(const double *psi, const double *phi, const double *t
     *F_out = Fk;
     *nkept = kept;
     *nrej = rej;
+}
+
+/* ---- coadded postage stamps and central moments (Sec. 3.3) -------------- */
+
+static int cmp_float(const void *a, const void *b) {
+    float x = *(const float *)a, y = *(const float *)b;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Sec. 3.3 postage stamp of one trajectory: for each stamp pixel (sx, sy) in
+ * [-r, r]^2, the science values n_e(x0 + dx_e + sx, y0 + dy_e + sy) of the epochs
+ * whose pixel is inside the image, finite and not masked, combined as their mean
+ * (mode 0) or median (mode 1: the middle value, the mean of the two middle ones
+ * for an even count); 0 where no epoch contributes.  Stamp layout [2r+1][2r+1],
+ * row sy + r, column sx + r.
+ */
+void kbo_stamp(const float *sci, const uint8_t *mask, int N, int H, int W, const int32_t *dx, const int32_t *dy,
+               int x0, int y0, int r, int mode, float *stamp) {
+    int S = 2 * r + 1;
+    float vals[4096];
+    size_t npix = (size_t)H * W;
+    for (int sy = -r; sy <= r; ++sy)
+        for (int sx = -r; sx <= r; ++sx) {
+            int n = 0;
+            double sum = 0.0;
+            for (int e = 0; e < N; ++e) {
+                int x = x0 + dx[e] + sx, y = y0 + dy[e] + sy;
+                if (x < 0 || x >= W || y < 0 || y >= H) continue;
+                size_t i = (size_t)e * npix + (size_t)y * W + x;
+                float v = sci[i];
+                if (!isfinite(v) || (mask && mask[i])) continue;
+                vals[n++] = v;
+                sum += v;
+            }
+            float out = 0.0f;
+            if (n > 0) {
+                if (mode == 0) {
+                    out = (float)(sum / n);
+                } else {
+                    qsort(vals, (size_t)n, sizeof(float), cmp_float);
+                    out = (n & 1) ? vals[n / 2] : (float)(0.5 * ((double)vals[n / 2 - 1] + (double)vals[n / 2]));
+                }
+            }
+            stamp[(size_t)(sy + r) * S + (sx + r)] = out;
+        }
+}
+
+/*
+ * Central moments of a stamp, pixel values as weights, coordinates relative to
+ * the stamp centre: m00 = sum I, centroid (mx, my) = sum (x, y) I / m00, and
+ * mu20, mu02, mu11 = sum (x - mx)^2 I, (y - my)^2 I, (x - mx)(y - my) I over m00.
+ * All zero when m00 == 0.
+ */
+void kbo_moments(const float *stamp, int r, double *m00, double *mx, double *my, double *mu20, double *mu02,
+                 double *mu11) {
+    int S = 2 * r + 1;
+    double s = 0.0, sx = 0.0, sy = 0.0;
+    for (int j = 0; j < S; ++j)
+        for (int i = 0; i < S; ++i) {
+            double v = stamp[(size_t)j * S + i];
+            s += v;
+            sx += (i - r) * v;
+            sy += (j - r) * v;
+        }
+    *m00 = s;
+    *mx = *my = *mu20 = *mu02 = *mu11 = 0.0;
+    if (s == 0.0) return;
+    double cx = sx / s, cy = sy / s, a = 0.0, b = 0.0, c = 0.0;
+    for (int j = 0; j < S; ++j)
+        for (int i = 0; i < S; ++i) {
+            double v = stamp[(size_t)j * S + i], x = i - r - cx, y = j - r - cy;
+            a += x * x * v;
+            b += y * y * v;
+            c += x * y * v;
+        }
+    *mx = cx;
+    *my = cy;
+    *mu20 = a / s;
+    *mu02 = b / s;
+    *mu11 = c / s;
 }

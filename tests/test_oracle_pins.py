@@ -524,3 +524,91 @@ def test_filter_masked_epoch_and_permutation_invariance():
     perm = np.array([3, 0, 6, 1, 5, 2, 4])
     r2 = oracle.filter_lightcurve(psi[perm], phi[perm], times[perm], z, z, 1, 1, 5.0)
     assert r2[:4] == (P, F, nk, nr)
+
+
+# ------------------------------------------------------------ Sec. 3.3 postage stamps and moments
+
+def test_moments_of_hand_stamps():
+    """A single pixel of value 5 at (2, -1): m00 = 5, centroid (2, -1), no spread.  Two unit
+    pixels at (-1, 0) and (1, 0): centroid 0, mu20 = 1, mu02 = mu11 = 0.  An empty stamp: zeros."""
+    r = 3
+    s = np.zeros((7, 7), np.float32)
+    s[-1 + r, 2 + r] = 5.0
+    assert oracle.moments(s) == (5.0, 2.0, -1.0, 0.0, 0.0, 0.0)
+    s = np.zeros((7, 7), np.float32)
+    s[r, r - 1] = s[r, r + 1] = 1.0
+    assert oracle.moments(s) == (2.0, 0.0, 0.0, 1.0, 0.0, 0.0)
+    assert oracle.moments(np.zeros((5, 5), np.float32)) == (0.0,) * 6
+
+
+def _moving_gaussian_stack(N, H, W, sigma, x0, y0, dx, dy, amp=100.0):
+    """A noiseless Gaussian of width sigma centred on the integer trajectory pixels."""
+    yy, xx = np.mgrid[0:H, 0:W]
+    sci = np.zeros((N, H, W), np.float32)
+    for e in range(N):
+        cx, cy = x0 + dx[e], y0 + dy[e]
+        sci[e] = (amp * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * sigma ** 2))).astype(np.float32)
+    return sci
+
+
+def test_stamp_of_a_noiseless_source_is_its_profile():
+    """Every epoch's stamp is the same sampled Gaussian, so the mean and the median coadds are
+    that Gaussian; its centroid is the stamp centre, mu11 = 0 and mu20 = mu02 = sigma^2 to the
+    accuracy of a sampled, truncated Gaussian (r = 6 sigma)."""
+    N, H, W, sigma, r = 5, 60, 80, 1.5, 9
+    dx = np.array([0, 4, 9, 13, 18], np.int32)
+    dy = np.array([0, -2, -5, -7, -9], np.int32)
+    sci = _moving_gaussian_stack(N, H, W, sigma, 25, 40, dx, dy)
+    yy, xx = np.mgrid[-r:r + 1, -r:r + 1]
+    profile = (100.0 * np.exp(-(xx ** 2 + yy ** 2) / (2 * sigma ** 2))).astype(np.float32)
+    for med in (False, True):
+        st = oracle.stamp(sci, None, dx, dy, 25, 40, r, median=med)
+        assert np.allclose(st, profile, rtol=1e-6, atol=1e-6)
+    m00, mx, my, mu20, mu02, mu11 = oracle.moments(oracle.stamp(sci, None, dx, dy, 25, 40, r))
+    assert abs(mx) < 1e-9 and abs(my) < 1e-9 and abs(mu11) < 1e-9
+    assert mu20 == pytest.approx(sigma ** 2, rel=1e-4) and mu02 == pytest.approx(sigma ** 2, rel=1e-4)
+
+
+def test_median_stamp_ignores_a_single_epoch_interloper():
+    """A bright source off the trajectory in one of 5 epochs: the median coadd is unchanged, the
+    mean carries a fifth of it (Sec. 3.3: the moment filter rejects off-centre light)."""
+    N, H, W, sigma, r = 5, 60, 80, 1.2, 6
+    dx = np.array([0, 3, 6, 9, 12], np.int32)
+    dy = np.zeros(N, np.int32)
+    sci = _moving_gaussian_stack(N, H, W, sigma, 20, 30, dx, dy)
+    clean_mean = oracle.stamp(sci, None, dx, dy, 20, 30, r)
+    sci[2, 30 + 3, 20 + dx[2] + 4] += 500.0           # interloper 4 px right, 3 px down in epoch 2
+    med = oracle.stamp(sci, None, dx, dy, 20, 30, r, median=True)
+    mean = oracle.stamp(sci, None, dx, dy, 20, 30, r)
+    assert np.array_equal(med, clean_mean)            # all epochs agreed before: same values
+    assert mean[3 + r, 4 + r] == pytest.approx(clean_mean[3 + r, 4 + r] + 100.0, rel=1e-5)
+    # by linearity: the clean stamp is centred, so the mean's centroid moves to 4 * 100 / (m00 + 100)
+    m00 = float(np.sum(clean_mean, dtype=np.float64))
+    assert oracle.moments(mean)[1] == pytest.approx(400.0 / (m00 + 100.0), rel=1e-5)
+    assert oracle.moments(mean)[2] == pytest.approx(300.0 / (m00 + 100.0), rel=1e-5)
+    assert abs(oracle.moments(med)[1]) < 1e-9
+
+
+def test_stamp_skips_masked_nan_and_outside_pixels():
+    """Masked or NaN pixels, and stamp pixels off the image, are left out of the coadd; a
+    stamp pixel no epoch covers is 0; the median of an even count is the mean of the two
+    middle values."""
+    N, H, W = 4, 10, 10
+    sci = np.zeros((N, H, W), np.float32)
+    sci[:, 5, 5] = [1.0, 2.0, 10.0, 40.0]
+    mask = np.zeros((N, H, W), np.uint8)
+    mask[3, 5, 5] = 1                                  # drops the 40
+    sci[2, 4, 5] = np.nan                              # a NaN above the centre in epoch 2
+    z = np.zeros(N, np.int32)
+    st = oracle.stamp(sci, mask, z, z, 5, 5, 1)
+    assert st[1, 1] == pytest.approx(13.0 / 3.0)       # mean of 1, 2, 10
+    med = oracle.stamp(sci, mask, z, z, 5, 5, 1, median=True)
+    assert med[1, 1] == 2.0
+    sci[1, 5, 5] = 4.0
+    med = oracle.stamp(sci, mask, np.zeros(N, np.int32), z, 5, 5, 1, median=True)
+    assert med[1, 1] == 4.0                            # middle of 1, 4, 10
+    mask[2, 5, 5] = 1
+    med = oracle.stamp(sci, mask, z, z, 5, 5, 1, median=True)
+    assert med[1, 1] == 2.5                            # two values left: (1 + 4) / 2
+    corner = oracle.stamp(sci, None, z, z, 0, 0, 2)
+    assert np.all(corner[:2, :] == 0.0) and np.all(corner[:, :2] == 0.0)
