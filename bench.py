@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=64)
     ap.add_argument("--filter", action="store_true",
                     help="also time the Sec. 3.3 light-curve outlier filter on the kept trajectories")
+    ap.add_argument("--stamps", type=int, default=0, metavar="M",
+                    help="also time Sec. 3.3 coadded stamps (radius 10, mean and median, moments and cuts) of "
+                         "the M highest-nu trajectories")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-load", type=float, default=0.75,
                     help="arrival rate as a fraction of the capacity measured on a saturated sample")
@@ -378,6 +381,28 @@ def run_ours(args):
                           "trajectories_per_s": H * W * k / (fms * 1e-3), "rejected_epochs": nrej,
                           "trajectories": H * W * k}
         del fout
+    if args.stamps > 0:
+        # Sec. 3.3 coadded stamps of the M best trajectories of the last search (21 x 21, every epoch)
+        M, r = args.stamps, 10
+        flat = res_np.reshape(-1)
+        best = np.argpartition(-np.where(flat["vidx"] >= 0, flat["nu"], -np.inf), M - 1)[:M]
+        cx, cy, cv = flat["x0"][best].copy(), flat["y0"][best].copy(), flat["vidx"][best].copy()
+        cuts = {"max_offset": 1.0, "min_var": 0.25, "max_var": 4.0, "max_mu11": 1.0}
+        line["stamps"] = {"kernel": "stamp_kernel", "candidates": M, "radius": r, "cuts": cuts}
+        S2 = (2 * r + 1) ** 2
+        for mode in ("mean", "median"):
+            job.stamps(sci, None, cx, cy, cv, r, median=mode == "median", cuts=cuts, stream=stream)
+            s0, s1 = ev(), ev()
+            s0.record(stream)
+            for _ in range(3):
+                _, mom = job.stamps(sci, None, cx, cy, cv, r, median=mode == "median", cuts=cuts, stream=stream)
+            s1.record(stream)
+            torch.cuda.synchronize(dev)
+            sms = s0.elapsed_time(s1) / 3
+            gathered = M * S2 * N * 4 + M * S2 * 4
+            line["stamps"][mode] = {"ms_per_call": sms, "stamps_per_s": M / (sms * 1e-3),
+                                    "gathered_GBps": gathered / (sms * 1e-3) / 1e9,
+                                    "passed_cuts": int(mom["passed"].sum())}
     if args.rescore:
         line["rescore"] = {"candidates_per_pixel": k + (max(2, k // 2) if args.storage == "bf16" else max(2, k // 4)),
                            "repaired_pixels": repaired,

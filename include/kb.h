@@ -284,6 +284,47 @@ typedef struct kb_filtered {
 int kb_filter_lightcurves(kb_job *job, const kb_stack *s, double nsigma, kb_filtered *out, size_t capacity,
                           size_t *n_written, void *stream);
 
+/* ---- coadded postage stamps and central moments (Sec. 3.3) --------------- */
+
+#define KB_STAMP_MEAN 0
+#define KB_STAMP_MEDIAN 1
+#define KB_MAX_STAMP_RADIUS 15   /* stamps up to 31 x 31 */
+
+/* Central moments of one coadded stamp (coordinates relative to its centre,
+ * pixel values as weights) and the result of the Gaussian-similarity cut. */
+typedef struct kb_moments {
+    double m00;            /* sum of the stamp */
+    double mx, my;         /* centroid */
+    double mu20, mu02, mu11; /* central second moments over m00 */
+    int32_t passed;        /* 1: passed the cuts (or no cuts given), 0: rejected */
+    int32_t reserved;
+} kb_moments;
+
+/* Cuts of the moment filter: a stamp passes when m00 > 0, |mx|, |my| <=
+ * max_offset, min_var <= mu20, mu02 <= max_var and |mu11| <= max_mu11. */
+typedef struct kb_moment_cuts {
+    double max_offset, min_var, max_var, max_mu11;
+} kb_moment_cuts;
+
+/* Sec. 3.3: coadded postage stamps along candidate trajectories of the job's
+ * last search.  For candidate i (start pixel (x0[i], y0[i]), velocity vidx[i]
+ * of that search) and stamp pixel (sx, sy) in [-r, r]^2, the values of
+ * sci[e][y0 + dy_e + sy][x0 + dx_e + sx] over the epochs e whose pixel is in
+ * the image, finite and not masked, with the search's own trajectory offsets,
+ * combined as their mean (KB_STAMP_MEAN, FP64 sum) or median (KB_STAMP_MEDIAN:
+ * the middle value, the mean of the two middle ones for an even count); 0 where
+ * no epoch contributes.  Then the stamp's central moments and, with `cuts`, the
+ * moment filter.
+ *   sci, mask  DEVICE [N][H][W] science images (and mask or NULL), the job's N, H, W
+ *   x0, y0, vidx  HOST [n] candidates
+ *   stamps     DEVICE float [n][2r+1][2r+1]; moments DEVICE [n] or NULL
+ * KB_EINVAL (no search yet, shapes, r outside 0..KB_MAX_STAMP_RADIUS, a
+ * candidate outside the image or velocity range, pointers).  Stream-ordered;
+ * the host arrays are read before the call returns. */
+int kb_stamps(kb_job *job, const float *sci, const uint8_t *mask, int N, int H, int W, const int32_t *x0,
+              const int32_t *y0, const int32_t *vidx, int n, int radius, int mode, const kb_moment_cuts *cuts,
+              float *stamps, kb_moments *moments, void *stream);
+
 /* Device bytes that one search will hold, for admission under an HBM budget:
  *   *stack  kb_stack_create(N, H, W, storage) plus kb_make_psi_phi with a K x K
  *           PSF (an upper bound: the tap table of a non-separable PSF)

@@ -32,6 +32,11 @@ FILTERED_DTYPE = np.dtype([("x0", "<i4"), ("y0", "<i4"), ("vidx", "<i4"), ("nobs
                            ("nu", "<f8"), ("alpha", "<f8")])
 assert FILTERED_DTYPE.itemsize == 72
 
+MOMENTS_DTYPE = np.dtype([("m00", "<f8"), ("mx", "<f8"), ("my", "<f8"), ("mu20", "<f8"), ("mu02", "<f8"),
+                          ("mu11", "<f8"), ("passed", "<i4"), ("reserved", "<i4")])
+assert MOMENTS_DTYPE.itemsize == 56
+KB_STAMP_MEAN, KB_STAMP_MEDIAN, KB_MAX_STAMP_RADIUS = 0, 1, 15
+
 if not os.path.exists(LIB_PATH):
     raise ImportError("libkb.so is not built (run paper_1901_02492_gb300.build.build() or "
                       "__graft_entry__.build()); there is no fallback path")
@@ -74,6 +79,8 @@ _kb_make_psi_phi_static = _sig("kb_make_psi_phi_static", _i32,
 _kb_estimate_bytes = _sig("kb_estimate_bytes", _i32, [_i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32,
                                                        ctypes.POINTER(_sz), ctypes.POINTER(_sz)])
 _kb_filter_lightcurves = _sig("kb_filter_lightcurves", _i32, [_P, _P, ctypes.c_double, _P, _sz, ctypes.POINTER(_sz), _P])
+_kb_stamps = _sig("kb_stamps", _i32, [_P, _P, _P, _i32, _i32, _i32, _P, _P, _P, _i32, _i32, _i32, _P, _P, _P,
+                                      _P])
 _kb_batch_create = _sig("kb_batch_create", _i32, [_P, _i32, _P, _i32, ctypes.POINTER(_P)])
 _kb_batch_run = _sig("kb_batch_run", _i32, [_P, _P])
 _kb_batch_groups = _sig("kb_batch_groups", _i32, [_P, _P, _i32, ctypes.POINTER(_i32)])
@@ -84,7 +91,14 @@ EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_s
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
             "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static",
             "kb_batch_create", "kb_batch_run", "kb_batch_groups", "kb_batch_free", "kb_estimate_bytes",
-            "kb_filter_lightcurves"]
+            "kb_filter_lightcurves", "kb_stamps"]
+
+
+class MomentCuts(ctypes.Structure):
+    """kb_moment_cuts: a stamp passes when m00 > 0, |mx|, |my| <= max_offset,
+    min_var <= mu20, mu02 <= max_var and |mu11| <= max_mu11."""
+    _fields_ = [("max_offset", ctypes.c_double), ("min_var", ctypes.c_double), ("max_var", ctypes.c_double),
+                ("max_mu11", ctypes.c_double)]
 
 
 class KBError(RuntimeError):
@@ -300,6 +314,36 @@ class Job:
         if out is None:
             return dev.cpu().numpy().view(FILTERED_DTYPE).reshape(self.H, self.W, self.k or self.topk)
         return out
+
+    def stamps(self, sci, mask, x0, y0, vidx, radius, median=False, cuts=None, moments=True, stream=None):
+        """Sec. 3.3 coadded stamps of candidates (x0, y0, vidx) of the last search from the device
+        science images sci [N][H][W] (float32) and mask (uint8 or None).  Returns the device
+        stamps [n][2r+1][2r+1] (float32) and, with moments, a MOMENTS_DTYPE numpy array [n].
+        cuts: None or a MomentCuts (or a dict of its fields)."""
+        import torch
+        x0 = np.ascontiguousarray(x0, np.int32)
+        y0 = np.ascontiguousarray(y0, np.int32)
+        vidx = np.ascontiguousarray(vidx, np.int32)
+        n = x0.size
+        if y0.size != n or vidx.size != n:
+            raise ValueError("x0, y0 and vidx differ in length")
+        N, H, W = sci.shape
+        if sci.dtype != torch.float32 or not sci.is_contiguous():
+            raise ValueError("sci must be a contiguous float32 [N][H][W] tensor")
+        if mask is not None and (mask.dtype != torch.uint8 or not mask.is_contiguous() or mask.shape != sci.shape):
+            raise ValueError("mask must be a contiguous uint8 tensor of the images' shape")
+        S = 2 * int(radius) + 1
+        dev = sci.device
+        st = torch.empty((n, S, S), dtype=torch.float32, device=dev)
+        mo = torch.empty(n * MOMENTS_DTYPE.itemsize, dtype=torch.uint8, device=dev) if moments else None
+        if isinstance(cuts, dict):
+            cuts = MomentCuts(**cuts)
+        self.ctx.check(_kb_stamps(self.h, _ptr(sci), _ptr(mask), N, H, W, _ptr(x0), _ptr(y0), _ptr(vidx), n,
+                                  int(radius), KB_STAMP_MEDIAN if median else KB_STAMP_MEAN,
+                                  None if cuts is None else ctypes.byref(cuts), _ptr(st), _ptr(mo), _stream(stream)))
+        if mo is None:
+            return st, None
+        return st, mo.cpu().numpy().view(MOMENTS_DTYPE)
 
     def free(self):
         if self.h:

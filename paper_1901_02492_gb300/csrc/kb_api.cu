@@ -1218,6 +1218,61 @@ int kb_filter_lightcurves(kb_job *job, const kb_stack *s, double nsigma, kb_filt
     return KB_OK;
 }
 
+int kb_stamps(kb_job *job, const float *sci, const uint8_t *mask, int N, int H, int W, const int32_t *x0,
+              const int32_t *y0, const int32_t *vidx, int n, int radius, int mode, const kb_moment_cuts *cuts,
+              float *stamps, kb_moments *moments, void *stream) {
+    if (!job) return KB_EINVAL;
+    kb_ctx *ctx = job->ctx;
+    if (job->k == 0) return fail(ctx, KB_EINVAL, "kb_stamps: no search has run on this job");
+    if (N != job->N || H != job->H || W != job->W)
+        return fail(ctx, KB_EINVAL, "kb_stamps: images %dx%dx%d are not the searched stack's %dx%dx%d", N, H, W,
+                    job->N, job->H, job->W);
+    if (radius < 0 || radius > KB_MAX_STAMP_RADIUS || (mode != KB_STAMP_MEAN && mode != KB_STAMP_MEDIAN) || n < 0)
+        return fail(ctx, KB_EINVAL, "kb_stamps: radius %d, mode %d or count %d out of range", radius, mode, n);
+    if (n == 0) return KB_OK;
+    if (!sci || !stamps || !x0 || !y0 || !vidx || !is_device_ptr(sci) || !is_device_ptr(stamps) ||
+        (mask && !is_device_ptr(mask)) || (moments && !is_device_ptr(moments)))
+        return fail(ctx, KB_EINVAL, "kb_stamps: images, stamps and moments must be device memory, candidates host");
+    std::vector<int4> cand(n);
+    for (int i = 0; i < n; ++i) {
+        if (x0[i] < 0 || x0[i] >= W || y0[i] < 0 || y0[i] >= H || vidx[i] < 0 || vidx[i] >= job->V)
+            return fail(ctx, KB_EINVAL, "kb_stamps: candidate %d (%d, %d, v %d) outside the search", i, x0[i], y0[i],
+                        vidx[i]);
+        cand[i] = make_int4(x0[i], y0[i], vidx[i], 0);
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int4 *dcand = nullptr;
+    size_t acct = 0;
+    int rc = dev_alloc(ctx, (size_t)n * sizeof(int4), (void **)&dcand, &acct);
+    if (rc != KB_OK) return rc;
+    kb::StampArgs a;
+    a.sci = sci;
+    a.mask = mask;
+    a.N = N;
+    a.H = H;
+    a.W = W;
+    a.epoch_of = job->epoch_of;
+    a.offs = job->offs;
+    a.cand = dcand;
+    a.n = n;
+    a.r = radius;
+    a.mode = mode;
+    a.cut = cuts != nullptr;
+    if (cuts) a.cuts = *cuts;
+    a.stamps = stamps;
+    a.moments = moments;
+    cudaError_t e = cudaMemcpyAsync(dcand, cand.data(), (size_t)n * sizeof(int4), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = kb::launch_stamps(a, st);
+    // the copy reads the host vector and the kernel the candidate list: both done before they go
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2;
+    dev_free(ctx, dcand);
+    dev_release(ctx, acct);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_stamps");
+    return KB_OK;
+}
+
 int kb_job_repaired(kb_job *job, size_t *n_pixels) {
     if (!job || !n_pixels) return KB_EINVAL;
     *n_pixels = 0;

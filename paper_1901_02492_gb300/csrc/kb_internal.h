@@ -237,4 +237,20 @@ struct FilterArgs {
 };
 cudaError_t launch_filter(const FilterArgs &a, cudaStream_t st);
 
+// Sec. 3.3 postage stamps and moments
+struct StampArgs {
+    const float *sci;        // [N][H][W]
+    const uint8_t *mask;     // [N][H][W] or null
+    int N, H, W;
+    const int *epoch_of;     // [N] time order -> stack epoch
+    const int2 *offs;        // [V][N] time order
+    const int4 *cand;        // [n] (x0, y0, vidx, 0)
+    int n, r, mode;
+    bool cut;
+    kb_moment_cuts cuts;
+    float *stamps;           // [n][S][S]
+    kb_moments *moments;     // [n] or null
+};
+cudaError_t launch_stamps(const StampArgs &a, cudaStream_t st);
+
 }  // namespace kb

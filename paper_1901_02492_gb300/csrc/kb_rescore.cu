@@ -413,6 +413,107 @@ cudaError_t launch_filter(const FilterArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Sec. 3.3 postage stamps: one CTA per candidate, one thread per stamp pixel.
+// A thread gathers its pixel's science values over the epochs along the search's
+// trajectory offsets (finite, unmasked, in the image), then takes their mean
+// (FP64 sum) or median (insertion sort of at most N values in local memory).
+// The CTA then reduces the stamp's central moments in FP64 and applies the cuts.
+__global__ void stamp_kernel(StampArgs a) {
+    __shared__ double red[6][32];
+    const int S = 2 * a.r + 1, npx = S * S;
+    const size_t plane = (size_t)a.H * a.W;
+    for (int c = blockIdx.x; c < a.n; c += gridDim.x) {
+        const int4 q = a.cand[c];
+        const int2 *ov = a.offs + (long long)q.z * a.N;
+        const int t = threadIdx.x;
+        float val = 0.0f;
+        if (t < npx) {
+            const int sy = t / S - a.r, sx = t % S - a.r;
+            float vals[KB_MAX_EPOCHS];
+            int m = 0;
+            double sum = 0.0;
+            for (int j = 0; j < a.N; ++j) {
+                const int2 d = __ldg(ov + j);
+                const int x = q.x + d.x + sx, y = q.y + d.y + sy;
+                if ((unsigned)x >= (unsigned)a.W || (unsigned)y >= (unsigned)a.H) continue;
+                const size_t i = (size_t)a.epoch_of[j] * plane + (size_t)y * a.W + x;
+                const float v = __ldg(a.sci + i);
+                if (!isfinite(v) || (a.mask && __ldg(a.mask + i))) continue;
+                if (a.mode == KB_STAMP_MEAN) {
+                    sum += (double)v;
+                } else {
+                    int k = m;                           // insertion into the sorted prefix
+                    while (k > 0 && vals[k - 1] > v) {
+                        vals[k] = vals[k - 1];
+                        --k;
+                    }
+                    vals[k] = v;
+                }
+                ++m;
+            }
+            if (m > 0)
+                val = a.mode == KB_STAMP_MEAN ? (float)(sum / m)
+                      : ((m & 1) ? vals[m / 2] : (float)(0.5 * ((double)vals[m / 2 - 1] + (double)vals[m / 2])));
+            a.stamps[(size_t)c * npx + t] = val;
+        }
+        if (!a.moments) continue;
+        // moments: sums of v, x v, y v, then (after the centroid) the central ones
+        const double x = t < npx ? (double)(t % S - a.r) : 0.0, y = t < npx ? (double)(t / S - a.r) : 0.0;
+        const double v = t < npx ? (double)val : 0.0;
+        double s[6] = {v, x * v, y * v, 0.0, 0.0, 0.0};
+        const int lane = t & 31, w = t >> 5, nw = (blockDim.x + 31) >> 5;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int lo = pass == 0 ? 0 : 3;
+            for (int i = lo; i < lo + 3; ++i) {
+                double u = s[i];
+                for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+                if (lane == 0) red[i][w] = u;
+            }
+            __syncthreads();
+            if (t < 32)
+                for (int i = lo; i < lo + 3; ++i) {
+                    double u = t < nw ? red[i][t] : 0.0;
+                    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+                    if (t == 0) red[i][0] = u;
+                }
+            __syncthreads();
+            if (pass == 0) {
+                const double m00 = red[0][0];
+                const double cx = m00 != 0.0 ? red[1][0] / m00 : 0.0, cy = m00 != 0.0 ? red[2][0] / m00 : 0.0;
+                s[3] = (x - cx) * (x - cx) * v;
+                s[4] = (y - cy) * (y - cy) * v;
+                s[5] = (x - cx) * (y - cy) * v;
+            }
+        }
+        if (t == 0) {
+            kb_moments mo;
+            mo.m00 = red[0][0];
+            const bool any = mo.m00 != 0.0;
+            mo.mx = any ? red[1][0] / mo.m00 : 0.0;
+            mo.my = any ? red[2][0] / mo.m00 : 0.0;
+            mo.mu20 = any ? red[3][0] / mo.m00 : 0.0;
+            mo.mu02 = any ? red[4][0] / mo.m00 : 0.0;
+            mo.mu11 = any ? red[5][0] / mo.m00 : 0.0;
+            mo.reserved = 0;
+            mo.passed = !a.cut || (mo.m00 > 0.0 && fabs(mo.mx) <= a.cuts.max_offset &&
+                                   fabs(mo.my) <= a.cuts.max_offset && mo.mu20 >= a.cuts.min_var &&
+                                   mo.mu20 <= a.cuts.max_var && mo.mu02 >= a.cuts.min_var &&
+                                   mo.mu02 <= a.cuts.max_var && fabs(mo.mu11) <= a.cuts.max_mu11);
+            a.moments[c] = mo;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_stamps(const StampArgs &a, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    const int S = 2 * a.r + 1;
+    const int threads = ((S * S + 31) / 32) * 32;
+    const int blocks = a.n < 152 * 16 ? a.n : 152 * 16;
+    stamp_kernel<<<blocks, threads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_expand(const ExpandArgs &a, cudaStream_t st) {
     if (a.count <= 0) return cudaSuccess;
     long long blocks = (a.count + 255) / 256;

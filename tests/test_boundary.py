@@ -72,17 +72,29 @@ def test_batch_struct_layouts_match_binding(tmp_path, lib):
         assert vals[1:] == [getattr(cls, f).offset for f in fs], name
 
 
-def test_filtered_record_layout_matches_binding(tmp_path, lib):
-    names = list(lib.FILTERED_DTYPE.names)
-    src = tmp_path / "flayout.c"
+def _c_layout(tmp_path, struct, names):
+    src = tmp_path / ("%s.c" % struct)
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "kb.h"\nint main(void){'
-                   'printf("%zu", sizeof(kb_filtered));'
-                   + "".join('printf(" %%zu", offsetof(kb_filtered, %s));' % f for f in names) + "return 0;}\n")
-    exe = tmp_path / "flayout"
+                   'printf("%%zu", sizeof(%s));' % struct
+                   + "".join('printf(" %%zu", offsetof(%s, %s));' % (struct, f) for f in names) + "return 0;}\n")
+    exe = tmp_path / struct
     subprocess.run(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
-    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    assert vals[0] == lib.FILTERED_DTYPE.itemsize
-    assert vals[1:] == [lib.FILTERED_DTYPE.fields[f][1] for f in names]
+    return [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+
+
+@pytest.mark.parametrize("struct,dtype", [("kb_filtered", "FILTERED_DTYPE"), ("kb_moments", "MOMENTS_DTYPE")])
+def test_record_layouts_match_binding(tmp_path, lib, struct, dtype):
+    dt = getattr(lib, dtype)
+    vals = _c_layout(tmp_path, struct, list(dt.names))
+    assert vals[0] == dt.itemsize
+    assert vals[1:] == [dt.fields[f][1] for f in dt.names]
+
+
+def test_moment_cuts_layout_matches_binding(tmp_path, lib):
+    names = [f[0] for f in lib.MomentCuts._fields_]
+    vals = _c_layout(tmp_path, "kb_moment_cuts", names)
+    assert vals[0] == ctypes.sizeof(lib.MomentCuts)
+    assert vals[1:] == [getattr(lib.MomentCuts, f).offset for f in names]
 
 
 def test_offsets_bit_exact_against_oracle(lib):
