@@ -68,6 +68,7 @@ def _load():
             lib.kbo_filter_lightcurve.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64, P, P, P, P, P]
             lib.kbo_stamp.argtypes = [P, P, i32, i32, i32, P, P, i32, i32, i32, i32, P]
             lib.kbo_moments.argtypes = [P, i32, P, P, P, P, P, P]
+            lib.kbo_cluster.argtypes = [P, P, P, P, P, P, ctypes.c_long, f64, f64, f64, i32, P, P, P]
             lib.kbo_search_pixels.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64, P, P, i64, P]
             lib.kbo_search_region.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64,
                                               i32, i32, i32, i32, P]
@@ -219,6 +220,25 @@ def moments(st):
     vals = [ctypes.c_double() for _ in range(6)]
     lib.kbo_moments(_ptr(st), r, *[ctypes.byref(v) for v in vals])
     return tuple(v.value for v in vals)
+
+
+def cluster(x0, y0, vx, vy, nu, vidx, w_pos, w_vel, eps, min_samples):
+    """Sec. 3.3 DBSCAN de-duplication (reading in kb_oracle.c): (label int32, keep bool, core bool)
+    per candidate.  label: the group's lowest core index, a noise point's own index, -1 for vidx < 0."""
+    lib = _load()
+    x0 = _c(x0, np.int32)
+    y0 = _c(y0, np.int32)
+    vx = _c(vx, np.float32)
+    vy = _c(vy, np.float32)
+    nu = _c(nu, np.float64)
+    vidx = _c(vidx, np.int32)
+    n = x0.size
+    label = np.empty(n, np.int32)
+    keep = np.empty(n, np.uint8)
+    core = np.empty(n, np.uint8)
+    lib.kbo_cluster(_ptr(x0), _ptr(y0), _ptr(vx), _ptr(vy), _ptr(nu), _ptr(vidx), n, float(w_pos), float(w_vel),
+                    float(eps), int(min_samples), _ptr(label), _ptr(keep), _ptr(core))
+    return label, keep.astype(bool), core.astype(bool)
 
 
 def search_region(psi, phi, times, dx, dy, k, nu_min=-np.inf, region=None):

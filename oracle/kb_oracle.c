@@ -20,6 +20,8 @@
  *                      of the others, recompute the likelihood (reading below)
  *   postage stamps     Sec. 3.3: mean / median coadd of science-image stamps along
  *                      a trajectory, and the stamp's central moments
+ *   de-duplication     Sec. 3.3: DBSCAN over (x0, y0, vx, vy), the highest-likelihood
+ *                      trajectory of each group kept (reading below)
  *
  * Readings of points the paper leaves open:
  *   - a pixel is masked when its mask byte is non-zero, when n or sigma^2 is not
@@ -530,4 +532,92 @@ void kbo_moments(const float *stamp, int r, double *m00, double *mx, double *my,
     *mu20 = a / s;
     *mu02 = b / s;
     *mu11 = c / s;
+}
+
+/* ---- Sec. 3.3: DBSCAN de-duplication of candidate trajectories -------------
+ *
+ * Reading.  The paper groups similar trajectories with DBSCAN over the start
+ * pixel and the velocity and keeps the highest-likelihood one of each group.
+ * It gives no metric or parameters.  Here the distance between candidates i, j
+ * is the Euclidean distance of (x0 w_pos, y0 w_pos, vx w_vel, vy w_vel),
+ * evaluated in FP64 as
+ *     d2 = ((ax*ax + ay*ay) + au*au) + av*av,
+ *     ax = (double)(x0_i - x0_j) * w_pos, ay likewise,
+ *     au = ((double)vx_i - (double)vx_j) * w_vel, av likewise,
+ * and j is a neighbour of i when d2 <= eps*eps (i is its own neighbour).
+ * DBSCAN's definitions then fix:
+ *   - core point: at least min_samples neighbours;
+ *   - clusters: the connected components of core points under the neighbour
+ *     relation, each labelled by the lowest index among its core points;
+ *   - border point (not core, with a core neighbour): DBSCAN lets it join any
+ *     neighbouring cluster; here it joins the cluster of its nearest core
+ *     neighbour (smallest d2, then lowest index), which makes the result unique;
+ *   - noise point (neither): a group of its own, labelled by its own index.
+ * Candidates with vidx < 0 (empty result slots) take no part: label -1.
+ * Of each group the member with the largest nu (then lowest index) is kept.
+ */
+static double kbo_cluster_d2(const int32_t *x0, const int32_t *y0, const float *vx, const float *vy, double w_pos,
+                             double w_vel, long i, long j) {
+    double ax = (double)((int64_t)x0[i] - (int64_t)x0[j]) * w_pos;
+    double ay = (double)((int64_t)y0[i] - (int64_t)y0[j]) * w_pos;
+    double au = ((double)vx[i] - (double)vx[j]) * w_vel;
+    double av = ((double)vy[i] - (double)vy[j]) * w_vel;
+    return ((ax * ax + ay * ay) + au * au) + av * av;
+}
+
+void kbo_cluster(const int32_t *x0, const int32_t *y0, const float *vx, const float *vy, const double *nu,
+                 const int32_t *vidx, long n, double w_pos, double w_vel, double eps, int min_samples,
+                 int32_t *label, uint8_t *keep, uint8_t *core) {
+    const double eps2 = eps * eps;
+    /* core points: neighbour counts by brute force */
+    for (long i = 0; i < n; ++i) {
+        long cnt = 0;
+        if (vidx[i] >= 0)
+            for (long j = 0; j < n; ++j)
+                if (vidx[j] >= 0 && kbo_cluster_d2(x0, y0, vx, vy, w_pos, w_vel, i, j) <= eps2) ++cnt;
+        core[i] = vidx[i] >= 0 && cnt >= min_samples;
+        label[i] = -1;
+        keep[i] = 0;
+    }
+    /* clusters: breadth-first search over core points, started in index order,
+       so each component is labelled by its lowest core index */
+    long *queue = (long *)malloc((size_t)(n > 0 ? n : 1) * sizeof(long));
+    for (long s = 0; s < n; ++s) {
+        if (!core[s] || label[s] >= 0) continue;
+        long head = 0, tail = 0;
+        queue[tail++] = s;
+        label[s] = (int32_t)s;
+        while (head < tail) {
+            long i = queue[head++];
+            for (long j = 0; j < n; ++j)
+                if (core[j] && label[j] < 0 && kbo_cluster_d2(x0, y0, vx, vy, w_pos, w_vel, i, j) <= eps2) {
+                    label[j] = (int32_t)s;
+                    queue[tail++] = j;
+                }
+        }
+    }
+    free(queue);
+    /* border and noise points */
+    for (long i = 0; i < n; ++i) {
+        if (vidx[i] < 0 || core[i]) continue;
+        long best = -1;
+        double bd = 0.0;
+        for (long j = 0; j < n; ++j) {
+            if (!core[j]) continue;
+            double d2 = kbo_cluster_d2(x0, y0, vx, vy, w_pos, w_vel, i, j);
+            if (d2 <= eps2 && (best < 0 || d2 < bd)) {
+                best = j;
+                bd = d2;
+            }
+        }
+        label[i] = best >= 0 ? label[best] : (int32_t)i;
+    }
+    /* the best member of each group */
+    for (long i = 0; i < n; ++i) {
+        if (label[i] < 0) continue;
+        int best = 1;
+        for (long j = 0; j < n && best; ++j)
+            if (j != i && label[j] == label[i] && (nu[j] > nu[i] || (nu[j] == nu[i] && j < i))) best = 0;
+        keep[i] = (uint8_t)best;
+    }
 }

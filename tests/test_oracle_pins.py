@@ -612,3 +612,144 @@ def test_stamp_skips_masked_nan_and_outside_pixels():
     assert med[1, 1] == 2.5                            # two values left: (1 + 4) / 2
     corner = oracle.stamp(sci, None, z, z, 0, 0, 2)
     assert np.all(corner[:2, :] == 0.0) and np.all(corner[:, :2] == 0.0)
+
+
+# ------------------------------------------------------------ Sec. 3.3 DBSCAN de-duplication
+
+def _hand_clusters():
+    """Two clusters in velocity space (start pixel 0, w_vel = 1, eps = 1, min_samples = 4), each with
+    one core point (a0 = (0, 0), b0 = (1.9, 0)) and three border points; p = (0.95, 0) lies at
+    exactly the same distance 0.95 from both cores (float(1.9) = 2 float(0.95)) with only 3
+    neighbours; q is noise; an empty slot (vidx -1) lies next to p."""
+    v = [(0.0, 0.0), (-0.9, 0.0), (-0.5, 0.8), (-0.3, -0.9),          # A: a0..a3, indices 0-3
+         (1.9, 0.0), (2.8, 0.0), (2.4, 0.8), (2.2, -0.9),             # B: b0..b3, indices 4-7
+         (0.95, 0.0),                                                 # p, index 8
+         (10.0, 10.0),                                                # q, index 9
+         (0.95, 0.05)]                                                # empty slot, index 10
+    vx = np.array([a for a, _ in v], np.float32)
+    vy = np.array([b for _, b in v], np.float32)
+    n = len(v)
+    nu = np.arange(n, dtype=np.float64)
+    nu[8] = 100.0                                      # p is A's best member
+    vidx = np.zeros(n, np.int32)
+    vidx[10] = -1
+    return np.zeros(n, np.int32), np.zeros(n, np.int32), vx, vy, nu, vidx
+
+
+def test_cluster_hand_example():
+    x0, y0, vx, vy, nu, vidx = _hand_clusters()
+    label, keep, core = oracle.cluster(x0, y0, vx, vy, nu, vidx, 1.0, 1.0, 1.0, 4)
+    assert list(np.nonzero(core)[0]) == [0, 4]          # a0 has a1, a2, a3, p; b0 likewise
+    # p ties between a0 and b0: the lower core index wins
+    assert list(label) == [0, 0, 0, 0, 4, 4, 4, 4, 0, 9, -1]
+    assert list(np.nonzero(keep)[0]) == [7, 8, 9]        # B's best is b3 (nu 7), A's is p, q alone
+    # moved towards b0, p joins B
+    vx2 = vx.copy()
+    vx2[8] = np.float32(0.96)
+    label2, _, _ = oracle.cluster(x0, y0, vx2, vy, nu, vidx, 1.0, 1.0, 1.0, 4)
+    assert label2[8] == 4
+    # the empty slot would have made p a core point (and merged A and B) had it counted
+    vidx2 = vidx.copy()
+    vidx2[10] = 3
+    label3, _, core3 = oracle.cluster(x0, y0, vx, vy, nu, vidx2, 1.0, 1.0, 1.0, 4)
+    assert core3[8] and label3[4] == 0 and label3[8] == 0
+
+
+def _clumps(rng, n_clumps, per, spread_px, spread_v, n_noise, W=500, V=300.0):
+    """Candidates around clump centres (start pixel, velocity) plus scattered ones."""
+    x0, y0, vx, vy = [], [], [], []
+    for _ in range(n_clumps):
+        cx, cy = rng.integers(0, W, 2)
+        cu, cv = rng.uniform(-V, V, 2)
+        m = int(rng.integers(1, per + 1))
+        x0 += list(np.clip(cx + rng.integers(-spread_px, spread_px + 1, m), 0, W - 1))
+        y0 += list(np.clip(cy + rng.integers(-spread_px, spread_px + 1, m), 0, W - 1))
+        vx += list(cu + rng.normal(0, spread_v, m))
+        vy += list(cv + rng.normal(0, spread_v, m))
+    x0 += list(rng.integers(0, W, n_noise))
+    y0 += list(rng.integers(0, W, n_noise))
+    vx += list(rng.uniform(-V, V, n_noise))
+    vy += list(rng.uniform(-V, V, n_noise))
+    n = len(x0)
+    return (np.array(x0, np.int32), np.array(y0, np.int32), np.array(vx, np.float32), np.array(vy, np.float32),
+            rng.normal(5.0, 2.0, n), np.where(rng.random(n) < 0.02, -1, 1).astype(np.int32))
+
+
+def _scaled(x0, y0, vx, vy, w_pos, w_vel):
+    return np.stack([x0.astype(np.float64) * w_pos, y0.astype(np.float64) * w_pos,
+                     vx.astype(np.float64) * w_vel, vy.astype(np.float64) * w_vel], axis=1)
+
+
+@pytest.mark.parametrize("min_samples", [2, 3, 5])
+def test_cluster_against_sklearn_dbscan(min_samples):
+    """Core points, the partition of core points and the noise set equal scikit-learn's DBSCAN on
+    the weighted features; border points sit in a cluster that has a core point within eps."""
+    sk = pytest.importorskip("sklearn.cluster")
+    rng = np.random.default_rng(40 + min_samples)
+    x0, y0, vx, vy, nu, vidx = _clumps(rng, 120, 12, 3, 4.0, 300)
+    w_pos, w_vel, eps = 1.0, 0.5, 4.0
+    label, keep, core = oracle.cluster(x0, y0, vx, vy, nu, vidx, w_pos, w_vel, eps, min_samples)
+    ok = vidx >= 0
+    feats = _scaled(x0, y0, vx, vy, w_pos, w_vel)[ok]
+    db = sk.DBSCAN(eps=eps, min_samples=min_samples).fit(feats)
+    idx = np.nonzero(ok)[0]
+    sk_core = np.zeros(x0.size, bool)
+    sk_core[idx[db.core_sample_indices_]] = True
+    assert np.array_equal(core, sk_core)
+    assert np.all(label[~ok] == -1) and not keep[~ok].any()
+    sk_label = np.full(x0.size, -2)
+    sk_label[idx] = db.labels_
+    # the same partition of the core points
+    pairs = {}
+    for i in np.nonzero(core)[0]:
+        assert pairs.setdefault(label[i], sk_label[i]) == sk_label[i]
+    assert len(set(pairs.values())) == len(pairs)
+    # noise: sklearn's -1 exactly where a point is its own group without being core
+    own = ok & ~core & (label == np.arange(x0.size))
+    assert np.array_equal(own, sk_label == -1)
+    # border points: in a cluster with a core point within eps
+    d2 = lambda i, j: float(np.sum((feats[np.searchsorted(idx, i)] - feats[np.searchsorted(idx, j)]) ** 2))
+    for i in np.nonzero(ok & ~core & ~own)[0]:
+        members = np.nonzero(core & (label == label[i]))[0]
+        assert min(d2(i, j) for j in members) <= eps * eps * (1 + 1e-12)
+    assert 10 < len(pairs) and own.sum() > 10
+    if min_samples > 2:                              # with 2, every point with a neighbour is core
+        assert (ok & ~core & ~own).sum() > 10
+
+
+def test_cluster_min_samples_one_is_connected_components():
+    """With min_samples = 1 every candidate is core and the groups are the connected components of
+    the eps-neighbour graph (scipy), each labelled by its lowest index."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    from scipy.spatial.distance import cdist
+    rng = np.random.default_rng(41)
+    x0, y0, vx, vy, nu, _ = _clumps(rng, 80, 10, 2, 1.0, 150)
+    vidx = np.zeros(x0.size, np.int32)
+    w_pos, w_vel, eps = 0.5, 1.0, 3.0
+    label, keep, core = oracle.cluster(x0, y0, vx, vy, nu, vidx, w_pos, w_vel, eps, 1)
+    assert core.all()
+    f = _scaled(x0, y0, vx, vy, w_pos, w_vel)
+    ncomp, comp = connected_components(csr_matrix(cdist(f, f) <= eps), directed=False)
+    for c in range(ncomp):
+        members = np.nonzero(comp == c)[0]
+        assert np.all(label[members] == members.min())
+        best = members[np.lexsort((members, -nu[members]))[0]]
+        assert list(np.nonzero(keep[members])[0]) == [list(members).index(best)]
+    assert ncomp < x0.size // 2
+
+
+def test_cluster_permutation_relabels_consistently():
+    rng = np.random.default_rng(42)
+    x0, y0, vx, vy, nu, vidx = _clumps(rng, 60, 10, 3, 4.0, 100)
+    args = (1.0, 0.5, 4.0, 3)
+    label, keep, core = oracle.cluster(x0, y0, vx, vy, nu, vidx, *args)
+    p = rng.permutation(x0.size)
+    l2, k2, c2 = oracle.cluster(x0[p], y0[p], vx[p], vy[p], nu[p], vidx[p], *args)
+    assert np.array_equal(c2, core[p]) and np.array_equal(k2, keep[p])
+    # same groups: candidates share a label after permuting iff they did before (core points;
+    # border points may choose another cluster only on an exact distance tie, absent here)
+    for a, b in [(label, l2[np.argsort(p)])]:
+        m = {}
+        for u, w in zip(a, b):
+            assert m.setdefault(u, w) == w
