@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--stamps", type=int, default=0, metavar="M",
                     help="also time Sec. 3.3 coadded stamps (radius 10, mean and median, moments and cuts) of "
                          "the M highest-nu trajectories")
+    ap.add_argument("--cluster", type=int, default=0, metavar="M",
+                    help="also time Sec. 3.3 DBSCAN de-duplication of the M highest-nu trajectories")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-load", type=float, default=0.75,
                     help="arrival rate as a fraction of the capacity measured on a saturated sample")
@@ -403,6 +405,25 @@ def run_ours(args):
             line["stamps"][mode] = {"ms_per_call": sms, "stamps_per_s": M / (sms * 1e-3),
                                     "gathered_GBps": gathered / (sms * 1e-3) / 1e9,
                                     "passed_cuts": int(mom["passed"].sum())}
+    if args.cluster > 0:
+        # Sec. 3.3 DBSCAN de-duplication of the M best trajectories of the last search: 2 px and
+        # 15 px/day (about half the velocity grid's radial step) per unit, eps 1.5, min_samples 4
+        M = args.cluster
+        flat = res_np.reshape(-1)
+        best = np.sort(np.argpartition(-np.where(flat["vidx"] >= 0, flat["nu"], -np.inf), M - 1)[:M])
+        cand = torch.from_numpy(flat[best].view(np.uint8).copy()).to(dev)
+        prm = dict(w_pos=0.5, w_vel=1.0 / 15.0, eps=1.5, min_samples=4)
+        ctx.cluster(cand, stream=stream, **prm)
+        c0, c1 = ev(), ev()
+        c0.record(stream)
+        for _ in range(3):
+            _, keep, _, groups = ctx.cluster(cand, stream=stream, **prm)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        cms = c0.elapsed_time(c1) / 3
+        line["cluster"] = {"kernels": "kb_cluster (7 launches)", "candidates": M, "params": prm,
+                           "ms_per_call": cms, "candidates_per_s": M / (cms * 1e-3), "groups": groups}
+        del cand
     if args.rescore:
         line["rescore"] = {"candidates_per_pixel": k + (max(2, k // 2) if args.storage == "bf16" else max(2, k // 4)),
                            "repaired_pixels": repaired,

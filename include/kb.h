@@ -325,6 +325,43 @@ int kb_stamps(kb_job *job, const float *sci, const uint8_t *mask, int N, int H, 
               const int32_t *y0, const int32_t *vidx, int n, int radius, int mode, const kb_moment_cuts *cuts,
               float *stamps, kb_moments *moments, void *stream);
 
+/* ---- de-duplication of candidates (Sec. 3.3) ------------------------------ */
+
+typedef struct kb_cluster_params {
+    double w_pos;        /* weight of the start-pixel coordinates (1/px) */
+    double w_vel;        /* weight of the velocity coordinates (day/px) */
+    double eps;          /* neighbourhood radius in the weighted coordinates */
+    int32_t min_samples; /* neighbours (the point included) that make a core point */
+    int32_t reserved;
+} kb_cluster_params;
+
+/* Sec. 3.3: groups similar candidate trajectories with DBSCAN and keeps the
+ * highest-likelihood trajectory of each group.  The distance between
+ * candidates i and j is the Euclidean distance of (x0 w_pos, y0 w_pos,
+ * vx w_vel, vy w_vel), evaluated in FP64 as
+ *     d2 = ((ax*ax + ay*ay) + au*au) + av*av,
+ *     ax = (double)(x0_i - x0_j) * w_pos (ay likewise),
+ *     au = ((double)vx_i - (double)vx_j) * w_vel (av likewise),
+ * every operation rounded (no fused multiply-add); j is a neighbour of i when
+ * d2 <= eps*eps, i included.  Then:
+ *   core point   at least min_samples neighbours;
+ *   cluster      a connected component of core points under the neighbour
+ *                relation, labelled by its lowest core index;
+ *   border point a non-core point with a core neighbour: joins the cluster of
+ *                its nearest core neighbour (smallest d2, then lowest index);
+ *   noise point  a group of its own, labelled by its own index;
+ *   vidx < 0     (an empty result slot) takes no part: label -1, keep 0.
+ * keep[i] = 1 for the member of each group with the largest nu (then lowest
+ * index).
+ *   cand       DEVICE [n] kb_result records (e.g. from kb_results)
+ *   label      DEVICE [n] int32; keep DEVICE [n] uint8; core DEVICE [n] or NULL
+ *   n_groups   HOST, or NULL: the number of kept candidates
+ * KB_EINVAL (n > 2^29, weights or eps not positive and finite, min_samples < 1,
+ * pointers, or a weighted coordinate beyond 2^30 eps).  Stream-ordered on
+ * `stream`; returns after the stream has finished the call's work. */
+int kb_cluster(kb_ctx *ctx, const kb_result *cand, size_t n, const kb_cluster_params *p, int32_t *label,
+               uint8_t *keep, uint8_t *core, size_t *n_groups, void *stream);
+
 /* Device bytes that one search will hold, for admission under an HBM budget:
  *   *stack  kb_stack_create(N, H, W, storage) plus kb_make_psi_phi with a K x K
  *           PSF (an upper bound: the tap table of a non-separable PSF)

@@ -81,6 +81,7 @@ _kb_estimate_bytes = _sig("kb_estimate_bytes", _i32, [_i32, _i32, _i32, _i32, _i
 _kb_filter_lightcurves = _sig("kb_filter_lightcurves", _i32, [_P, _P, ctypes.c_double, _P, _sz, ctypes.POINTER(_sz), _P])
 _kb_stamps = _sig("kb_stamps", _i32, [_P, _P, _P, _i32, _i32, _i32, _P, _P, _P, _i32, _i32, _i32, _P, _P, _P,
                                       _P])
+_kb_cluster = _sig("kb_cluster", _i32, [_P, _P, _sz, _P, _P, _P, _P, ctypes.POINTER(_sz), _P])
 _kb_batch_create = _sig("kb_batch_create", _i32, [_P, _i32, _P, _i32, ctypes.POINTER(_P)])
 _kb_batch_run = _sig("kb_batch_run", _i32, [_P, _P])
 _kb_batch_groups = _sig("kb_batch_groups", _i32, [_P, _P, _i32, ctypes.POINTER(_i32)])
@@ -91,7 +92,13 @@ EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_s
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
             "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static",
             "kb_batch_create", "kb_batch_run", "kb_batch_groups", "kb_batch_free", "kb_estimate_bytes",
-            "kb_filter_lightcurves", "kb_stamps"]
+            "kb_filter_lightcurves", "kb_stamps", "kb_cluster"]
+
+
+class ClusterParams(ctypes.Structure):
+    """kb_cluster_params: weights of the start pixel and velocity coordinates, eps, min_samples."""
+    _fields_ = [("w_pos", ctypes.c_double), ("w_vel", ctypes.c_double), ("eps", ctypes.c_double),
+                ("min_samples", _i32), ("reserved", _i32)]
 
 
 class MomentCuts(ctypes.Structure):
@@ -167,6 +174,25 @@ class Context:
     @property
     def hbm_in_use(self) -> int:
         return int(_kb_hbm_in_use(self.h))
+
+    def cluster(self, cand, w_pos, w_vel, eps, min_samples, core=False, stream=None):
+        """Sec. 3.3 DBSCAN de-duplication of device kb_result records `cand` (a CUDA tensor
+        holding RESULT_DTYPE records).  Returns (label int32, keep bool, core bool or None) as
+        device tensors and the number of groups."""
+        import torch
+        nbytes = cand.numel() * cand.element_size()
+        if nbytes % RESULT_DTYPE.itemsize or not cand.is_contiguous():
+            raise ValueError("cand must be a contiguous tensor of kb_result records")
+        n = nbytes // RESULT_DTYPE.itemsize
+        dev = cand.device
+        label = torch.empty(n, dtype=torch.int32, device=dev)
+        keep = torch.empty(n, dtype=torch.uint8, device=dev)
+        cor = torch.empty(n, dtype=torch.uint8, device=dev) if core else None
+        p = ClusterParams(float(w_pos), float(w_vel), float(eps), int(min_samples), 0)
+        groups = _sz()
+        self.check(_kb_cluster(self.h, _ptr(cand), n, ctypes.byref(p), _ptr(label), _ptr(keep), _ptr(cor),
+                               ctypes.byref(groups), _stream(stream)))
+        return label, keep.bool(), None if cor is None else cor.bool(), int(groups.value)
 
     def close(self):
         if self.h:

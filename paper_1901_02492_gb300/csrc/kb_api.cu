@@ -1273,6 +1273,70 @@ int kb_stamps(kb_job *job, const float *sci, const uint8_t *mask, int N, int H, 
     return KB_OK;
 }
 
+int kb_cluster(kb_ctx *ctx, const kb_result *cand, size_t n, const kb_cluster_params *p, int32_t *label,
+               uint8_t *keep, uint8_t *core, size_t *n_groups, void *stream) {
+    if (!ctx || !p) return fail(ctx, KB_EINVAL, "kb_cluster: null context or parameters");
+    if (n_groups) *n_groups = 0;
+    if (n > ((size_t)1 << 29))
+        return fail(ctx, KB_EINVAL, "kb_cluster: %zu candidates (at most 2^29)", n);
+    auto pos_fin = [](double v) { return std::isfinite(v) && v > 0.0; };
+    if (!pos_fin(p->w_pos) || !pos_fin(p->w_vel) || !pos_fin(p->eps) || p->min_samples < 1)
+        return fail(ctx, KB_EINVAL, "kb_cluster: weights %g, %g, eps %g must be positive and finite, "
+                    "min_samples %d >= 1", p->w_pos, p->w_vel, p->eps, p->min_samples);
+    if (n == 0) return KB_OK;
+    if (!cand || !label || !keep || !is_device_ptr(cand) || !is_device_ptr(label) || !is_device_ptr(keep) ||
+        (core && !is_device_ptr(core)))
+        return fail(ctx, KB_EINVAL, "kb_cluster: candidates and outputs must be device memory");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int T = 1;
+    while (T < 2 * (int)n) T <<= 1;
+    const size_t words = 2 * (size_t)T + 3 * n;   // owner, head | next, parent, bestidx
+    const size_t bytes = words * sizeof(int) + n * sizeof(unsigned long long) + n + 2 * sizeof(int) + 16;
+    void *buf = nullptr;
+    size_t acct = 0;
+    int rc = dev_alloc(ctx, bytes, &buf, &acct);
+    if (rc != KB_OK) return rc;
+    kb::ClusterArgs a;
+    a.cand = cand;
+    a.n = (int)n;
+    a.T = T;
+    a.w_pos = p->w_pos;
+    a.w_vel = p->w_vel;
+    a.eps2 = p->eps * p->eps;
+    // cells a little wider than eps: the rounding of the weighted coordinates
+    // cannot put two neighbours more than one cell apart
+    a.inv_side = 1.0 / (p->eps * (1.0 + 1.0 / 1048576.0));
+    a.min_samples = p->min_samples;
+    unsigned long long *bestnu = reinterpret_cast<unsigned long long *>(buf);
+    int *w = reinterpret_cast<int *>(bestnu + n);
+    a.bestnu = bestnu;
+    a.owner = w;
+    a.head = w + T;
+    a.next = w + 2 * (size_t)T;
+    a.parent = a.next + n;
+    a.bestidx = a.parent + n;
+    a.count = reinterpret_cast<unsigned *>(a.bestidx + n);
+    a.status = reinterpret_cast<int *>(a.count + 1);
+    a.core = reinterpret_cast<uint8_t *>(a.status + 1);
+    a.label = label;
+    a.keep = keep;
+    a.core_out = core;
+    unsigned hc[2] = {0u, 0u};
+    cudaError_t e = kb::launch_cluster(a, ctx->sm_count, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, a.count, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2;
+    dev_free(ctx, buf);
+    dev_release(ctx, acct);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_cluster");
+    if (hc[1] == 1)
+        return fail(ctx, KB_EINVAL, "kb_cluster: a weighted coordinate is beyond 2^30 eps (weights or eps unusable)");
+    if (hc[1] != 0) return fail(ctx, KB_ECUDA, "kb_cluster: an internal loop bound was reached (status %u)", hc[1]);
+    if (n_groups) *n_groups = hc[0];
+    return KB_OK;
+}
+
 int kb_job_repaired(kb_job *job, size_t *n_pixels) {
     if (!job || !n_pixels) return KB_EINVAL;
     *n_pixels = 0;

@@ -253,4 +253,23 @@ struct StampArgs {
 };
 cudaError_t launch_stamps(const StampArgs &a, cudaStream_t st);
 
+// Sec. 3.3 de-duplication (DBSCAN over start pixel and velocity)
+struct ClusterArgs {
+    const kb_result *cand;   // [n]
+    int n, T;                // candidates, hash slots (a power of two >= 2n)
+    double w_pos, w_vel, eps2, inv_side;
+    int min_samples;
+    int *owner, *head;       // [T] first candidate of the slot's cell, list head
+    int *next, *parent;      // [n]
+    uint8_t *core;           // [n]
+    unsigned long long *bestnu;  // [n] per group: ordered bits of the best nu
+    int *bestidx;            // [n] per group: lowest index reaching it
+    int32_t *label;          // [n] out
+    uint8_t *keep;           // [n] out
+    uint8_t *core_out;       // [n] out or null
+    unsigned *count;         // groups kept
+    int *status;             // 1: coordinates out of range, 2: a loop bound was reached
+};
+cudaError_t launch_cluster(const ClusterArgs &a, int sm_count, cudaStream_t st);
+
 }  // namespace kb
