@@ -421,7 +421,7 @@ def run_ours(args):
         c1.record(stream)
         torch.cuda.synchronize(dev)
         cms = c0.elapsed_time(c1) / 3
-        line["cluster"] = {"kernels": "kb_cluster (7 launches)", "candidates": M, "params": prm,
+        line["cluster"] = {"kernels": "kb_cluster (8 launches)", "candidates": M, "params": prm,
                            "ms_per_call": cms, "candidates_per_s": M / (cms * 1e-3), "groups": groups}
         del cand
     if args.rescore:

@@ -1292,7 +1292,8 @@ int kb_cluster(kb_ctx *ctx, const kb_result *cand, size_t n, const kb_cluster_pa
     int T = 1;
     while (T < 2 * (int)n) T <<= 1;
     const size_t words = 2 * (size_t)T + 3 * n;   // owner, head | next, parent, bestidx
-    const size_t bytes = words * sizeof(int) + n * sizeof(unsigned long long) + n + 2 * sizeof(int) + 16;
+    const size_t bytes = 2 * n * sizeof(int4) + n * sizeof(unsigned long long) + words * sizeof(int) +
+                         2 * sizeof(int) + 2 * n + 16;
     void *buf = nullptr;
     size_t acct = 0;
     int rc = dev_alloc(ctx, bytes, &buf, &acct);
@@ -1308,7 +1309,9 @@ int kb_cluster(kb_ctx *ctx, const kb_result *cand, size_t n, const kb_cluster_pa
     // cannot put two neighbours more than one cell apart
     a.inv_side = 1.0 / (p->eps * (1.0 + 1.0 / 1048576.0));
     a.min_samples = p->min_samples;
-    unsigned long long *bestnu = reinterpret_cast<unsigned long long *>(buf);
+    a.pts = reinterpret_cast<int4 *>(buf);
+    a.cells = a.pts + n;
+    unsigned long long *bestnu = reinterpret_cast<unsigned long long *>(a.cells + n);
     int *w = reinterpret_cast<int *>(bestnu + n);
     a.bestnu = bestnu;
     a.owner = w;
@@ -1319,6 +1322,7 @@ int kb_cluster(kb_ctx *ctx, const kb_result *cand, size_t n, const kb_cluster_pa
     a.count = reinterpret_cast<unsigned *>(a.bestidx + n);
     a.status = reinterpret_cast<int *>(a.count + 1);
     a.core = reinterpret_cast<uint8_t *>(a.status + 1);
+    a.valid = a.core + n;
     a.label = label;
     a.keep = keep;
     a.core_out = core;

@@ -2,10 +2,11 @@
 //
 // Distance, core points, clusters, border and noise points are as documented at
 // kb_cluster in include/kb.h.  The GPU form:
-//   - a 4-D uniform grid of cells a little wider than eps (in the weighted
-//     coordinates), so that every neighbour of a point lies in the 3^4 cells
-//     around its own; the cells live in an open-addressing hash table whose
-//     slots hold a linked list of their points (built with atomics);
+//   - a first pass packs each candidate into 16 bytes (x0, y0, vx, vy) and
+//     computes its cell of a 4-D uniform grid of cells a little wider than eps
+//     (in the weighted coordinates), so that every neighbour of a point lies in
+//     the 3^4 cells around its own; the cells live in an open-addressing hash
+//     table whose slots hold a linked list of their points (built with atomics);
 //   - neighbour counts (stopping at min_samples) give the core points;
 //   - a lock-free union-find over the core points, always hooking the larger
 //     root under the smaller, so every cluster ends rooted at its lowest core
@@ -27,11 +28,12 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ double dist2(const kb_result &a, const kb_result &b, double w_pos, double w_vel) {
-    const double ax = __dmul_rn((double)((long long)a.x0 - (long long)b.x0), w_pos);
-    const double ay = __dmul_rn((double)((long long)a.y0 - (long long)b.y0), w_pos);
-    const double au = __dmul_rn(__dsub_rn((double)a.vx, (double)b.vx), w_vel);
-    const double av = __dmul_rn(__dsub_rn((double)a.vy, (double)b.vy), w_vel);
+// Points are packed as (x0, y0, bits of vx, bits of vy).
+__device__ __forceinline__ double dist2(int4 a, int4 b, double w_pos, double w_vel) {
+    const double ax = __dmul_rn((double)((long long)a.x - (long long)b.x), w_pos);
+    const double ay = __dmul_rn((double)((long long)a.y - (long long)b.y), w_pos);
+    const double au = __dmul_rn(__dsub_rn((double)__int_as_float(a.z), (double)__int_as_float(b.z)), w_vel);
+    const double av = __dmul_rn(__dsub_rn((double)__int_as_float(a.w), (double)__int_as_float(b.w)), w_vel);
     return __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(au, au)),
                      __dmul_rn(av, av));
 }
@@ -59,8 +61,8 @@ __device__ __forceinline__ unsigned hash4(int4 c, unsigned mask) {
 }
 
 __device__ __forceinline__ bool same_cell(const ClusterArgs &a, int o, int4 c) {
-    int4 d;
-    return cell_of(a.cand[o], a, d) && d.x == c.x && d.y == c.y && d.z == c.z && d.w == c.w;
+    const int4 d = a.cells[o];
+    return d.x == c.x && d.y == c.y && d.z == c.z && d.w == c.w;
 }
 
 // Slot of cell c in the finished table, or -1.
@@ -110,15 +112,25 @@ __global__ void init_kernel(ClusterArgs a) {
     }
 }
 
-__global__ void insert_kernel(ClusterArgs a) {
+__global__ void prep_kernel(ClusterArgs a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         const kb_result r = a.cand[i];
-        if (r.vidx < 0) continue;
-        int4 c;
-        if (!cell_of(r, a, c)) {
+        int4 c = make_int4(0, 0, 0, 0);
+        bool ok = r.vidx >= 0;
+        if (ok && !cell_of(r, a, c)) {
             atomicExch(a.status, 1);
-            continue;
+            ok = false;
         }
+        a.pts[i] = make_int4(r.x0, r.y0, __float_as_int(r.vx), __float_as_int(r.vy));
+        a.cells[i] = c;
+        a.valid[i] = ok ? 1 : 0;
+    }
+}
+
+__global__ void insert_kernel(ClusterArgs a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        if (!a.valid[i]) continue;
+        const int4 c = a.cells[i];
         unsigned s = hash4(c, a.T - 1);
         bool placed = false;
         for (int probe = 0; probe < a.T && !placed; ++probe) {
@@ -136,9 +148,8 @@ __global__ void insert_kernel(ClusterArgs a) {
 
 // Visits every candidate j in the 3^4 cells around i's cell; f(j) returns false to stop.
 template <class F>
-__device__ void for_neighbours(const ClusterArgs &a, const kb_result &r, F f) {
-    int4 c;
-    if (!cell_of(r, a, c)) return;
+__device__ void for_neighbours(const ClusterArgs &a, int i, F f) {
+    const int4 c = a.cells[i];
     for (int d = 0; d < 81; ++d) {
         const int4 q = make_int4(c.x + d % 3 - 1, c.y + (d / 3) % 3 - 1, c.z + (d / 9) % 3 - 1, c.w + d / 27 - 1);
         const int s = find_slot(a, q);
@@ -153,14 +164,16 @@ __device__ void for_neighbours(const ClusterArgs &a, const kb_result &r, F f) {
 
 __global__ void core_kernel(ClusterArgs a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        const kb_result r = a.cand[i];
+        const bool ok = a.valid[i];
         int cnt = 0;
-        if (r.vidx >= 0)
-            for_neighbours(a, r, [&](int j) {
-                if (dist2(r, a.cand[j], a.w_pos, a.w_vel) <= a.eps2) ++cnt;
+        if (ok) {
+            const int4 p = a.pts[i];
+            for_neighbours(a, i, [&](int j) {
+                if (dist2(p, a.pts[j], a.w_pos, a.w_vel) <= a.eps2) ++cnt;
                 return cnt < a.min_samples;
             });
-        a.core[i] = (r.vidx >= 0 && cnt >= a.min_samples) ? 1 : 0;
+        }
+        a.core[i] = (ok && cnt >= a.min_samples) ? 1 : 0;
     }
 }
 
@@ -168,9 +181,9 @@ __global__ void union_kernel(ClusterArgs a) {
     volatile int *parent = a.parent;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         if (!a.core[i]) continue;
-        const kb_result r = a.cand[i];
-        for_neighbours(a, r, [&](int j) {
-            if (j < i && a.core[j] && dist2(r, a.cand[j], a.w_pos, a.w_vel) <= a.eps2) {
+        const int4 p = a.pts[i];
+        for_neighbours(a, i, [&](int j) {
+            if (j < i && a.core[j] && dist2(p, a.pts[j], a.w_pos, a.w_vel) <= a.eps2) {
                 int u = i, v = j;
                 for (int it = 0; it <= 2 * a.n + 2; ++it) {
                     u = find_root(parent, u, a.n, a.status);
@@ -194,17 +207,17 @@ __global__ void union_kernel(ClusterArgs a) {
 __global__ void label_kernel(ClusterArgs a) {
     volatile int *parent = a.parent;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        const kb_result r = a.cand[i];
         int lab = -1;
-        if (r.vidx >= 0) {
+        if (a.valid[i]) {
             if (a.core[i]) {
                 lab = find_root(parent, i, a.n, a.status);
             } else {
+                const int4 p = a.pts[i];
                 int best = -1;
                 double bd = 0.0;
-                for_neighbours(a, r, [&](int j) {
+                for_neighbours(a, i, [&](int j) {
                     if (a.core[j]) {
-                        const double d2 = dist2(r, a.cand[j], a.w_pos, a.w_vel);
+                        const double d2 = dist2(p, a.pts[j], a.w_pos, a.w_vel);
                         if (d2 <= a.eps2 && (best < 0 || d2 < bd || (d2 == bd && j < best))) {
                             best = j;
                             bd = d2;
@@ -214,7 +227,7 @@ __global__ void label_kernel(ClusterArgs a) {
                 });
                 lab = best >= 0 ? find_root(parent, best, a.n, a.status) : i;
             }
-            atomicMax(&a.bestnu[lab], nu_key(r.nu));
+            atomicMax(&a.bestnu[lab], nu_key(a.cand[i].nu));
         }
         a.label[i] = lab;
         if (a.core_out) a.core_out[i] = a.core[i];
@@ -247,6 +260,7 @@ cudaError_t launch_cluster(const ClusterArgs &a, int sm_count, cudaStream_t st) 
     auto grid = [&](long long m) { return (int)std::max(1LL, std::min<long long>((m + kThreads - 1) / kThreads, cap)); };
     init_kernel<<<grid(std::max<long long>(a.T, a.n)), kThreads, 0, st>>>(a);
     if (a.n > 0) {
+        prep_kernel<<<grid(a.n), kThreads, 0, st>>>(a);
         insert_kernel<<<grid(a.n), kThreads, 0, st>>>(a);
         core_kernel<<<grid(a.n), kThreads, 0, st>>>(a);
         union_kernel<<<grid(a.n), kThreads, 0, st>>>(a);

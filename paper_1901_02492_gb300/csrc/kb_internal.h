@@ -259,6 +259,8 @@ struct ClusterArgs {
     int n, T;                // candidates, hash slots (a power of two >= 2n)
     double w_pos, w_vel, eps2, inv_side;
     int min_samples;
+    int4 *pts, *cells;       // [n] packed (x0, y0, vx bits, vy bits), grid cell
+    uint8_t *valid;          // [n] takes part (vidx >= 0, cell in range)
     int *owner, *head;       // [T] first candidate of the slot's cell, list head
     int *next, *parent;      // [n]
     uint8_t *core;           // [n]
