@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--psf", default="gaussian", choices=["gaussian", "general"],
+                    help="gaussian: the separable 17x17 Gaussians; general: rotated elliptical Gaussians "
+                         "(not separable: the single-pass kernel over all K^2 taps)")
     ap.add_argument("--rescore", action="store_true")
     ap.add_argument("--size", type=int, default=4096, help="image side (4096 = the DECam workload)")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -93,17 +96,46 @@ def setup_device(world, local):
     return dev
 
 
-def workload(size):
+def workload(size, psf="gaussian"):
     import synth
     st = synth.decam(H=size, W=size)
+    if psf == "general":
+        st.psf = synth.elongate_psfs(st.psf)       # rotated elliptical Gaussians: not separable
     return st
+
+
+def roofline_psi_phi(args, st, ms, nbytes, hbm, clocks):
+    """Stage (a) roofline.  Separable PSFs: HBM-bound (8 B read, 8 B written per pixel, more
+    with 16-bit storage).  General PSFs: 2 K^2 FP32 FMAs per pixel (psi and phi) make it
+    arithmetic-bound; the peak is 128 FP32 FMA lanes per SM x 2 FLOP x SM count x the SM clock
+    sampled during the run."""
+    import torch
+    line = {"bound": "hbm", "kernel": "psi_phi_sep_kernel", "ms_per_launch": ms,
+            "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    if args.psf == "general":
+        N, H, W = st.sci.shape
+        K = st.psf.shape[-1]
+        flops = 4.0 * N * H * W * K * K
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        mhz = clocks.get("sm_mhz") or 2070.0
+        peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        tf = flops / (ms * 1e-3) / 1e12
+        line = {"bound": "alu", "kernel": "psi_phi_gen_kernel<%d>" % K, "ms_per_launch": ms,
+                "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                "flops_per_launch": flops,
+                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (sampled SM clock)" % (sms, mhz),
+                "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm}
+    return line
 
 
 def workload_config(args, st, world):
     N, H, W = st.sci.shape
     name = "decam %dx%dx%d, %d velocities, k=%d" % (N, H, W, st.vx.size, st.k)
     return {"workload": name, "epochs": N, "height": H, "width": W, "velocities": int(st.vx.size),
-            "topk": st.k, "psf": "17x17 Gaussian, FWHM 3.5-4.5 px", "storage": args.storage,
+            "topk": st.k, "psf": ("17x17 Gaussian, FWHM 3.5-4.5 px" if args.psf == "gaussian" else
+                                  "17x17 rotated elliptical Gaussian, major FWHM 3.5-4.5 px, axis ratio "
+                                  "0.6-0.9 (not separable)"), "storage": args.storage,
             "rescore_fp64": bool(args.rescore), "search_variant": args.variant, "carveout": args.carveout,
             "evals_per_step": int(N * H * W * st.vx.size),
             "l2": "inputs larger than L2 (%.2f GB of psi/phi planes)" % (N * H * W * 8 / 1e9),
@@ -225,7 +257,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    st = workload(args.size)
+    st = workload(args.size, args.psf)
     cfg = workload_config(args, st, 1)
     rng = np.random.default_rng(1234)
     per_step = max(2.0, min(10.0, 150.0 / max(args.steps + args.warmup, 1)))
@@ -262,7 +294,7 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_1901_02492_gb300 import binding as kb
 
-    st = workload(args.size)
+    st = workload(args.size, args.psf)
     N, H, W = st.sci.shape
     V = st.vx.size
     if args.topk:
@@ -358,10 +390,7 @@ def run_ours(args):
                          "peak_source": "measured in this run by kb_measure_gather_peak: L2-resident 256-byte "
                                         "warp-span loads (the search's access form), no HBM or L1 term",
                          "ms_per_launch": ms_search, "alg_bytes_per_launch": alg_bytes},
-            "roofline_psi_phi": {"bound": "hbm", "kernel": "psi_phi_sep_kernel", "ms_per_launch": ms_psiphi,
-                                 "achieved": psiphi_bytes / (ms_psiphi * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                                 "frac": psiphi_bytes / (ms_psiphi * 1e-3) / 1e9 / hbm,
-                                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "roofline_psi_phi": roofline_psi_phi(args, st, ms_psiphi, psiphi_bytes, hbm, clocks),
             "clocks": clocks,
             "e2e": {"value": world * evals / (e2e_ms * 1e-3), "unit": "evals/s",
                     "h2d_bytes_per_step": int(sci_h.numel() * 4 + var_h.numel() * 4),

@@ -9,7 +9,10 @@
 //   - separable PSF T(dy, dx) = a(dy) b(dx): a horizontal pass into a second
 //     shared tile and a vertical pass to the output (2 K taps per pixel), or
 //   - general PSF: a single pass over the K x K taps (the paper's own choice,
-//     Sec. 2.3, kept for non-Gaussian PSFs).
+//     Sec. 2.3, kept for non-Gaussian PSFs).  For the common sides (K <= 21) a
+//     register-blocked form: each thread owns VR consecutive output rows of one
+//     column and walks the tap columns, holding a column of taps in registers,
+//     so one shared load of the tile feeds up to VR outputs.
 // The (psi, phi) pair is carried through both passes as one 64-bit register pair
 // and updated with packed fma.rn.f32x2.  The kernel is HBM-bound: it reads 8 B
 // (9 B with a mask) and writes 8 B per pixel.
@@ -207,6 +210,68 @@ __global__ void __launch_bounds__(THREADS) psi_phi_sep_kernel(PsiPhiArgs a) {
     }
 }
 
+// General PSF, register-blocked, K = KT taps per side (3 <= KT <= 21).  Thread
+// (column c, strip s) computes rows s*VR .. s*VR+VR-1 of column c.  For each tap
+// column dx it keeps T(., dx) in registers and streams the VR + K - 1 tile rows
+// of column c + dx through them: every output accumulates its taps with one
+// packed FMA each, tap columns outer, tap rows inner.
+constexpr int GVR = 16, GTY = (THREADS / TX) * GVR;   // rows per thread, rows per CTA
+
+template <int KT>
+__global__ void __launch_bounds__(THREADS) psi_phi_gen_kernel(PsiPhiArgs a) {
+    extern __shared__ float4 smem_raw[];
+    constexpr int K = KT, r = K / 2, VR = GVR;
+    constexpr int AW = TX + 2 * r, AH = GTY + 2 * r;
+    const int e = blockIdx.z;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * GTY;
+    float *s_taps = reinterpret_cast<float *>(smem_raw);
+    constexpr int ntaps = 2 * K * K;
+    float2 *A = reinterpret_cast<float2 *>(s_taps + ((ntaps + 3) & ~3));
+    const float *taps = a.taps + (size_t)e * ntaps;
+    for (int i = threadIdx.x; i < ntaps; i += THREADS) s_taps[i] = taps[i];
+    stage_tile(a, e, x0, y0, r, AW, AH, A);
+    __syncthreads();
+
+    const float2 *t = reinterpret_cast<const float2 *>(s_taps);
+    const int c = threadIdx.x % TX, oy = (threadIdx.x / TX) * VR;
+    float2 o[VR];
+#pragma unroll
+    for (int i = 0; i < VR; ++i) o[i] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+    for (int dx = 0; dx < K; ++dx) {
+        float2 tc[K];
+#pragma unroll
+        for (int dy = 0; dy < K; ++dy) tc[dy] = t[dy * K + dx];
+        const float2 *col = A + oy * AW + c + dx;
+#pragma unroll
+        for (int j = 0; j < VR + K - 1; ++j) {
+            const float2 v = col[j * AW];
+#pragma unroll
+            for (int i = 0; i < VR; ++i)
+                if (j - i >= 0 && j - i < K) o[i] = fma2(v, tc[j - i], o[i]);
+        }
+    }
+    float2 *out = a.out + e * a.plane_elems + a.origin;
+    float mpsi = 0.0f, mphi = 0.0f;
+    const int x = x0 + c;
+#pragma unroll
+    for (int i = 0; i < VR; ++i) {
+        const int y = y0 + oy + i;
+        if (y < a.H && x < a.W) {
+            out[(long long)y * a.pitch + x] = o[i];
+            track_max(a, o[i], mpsi, mphi);
+        }
+    }
+    if (a.maxbits) {
+        unsigned bp = __reduce_max_sync(0xffffffffu, __float_as_uint(mpsi));
+        unsigned bf = __reduce_max_sync(0xffffffffu, __float_as_uint(mphi));
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(a.maxbits + 2 * e, bp);
+            atomicMax(a.maxbits + 2 * e + 1, bf);
+        }
+    }
+}
+
 // General PSF: one pass over the K x K taps (the single-pass form of Sec. 2.3).
 __global__ void __launch_bounds__(THREADS) psi_phi_kernel(PsiPhiArgs a) {
     extern __shared__ float4 smem_raw[];
@@ -322,6 +387,18 @@ cudaError_t launch_sep(const PsiPhiArgs &a, dim3 grid, size_t smem, cudaStream_t
     return cudaGetLastError();
 }
 
+template <int KT>
+cudaError_t launch_gen(const PsiPhiArgs &a, dim3, size_t, cudaStream_t st) {
+    constexpr int r = KT / 2;
+    const dim3 grid((a.W + TX - 1) / TX, (a.H + GTY - 1) / GTY, a.N);
+    const size_t smem = ((2 * KT * KT + 3) & ~3) * sizeof(float) + (size_t)(GTY + 2 * r) * (TX + 2 * r) * sizeof(float2);
+    cudaError_t err = cudaFuncSetAttribute(psi_phi_gen_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    psi_phi_gen_kernel<KT><<<grid, THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_psi_phi(const PsiPhiArgs &a, cudaStream_t st) {
     dim3 grid((a.W + TX - 1) / TX, (a.H + TY - 1) / TY, a.N);
     size_t smem = psi_phi_smem(a.K, a.separable);
@@ -339,6 +416,19 @@ cudaError_t launch_psi_phi(const PsiPhiArgs &a, cudaStream_t st) {
             case 21: return launch_sep<21>(a, grid, smem, st);
             default: return launch_sep<0>(a, grid, smem, st);
         }
+    }
+    switch (a.K) {   // register-blocked single pass for the common sides
+        case 3: return launch_gen<3>(a, grid, smem, st);
+        case 5: return launch_gen<5>(a, grid, smem, st);
+        case 7: return launch_gen<7>(a, grid, smem, st);
+        case 9: return launch_gen<9>(a, grid, smem, st);
+        case 11: return launch_gen<11>(a, grid, smem, st);
+        case 13: return launch_gen<13>(a, grid, smem, st);
+        case 15: return launch_gen<15>(a, grid, smem, st);
+        case 17: return launch_gen<17>(a, grid, smem, st);
+        case 19: return launch_gen<19>(a, grid, smem, st);
+        case 21: return launch_gen<21>(a, grid, smem, st);
+        default: break;
     }
     cudaError_t err = cudaFuncSetAttribute(psi_phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;

@@ -62,6 +62,33 @@ def gaussian_psf(K: int, sigma: float) -> np.ndarray:
     return (k2 / k2.sum()).astype(np.float32)
 
 
+def elliptical_psf(K: int, sigma_major: float, sigma_minor: float, theta: float) -> np.ndarray:
+    """K x K elliptical Gaussian, major axis at angle theta, normalised to sum 1 (not separable
+    unless the axes are equal or aligned with the grid)."""
+    r = K // 2
+    d = np.arange(-r, r + 1, dtype=np.float64)
+    yy, xx = np.meshgrid(d, d, indexing="ij")
+    c, s = math.cos(theta), math.sin(theta)
+    u = c * xx + s * yy
+    w = -s * xx + c * yy
+    g = np.exp(-0.5 * ((u / sigma_major) ** 2 + (w / sigma_minor) ** 2))
+    return (g / g.sum()).astype(np.float32)
+
+
+def elongate_psfs(psf: np.ndarray, seed: int = 11, q_lo: float = 0.6, q_hi: float = 0.9) -> np.ndarray:
+    """Per epoch, an elliptical version of a Gaussian PSF stack: the same major-axis width
+    (its second moment), axis ratio U[q_lo, q_hi], orientation U[0, pi)."""
+    rng = np.random.default_rng(seed)
+    N, K = psf.shape[0], psf.shape[-1]
+    r = K // 2
+    d = np.arange(-r, r + 1, dtype=np.float64)
+    out = []
+    for e in range(N):
+        sig = math.sqrt(float(np.sum(psf[e].astype(np.float64).sum(axis=0) * d ** 2)))
+        out.append(elliptical_psf(K, sig, sig * rng.uniform(q_lo, q_hi), rng.uniform(0.0, math.pi)))
+    return np.stack(out)
+
+
 def velocity_grid(n_angles, n_speeds, theta_lo, theta_hi, s_lo, s_hi, angle_endpoint=True,
                   speed_endpoint=True):
     """Linearly spaced angle x speed grid (Sec. 3.2); index = i_angle * n_speeds + j_speed."""
