@@ -253,6 +253,19 @@ int kb_job_repaired(kb_job *job, size_t *n_pixels);
  * copies).  KB_ERANGE (with *n_written = H*W*topk) if capacity is too small. */
 int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream);
 
+/* kb_results without any host wait: the expansion and the copies are enqueued
+ * on `stream` (which first waits for the job's last search), and the call
+ * returns.  A host destination is served by one expansion into job-owned
+ * device staging of H*W*topk records (allocated on first use, under the HBM
+ * budget) and one copy, so that after the short expansion only the copy engine
+ * works and the copy overlaps later kernels.  out must be device memory or page-locked host memory
+ * (cudaMallocHost / cudaHostRegister), else KB_EINVAL; it is complete once
+ * `stream` has reached this point.  A later kb_search or kb_batch_run of the
+ * job, and kb_job_free, wait on the device for the read to finish, so results
+ * of one job can be copied out while another job searches.  The search's
+ * device status is read with kb_job_wait. */
+int kb_results_async(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream);
+
 /* ---- light-curve outlier filter of kept trajectories (Sec. 3.3) ---------- */
 
 /* One filtered trajectory (72 bytes). */

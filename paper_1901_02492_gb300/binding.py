@@ -81,6 +81,7 @@ _kb_estimate_bytes = _sig("kb_estimate_bytes", _i32, [_i32, _i32, _i32, _i32, _i
 _kb_filter_lightcurves = _sig("kb_filter_lightcurves", _i32, [_P, _P, ctypes.c_double, _P, _sz, ctypes.POINTER(_sz), _P])
 _kb_stamps = _sig("kb_stamps", _i32, [_P, _P, _P, _i32, _i32, _i32, _P, _P, _P, _i32, _i32, _i32, _P, _P, _P,
                                       _P])
+_kb_results_async = _sig("kb_results_async", _i32, [_P, _P, _sz, ctypes.POINTER(_sz), _P])
 _kb_cluster = _sig("kb_cluster", _i32, [_P, _P, _sz, _P, _P, _P, _P, ctypes.POINTER(_sz), _P])
 _kb_batch_create = _sig("kb_batch_create", _i32, [_P, _i32, _P, _i32, ctypes.POINTER(_P)])
 _kb_batch_run = _sig("kb_batch_run", _i32, [_P, _P])
@@ -92,7 +93,7 @@ EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_s
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
             "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static",
             "kb_batch_create", "kb_batch_run", "kb_batch_groups", "kb_batch_free", "kb_estimate_bytes",
-            "kb_filter_lightcurves", "kb_stamps", "kb_cluster"]
+            "kb_filter_lightcurves", "kb_stamps", "kb_cluster", "kb_results_async"]
 
 
 class ClusterParams(ctypes.Structure):
@@ -323,6 +324,15 @@ class Job:
         self.ctx.check(_kb_results(self.h, _ptr(out), cap, ctypes.byref(written), _stream(stream)))
         if isinstance(out, np.ndarray):
             return out.reshape(self.H, self.W, self.k)
+        return out
+
+    def results_async(self, out, stream=None):
+        """Enqueue the records [H][W][k] into `out` (a CUDA uint8 tensor, or page-locked host memory:
+        a pinned torch tensor or a numpy view of one) on `stream` without waiting; `out` is
+        complete once the stream reaches this point."""
+        cap = (out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes) // RESULT_DTYPE.itemsize
+        written = _sz()
+        self.ctx.check(_kb_results_async(self.h, _ptr(out), cap, ctypes.byref(written), _stream(stream)))
         return out
 
     def filter_lightcurves(self, stack: Stack, nsigma=5.0, out=None, stream=None):

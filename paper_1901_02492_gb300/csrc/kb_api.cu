@@ -600,6 +600,7 @@ int kb_job_create(kb_ctx *ctx, int H, int W, int N, int V, int topk, int flags, 
         }
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->stage_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->rdone, cudaEventDisableTiming);
         if (e != cudaSuccess) rc = cuda_fail(ctx, e, "kb_job_create");
     }
     if (rc != KB_OK) {
@@ -621,6 +622,10 @@ void kb_job_free(kb_job *j) {
     if (j->done) {
         cudaStreamWaitEvent(ctx->astream, j->done, 0);   // the last search's kernels
         cudaEventDestroy(j->done);
+    }
+    if (j->rdone) {
+        cudaStreamWaitEvent(ctx->astream, j->rdone, 0);  // the last results read
+        cudaEventDestroy(j->rdone);
     }
     dev_free(ctx, j->offs);
     dev_free(ctx, j->vorder);
@@ -791,6 +796,8 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     kb::SearchArgs a;
     kb::RescoreArgs r;
     bool rescore = false;
+    // a results read still in flight (kb_results_async) must finish before the records change
+    cudaStreamWaitEvent(st, job->rdone, 0);
     int rc = prepare_search(job, s, times, vx, vy, V, topk, nu_min, flags, st, a, r, rescore);
     if (rc != KB_OK) return rc;
     cudaError_t e;
@@ -1090,7 +1097,9 @@ int kb_batch_run(kb_batch *b, void *stream) {
     kb_ctx *ctx = b->ctx;
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaGraphLaunch(b->exec, st);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < b->jobs.size() && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(st, b->jobs[i]->rdone, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, st);
     for (size_t i = 0; i < b->jobs.size() && e == cudaSuccess; ++i) e = cudaEventRecord(b->jobs[i]->done, st);
     for (size_t i = 0; i < b->stacks.size() && e == cudaSuccess; ++i) e = cudaEventRecord(b->stacks[i]->used, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_batch_run");
@@ -1127,16 +1136,16 @@ void kb_batch_free(kb_batch *b) {
     delete b;
 }
 
-int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream) {
-    if (!job) return KB_EINVAL;
+// Enqueues the expansion of the job's records into `out` (device: directly;
+// host: through the device staging buffer, each piece copied out in stream
+// order) and records rdone.  Nothing waits on the host.  `whole` stages all
+// records at once (one expansion, one copy: after the expansion only the copy
+// engine is busy, so the copy overlaps whatever runs next); otherwise pieces of
+// 2^22 records keep the staging small.
+static int enqueue_results(kb_job *job, kb_result *out, size_t need, bool dev, bool whole, cudaStream_t st) {
     kb_ctx *ctx = job->ctx;
-    if (job->k == 0) return fail(ctx, KB_EINVAL, "kb_results: no search has run on this job");
-    size_t need = (size_t)job->H * job->W * job->k;
-    if (n_written) *n_written = need;
-    if (!out) return fail(ctx, KB_EINVAL, "kb_results: out is NULL");
-    if (capacity < need) return fail(ctx, KB_ERANGE, "kb_results: capacity %zu < %zu records", capacity, need);
-    DeviceGuard g(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
+    // the job's last search must be complete before its records are read
+    cudaStreamWaitEvent(st, job->done, 0);
     kb::ExpandArgs a;
     a.recs = job->rescored ? nullptr : job->recs;
     a.recs64 = job->rescored ? job->recs64 : nullptr;
@@ -1146,17 +1155,19 @@ int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, 
     a.W = job->W;
     a.vq = job->vq;
     cudaError_t e;
-    if (is_device_ptr(out)) {
+    if (dev) {
         a.first = 0;
         a.count = (long long)need;
         a.out = out;
         e = kb::launch_expand(a, st);
+        if (e == cudaSuccess) e = cudaEventRecord(job->rdone, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "expand kernel");
         return KB_OK;
     }
-    const size_t chunk = std::min(need, (size_t)1 << 22);
+    const size_t chunk = whole ? need : std::min(need, (size_t)1 << 22);
     if (job->expand_cap < chunk) {
         cudaStreamWaitEvent(ctx->astream, job->done, 0);
+        cudaStreamWaitEvent(ctx->astream, job->rdone, 0);   // a read still using the old staging
         dev_free(ctx, job->expand);
         dev_release(ctx, job->expand_cap * sizeof(kb_result));
         job->bytes -= std::min(job->bytes, job->expand_cap * sizeof(kb_result));
@@ -1176,9 +1187,48 @@ int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, 
             e = cudaMemcpyAsync(out + first, job->expand, n * sizeof(kb_result), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_results");
     }
-    e = cudaStreamSynchronize(st);
+    e = cudaEventRecord(job->rdone, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_results");
+    return KB_OK;
+}
+
+int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream) {
+    if (!job) return KB_EINVAL;
+    kb_ctx *ctx = job->ctx;
+    if (job->k == 0) return fail(ctx, KB_EINVAL, "kb_results: no search has run on this job");
+    size_t need = (size_t)job->H * job->W * job->k;
+    if (n_written) *n_written = need;
+    if (!out) return fail(ctx, KB_EINVAL, "kb_results: out is NULL");
+    if (capacity < need) return fail(ctx, KB_ERANGE, "kb_results: capacity %zu < %zu records", capacity, need);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool dev = is_device_ptr(out);
+    int rc = enqueue_results(job, out, need, dev, false, st);
+    if (rc != KB_OK || dev) return rc;
+    cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_results");
     return kb_job_wait(job);
+}
+
+int kb_results_async(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream) {
+    if (!job) return KB_EINVAL;
+    kb_ctx *ctx = job->ctx;
+    if (job->k == 0) return fail(ctx, KB_EINVAL, "kb_results_async: no search has run on this job");
+    size_t need = (size_t)job->H * job->W * job->k;
+    if (n_written) *n_written = need;
+    if (!out) return fail(ctx, KB_EINVAL, "kb_results_async: out is NULL");
+    if (capacity < need)
+        return fail(ctx, KB_ERANGE, "kb_results_async: capacity %zu < %zu records", capacity, need);
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, out) != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    const bool dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (!dev && at.type != cudaMemoryTypeHost)
+        return fail(ctx, KB_EINVAL, "kb_results_async: out must be device or page-locked host memory");
+    DeviceGuard g(ctx->device);
+    return enqueue_results(job, out, need, dev, true, (cudaStream_t)stream);
 }
 
 int kb_filter_lightcurves(kb_job *job, const kb_stack *s, double nsigma, kb_filtered *out, size_t capacity,

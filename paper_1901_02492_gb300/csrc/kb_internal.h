@@ -125,6 +125,7 @@ struct kb_job {
     int *ucount = nullptr;       // their number (rescoring)
     int kkeep_cap = 0;
     kb_result *expand = nullptr; // device staging for host-bound kb_results (lazy)
+    cudaEvent_t rdone = nullptr; // recorded after the last results read (kb_results_async)
     kb_batch *owner = nullptr;   // the batch whose tables this job holds (kb_search refuses it)
     size_t expand_cap = 0;
     size_t bytes = 0;

@@ -293,3 +293,41 @@ def test_banded_launch_equals_single_launch(kb, ctx, k):
     finally:
         ctx.set_search_waves(-1)
     assert got.tobytes() == ref.tobytes()
+
+
+def test_results_async_overlaps_and_orders_reads(kb, ctx):
+    """kb_results_async into pinned host memory on a second stream equals kb_results; a search
+    enqueued right after the read (same job, other velocities) waits for the read, so the
+    buffer holds the first search's records; pageable host memory is refused."""
+    st = synth.small_stack(91, 6, 90, 140, K=5, nan_frac=0.01, n_angles=8, n_speeds=8, s_hi=12.0, n_sources=3,
+                           flux=40.0)
+    N, H, W = st.sci.shape
+    s = gpu_planes(kb, ctx, st)
+    jobs = [kb.Job(ctx, H, W, N, st.vx.size, st.k, 0) for _ in range(2)]
+    vx2, vy2 = st.vx[::-1].copy() * 0.5, st.vy[::-1].copy() * 0.5
+    n = H * W * st.k * kb.RESULT_DTYPE.itemsize
+    pinned = [torch.empty(n, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+    s_out = torch.cuda.Stream()
+    ref1 = None
+    for j in jobs:
+        j.search(s, st.times, st.vx, st.vy, st.k, -math.inf, 0)
+        ref1 = j.results()
+    torch.cuda.synchronize()
+    for b, j in enumerate(jobs):
+        j.search(s, st.times, st.vx, st.vy, st.k, -math.inf, 0)
+        j.results_async(pinned[b], stream=s_out)
+        j.search(s, st.times, vx2, vy2, st.k, -math.inf, 0)     # must not overtake the read
+    torch.cuda.synchronize()
+    for b, j in enumerate(jobs):
+        assert pinned[b].numpy().tobytes() == ref1.tobytes()
+        ref2 = j.results()
+        assert ref2.tobytes() != ref1.tobytes()
+        dev = torch.empty(n, dtype=torch.uint8, device=DEV)
+        j.results_async(dev)
+        torch.cuda.synchronize()
+        assert dev.cpu().numpy().tobytes() == ref2.tobytes()
+    with pytest.raises(kb.KBError):
+        jobs[0].results_async(np.empty(H * W * st.k, kb.RESULT_DTYPE))
+    for j in jobs:
+        j.free()
+    s.free()
