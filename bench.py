@@ -360,7 +360,9 @@ def run_ours(args):
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_psi = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_step(i):
+    comp_ev = []
+
+    def e2e_step(i, timed=False):
         b = i % 2
         s_in.wait_event(ev_psi[b])                 # psi/phi of step i-2 has read buffer b
         with torch.cuda.stream(s_in):
@@ -368,10 +370,15 @@ def run_ours(args):
             var_d[b].copy_(var_h, non_blocking=True)
         ev_in[b].record(s_in)
         stream.wait_event(ev_in[b])
+        if timed:
+            comp_ev.append((ev(), ev()))
+            comp_ev[-1][0].record(stream)
         stack.make_psi_phi(sci_d[b], var_d[b], None, st.psf, stream=stream)
         ev_psi[b].record(stream)
         # waits (on the device) for the read of this job's step i-2 records
         jobs[b].search(stack, st.times, st.vx, st.vy, k, -math.inf, flags, stream=stream)
+        if timed:
+            comp_ev[-1][1].record(stream)
         jobs[b].results_async(res_h[b], stream=s_out)
 
     n_e2e = max(args.e2e_steps, 2)
@@ -380,9 +387,11 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     a = time.perf_counter()
     for i in range(2, 2 + n_e2e):
-        e2e_step(i)
+        e2e_step(i, timed=True)
     torch.cuda.synchronize(dev)
     e2e_ms = 1e3 * (time.perf_counter() - a) / n_e2e
+    # device time of psi/phi + search inside the pipeline (beside the copies)
+    e2e_comp_ms = float(np.mean([t0.elapsed_time(t1) for t0, t1 in comp_ev]))
     for j in jobs:
         j.wait()
     res_np = res_h[(1 + n_e2e) % 2].numpy().view(kb.RESULT_DTYPE)   # the last step's records
@@ -418,7 +427,8 @@ def run_ours(args):
             "e2e": {"value": world * evals / (e2e_ms * 1e-3), "unit": "evals/s",
                     "h2d_bytes_per_step": int(sci_h.numel() * 4 + var_h.numel() * 4),
                     "d2h_bytes_per_step": int(H * W * k * kb.RESULT_DTYPE.itemsize), "ms_per_step": e2e_ms,
-                    "steps": n_e2e, "pipeline": "host clock over %d steps; inputs and jobs double-buffered, uploads, "
+                    "steps": n_e2e, "compute_ms_per_step": e2e_comp_ms,
+                    "pipeline": "host clock over %d steps; inputs and jobs double-buffered, uploads, "
                                                "compute and kb_results_async reads on three streams" % n_e2e},
             "gpu_launches": launches_per_step * args.steps}
     if args.filter:
