@@ -126,6 +126,16 @@ int kb_set_search_carveout(kb_ctx *ctx, int percent);
  * Results do not depend on it. */
 int kb_set_search_waves(kb_ctx *ctx, int waves);
 
+/* Tuning knob: the order in which the register-gather search kernel's CTAs
+ * take their start-pixel tiles.  cols > 0: the tiles are dealt out in
+ * super-columns `cols` tiles wide, row by row within each (so the CTAs resident
+ * at one time cover a block about cols tiles wide instead of whole rows of
+ * tiles); 0: row by row over the whole image; -1: automatic, which is 8.  The
+ * late epochs' rows that a resident block reads then stay in L2: on the
+ * 12 x 4096^2 stack (64 tiles per row) the FP32 search takes 97.7 ms with 8
+ * against 117.4 ms row by row.  Results do not depend on it. */
+int kb_set_search_swizzle(kb_ctx *ctx, int cols);
+
 /* Measurement helper (no counterpart in the paper): the L2-to-SM bandwidth, in
  * GB/s, of the search's own access form -- warp-contiguous 8-byte loads of
  * 256-byte spans at scattered offsets of an L2-resident 64 MB buffer, from every

@@ -60,6 +60,7 @@ _kb_hbm_in_use = _sig("kb_hbm_in_use", _sz, [_P])
 _kb_set_search_variant = _sig("kb_set_search_variant", _i32, [_P, _i32])
 _kb_set_search_carveout = _sig("kb_set_search_carveout", _i32, [_P, _i32])
 _kb_set_search_waves = _sig("kb_set_search_waves", _i32, [_P, _i32])
+_kb_set_search_swizzle = _sig("kb_set_search_swizzle", _i32, [_P, _i32])
 _kb_measure_gather_peak = _sig("kb_measure_gather_peak", _i32, [_P, ctypes.POINTER(ctypes.c_double)])
 _kb_stack_create = _sig("kb_stack_create", _i32, [_P, _i32, _i32, _i32, _i32, ctypes.POINTER(_P)])
 _kb_stack_free = _sig("kb_stack_free", None, [_P])
@@ -89,7 +90,7 @@ _kb_batch_groups = _sig("kb_batch_groups", _i32, [_P, _P, _i32, ctypes.POINTER(_
 _kb_batch_free = _sig("kb_batch_free", None, [_P])
 
 EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_search_variant",
-            "kb_set_search_carveout", "kb_set_search_waves", "kb_measure_gather_peak", "kb_stack_create", "kb_stack_free",
+            "kb_set_search_carveout", "kb_set_search_waves", "kb_set_search_swizzle", "kb_measure_gather_peak", "kb_stack_create", "kb_stack_free",
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
             "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static",
             "kb_batch_create", "kb_batch_run", "kb_batch_groups", "kb_batch_free", "kb_estimate_bytes",
@@ -161,6 +162,10 @@ class Context:
 
     def set_search_carveout(self, percent: int):
         self.check(_kb_set_search_carveout(self.h, int(percent)))
+
+    def set_search_swizzle(self, cols: int):
+        """Search tile order: super-columns of `cols` tiles (-1 automatic, 0 row by row)."""
+        self.check(_kb_set_search_swizzle(self.h, int(cols)))
 
     def set_search_waves(self, waves: int):
         """Launch the search in bands of `waves` resident waves of CTAs (-1 automatic, 0 one launch)."""

@@ -272,6 +272,13 @@ int kb_set_search_waves(kb_ctx *ctx, int waves) {
     return KB_OK;
 }
 
+int kb_set_search_swizzle(kb_ctx *ctx, int cols) {
+    if (!ctx) return KB_EINVAL;
+    if (cols < -1 || cols > 65535) return fail(ctx, KB_EINVAL, "swizzle %d not in -1..65535", cols);
+    ctx->search_swizzle = cols;
+    return KB_OK;
+}
+
 int kb_set_search_carveout(kb_ctx *ctx, int percent) {
     if (!ctx) return KB_EINVAL;
     if (percent < -1 || percent > 100) return fail(ctx, KB_EINVAL, "carveout %d not in -1..100", percent);
@@ -757,6 +764,9 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
     a.by0 = 0;
     a.nby = 0;
     a.waves = ctx->search_waves < 0 ? 0 : ctx->search_waves;
+    // automatic tile order: super-columns of 8 tiles (12 x 4096^2, FP32, k = 8: 97.7 ms
+    // against 117.4 ms row by row; 6 and 12 tiles within 1 %)
+    a.swz = ctx->search_swizzle < 0 ? 8 : ctx->search_swizzle;
     if (rescore) {
         r.f32 = s->f32;
         r.plane_elems = a.plane_elems;

@@ -63,6 +63,7 @@ struct kb_ctx {
     size_t smem_optin = 0;
     int search_variant = 0;   // 0 = automatic
     int search_carveout = -1; // -1 = automatic
+    int search_swizzle = -1;  // register-gather search: tile order in super-columns of this many tiles (0: rows)
     int search_waves = -1;    // register-gather search launched in bands of this many resident waves (0 and -1: one launch)
     std::string err;
     std::mutex mu;
@@ -177,6 +178,7 @@ struct SearchArgs {
     int *status;             // device status word: KB_ETIMEOUT if a bounded wait gave up
     int by0, nby;            // register-gather kernel: row tiles by0 .. by0 + nby - 1 (nby 0: all)
     int waves;               // launch in bands of this many resident waves of CTAs (0: one launch)
+    int swz;                 // tile order: super-columns of this many tiles (0: row by row)
 };
 // register-gather kernel (variant 0 = its default shape, 1..4)
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, int sm_count);

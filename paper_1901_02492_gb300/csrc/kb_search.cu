@@ -40,7 +40,11 @@
 //   - velocities are processed in the order the host planner gives (sorted by
 //     their latest-epoch offset, for L2 locality of the resident CTAs); ties in
 //     nu are broken by the caller's velocity index, so the order changes no
-//     result.
+//     result;
+//   - CTAs take their tiles in super-columns a few tiles wide, row by row within
+//     each, so the CTAs resident at one time cover a compact block of start
+//     pixels and the late epochs' rows they read stay in L2 (row-by-row order
+//     makes them span whole image rows, whose late-epoch windows fall out).
 // The Psi/Phi of each kept trajectory are recomputed at the end by the same
 // sequence of operations (bit-identical) together with nobs.
 #include <cuda_runtime.h>
@@ -467,7 +471,17 @@ template <int STORAGE, int P, int C, bool PT, typename I>
 __global__ void __launch_bounds__(THREADS, min_ctas<STORAGE, P, PT>()) search_kernel(SearchArgs a) {
     __shared__ float2 s_scale[KB_MAX_EPOCHS];
     extern __shared__ int4 s_dyn4[];
-    search_tile<STORAGE, P, C, PT, I>(a, blockIdx.x, a.by0 + blockIdx.y, s_scale, s_dyn4);
+    int bx = blockIdx.x, by = blockIdx.y;
+    if (a.swz > 0 && a.swz < (int)gridDim.x) {
+        // CTAs start roughly in linear order: deal the tiles out in super-columns of
+        // swz tiles, row by row within each (the last super-column may be narrower)
+        const int gx = gridDim.x, lin = blockIdx.y * gx + blockIdx.x;
+        const int per = a.swz * gridDim.y, s = lin / per, r = lin - s * per;
+        const int w = min(a.swz, gx - s * a.swz);
+        by = r / w;
+        bx = s * a.swz + (r - by * w);
+    }
+    search_tile<STORAGE, P, C, PT, I>(a, bx, a.by0 + by, s_scale, s_dyn4);
 }
 
 // Persistent batch search: CTAs take (job, tile) work items from an atomic

@@ -331,3 +331,17 @@ def test_results_async_overlaps_and_orders_reads(kb, ctx):
     for j in jobs:
         j.free()
     s.free()
+
+
+@pytest.mark.parametrize("cols", [1, 3, 5])
+def test_tile_order_swizzle_equals_row_order(kb, ctx, cols):
+    """kb_set_search_swizzle: tiles dealt out in super-columns (the last one narrower: 7 tile
+    columns) give the row-order records byte for byte."""
+    st = synth.small_stack(78, 4, 37, 7 * 64 - 5, K=3, n_angles=5, n_speeds=4, s_lo=5.0, s_hi=60.0, k=4)
+    ref = gpu_search(kb, ctx, st)
+    ctx.set_search_swizzle(cols)
+    try:
+        got = gpu_search(kb, ctx, st)
+    finally:
+        ctx.set_search_swizzle(-1)
+    assert got.tobytes() == ref.tobytes()
