@@ -883,8 +883,12 @@ void make_items(const kb_batch *b, int g, int variant, double frac, std::vector<
             y0 = (ty - n) / 2;
             y1 = y0 + n;
         }
-        for (int by = y0; by < y1; ++by)
-            for (int bx = 0; bx < tx; ++bx) out.push_back(make_int4(j, bx, by, 0));
+        // the one-search kernel's tile order: super-columns of a.swz tiles (0: rows), row by
+        // row within each, so the CTAs working at one time cover a compact block
+        const int sw = a.swz > 0 && a.swz < tx ? a.swz : tx;
+        for (int s0 = 0; s0 < tx; s0 += sw)
+            for (int by = y0; by < y1; ++by)
+                for (int bx = s0; bx < std::min(tx, s0 + sw); ++bx) out.push_back(make_int4(j, bx, by, 0));
     }
 }
 
