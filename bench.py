@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--topk", type=int, default=0, help="results per pixel (0 = the workload's k)")
     ap.add_argument("--carveout", type=int, default=-1, help="search shared-memory carveout percent (-1 = auto)")
     ap.add_argument("--swizzle", type=int, default=-1, help="search tile order: super-columns of N tiles (-1 = auto)")
+    ap.add_argument("--vorder", type=int, default=-1,
+                    help="velocity order: 0 latest (dy, dx), 1 Hilbert, 2 the caller's (-1 = auto)")
     ap.add_argument("--workload", default="decam", choices=["decam", "batch", "serve"],
                     help="decam: the 12x4096^2 stack; batch: 64 uneven 2048x4096 stacks in one batched launch; "
                          "serve: a Poisson stream of search jobs through the serving loop")
@@ -138,6 +140,7 @@ def workload_config(args, st, world):
                                   "17x17 rotated elliptical Gaussian, major FWHM 3.5-4.5 px, axis ratio "
                                   "0.6-0.9 (not separable)"), "storage": args.storage,
             "rescore_fp64": bool(args.rescore), "search_variant": args.variant, "carveout": args.carveout, "swizzle": args.swizzle,
+            "velocity_order": args.vorder,
             "evals_per_step": int(N * H * W * st.vx.size),
             "l2": "inputs larger than L2 (%.2f GB of psi/phi planes)" % (N * H * W * 8 / 1e9),
             "parallelism": "replicas%d" % world}
@@ -307,6 +310,7 @@ def run_ours(args):
     ctx.set_search_variant(args.variant)
     ctx.set_search_carveout(args.carveout)
     ctx.set_search_swizzle(args.swizzle)
+    ctx.set_search_order(args.vorder)
     stack = kb.Stack(ctx, N, H, W, args.storage)
     job = kb.Job(ctx, H, W, N, V, k, flags)
     sci_h = torch.from_numpy(st.sci).pin_memory()

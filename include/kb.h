@@ -136,6 +136,14 @@ int kb_set_search_waves(kb_ctx *ctx, int waves);
  * against 117.4 ms row by row.  Results do not depend on it. */
 int kb_set_search_swizzle(kb_ctx *ctx, int cols);
 
+/* Tuning knob: the order in which every CTA of the search walks the velocities.
+ * 0: by the trajectory offset at the latest epoch, dy then dx; 1: along a
+ * Hilbert curve over those offsets (velocities walked close together are close
+ * in both axes); 2: the caller's order; -1: automatic (0).  On the
+ * 12 x 4096^2 stack: 97.7, 102.5 and 98.7 ms.  Ties in nu are broken by the
+ * caller's velocity index, so results do not depend on it. */
+int kb_set_search_order(kb_ctx *ctx, int order);
+
 /* Measurement helper (no counterpart in the paper): the L2-to-SM bandwidth, in
  * GB/s, of the search's own access form -- warp-contiguous 8-byte loads of
  * 256-byte spans at scattered offsets of an L2-resident 64 MB buffer, from every

@@ -272,6 +272,13 @@ int kb_set_search_waves(kb_ctx *ctx, int waves) {
     return KB_OK;
 }
 
+int kb_set_search_order(kb_ctx *ctx, int order) {
+    if (!ctx) return KB_EINVAL;
+    if (order < -1 || order > 2) return fail(ctx, KB_EINVAL, "order %d not in -1..2", order);
+    ctx->search_order = order;
+    return KB_OK;
+}
+
 int kb_set_search_swizzle(kb_ctx *ctx, int cols) {
     if (!ctx) return KB_EINVAL;
     if (cols < -1 || cols > 65535) return fail(ctx, KB_EINVAL, "swizzle %d not in -1..65535", cols);
@@ -660,6 +667,28 @@ static cudaError_t readback_status(kb_job *job, cudaStream_t st) {
     return e;
 }
 
+// Distance along a Hilbert curve filling the 2^16 x 2^16 grid: at each level
+// from the coarsest, the quadrant's index in the curve's visiting order, then the
+// coordinates turned into the quadrant's own frame.
+uint64_t hilbert_index(uint32_t x, uint32_t y) {
+    const uint32_t n = 1u << 16;
+    uint64_t d = 0;
+    for (uint32_t s = n >> 1; s > 0; s >>= 1) {
+        const uint32_t rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+        d += (uint64_t)s * s * ((3u * rx) ^ ry);
+        if (ry == 0) {   // rotate the quadrant
+            if (rx == 1) {
+                x = s - 1 - (x & (s - 1));
+                y = s - 1 - (y & (s - 1));
+            }
+            std::swap(x, y);
+        }
+        x &= s - 1;
+        y &= s - 1;
+    }
+    return d;
+}
+
 // Validation, fixed-point offset table, processing order and upload of one
 // search's tables (stream-ordered), and the kernels' argument blocks.  Shared by
 // kb_search and kb_batch_create.
@@ -708,12 +737,32 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
     // every epoch's plane that a band reads are used by a contiguous run of
     // velocities, so the live set of all epochs stays in L2 instead of each
     // velocity re-fetching its rows from HBM.
+    // Other orders (kb_set_search_order): along a Hilbert curve over the latest
+    // offsets, so that velocities processed close together are close in both axes,
+    // or the caller's order.
     {
         const int2 *last = h_offs + (N - 1);
-        std::stable_sort(h_vorder, h_vorder + V, [&](int a, int b) {
-            int2 oa = last[(size_t)a * N], ob = last[(size_t)b * N];
-            return oa.y < ob.y || (oa.y == ob.y && oa.x < ob.x);
-        });
+        const int order = ctx->search_order < 0 ? 0 : ctx->search_order;
+        if (order == 0) {
+            std::stable_sort(h_vorder, h_vorder + V, [&](int a, int b) {
+                int2 oa = last[(size_t)a * N], ob = last[(size_t)b * N];
+                return oa.y < ob.y || (oa.y == ob.y && oa.x < ob.x);
+            });
+        } else if (order == 1) {
+            int mnx = INT_MAX, mny = INT_MAX;
+            for (int v = 0; v < V; ++v) {
+                mnx = std::min(mnx, last[(size_t)v * N].x);
+                mny = std::min(mny, last[(size_t)v * N].y);
+            }
+            std::vector<uint64_t> key(V);
+            for (int v = 0; v < V; ++v) {
+                const int2 o = last[(size_t)v * N];
+                const uint32_t x = (uint32_t)std::min<int64_t>((int64_t)o.x - mnx, 65535);
+                const uint32_t y = (uint32_t)std::min<int64_t>((int64_t)o.y - mny, 65535);
+                key[v] = hilbert_index(x, y);
+            }
+            std::stable_sort(h_vorder, h_vorder + V, [&](int a, int b) { return key[a] < key[b]; });
+        }
     }
     for (int j = 0; j < N; ++j) h_epoch[j] = pl.epoch_of[j];
     // producer table of the pipelined kernel: (dx, dy) as int16 pairs for the

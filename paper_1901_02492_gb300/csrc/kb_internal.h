@@ -63,6 +63,7 @@ struct kb_ctx {
     size_t smem_optin = 0;
     int search_variant = 0;   // 0 = automatic
     int search_carveout = -1; // -1 = automatic
+    int search_order = -1;    // velocity processing order: 0 by latest (dy, dx), 1 Hilbert, 2 the caller's
     int search_swizzle = -1;  // register-gather search: tile order in super-columns of this many tiles (0: rows)
     int search_waves = -1;    // register-gather search launched in bands of this many resident waves (0 and -1: one launch)
     std::string err;

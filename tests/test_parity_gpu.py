@@ -345,3 +345,18 @@ def test_tile_order_swizzle_equals_row_order(kb, ctx, cols):
     finally:
         ctx.set_search_swizzle(-1)
     assert got.tobytes() == ref.tobytes()
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_velocity_order_changes_no_result(kb, ctx, order):
+    """kb_set_search_order: the Hilbert and the caller's velocity orders give the records of the
+    default order byte for byte (ties in nu resolved by the caller's velocity index)."""
+    st = synth.small_stack(79, 5, 60, 200, K=5, n_angles=9, n_speeds=7, s_lo=2.0, s_hi=40.0, k=8, n_sources=3,
+                           flux=30.0)
+    ref = gpu_search(kb, ctx, st)
+    ctx.set_search_order(order)
+    try:
+        got = gpu_search(kb, ctx, st)
+    finally:
+        ctx.set_search_order(-1)
+    assert got.tobytes() == ref.tobytes()
