@@ -90,11 +90,13 @@ def test_record_layouts_match_binding(tmp_path, lib, struct, dtype):
     assert vals[1:] == [dt.fields[f][1] for f in dt.names]
 
 
-def test_moment_cuts_layout_matches_binding(tmp_path, lib):
-    names = [f[0] for f in lib.MomentCuts._fields_]
-    vals = _c_layout(tmp_path, "kb_moment_cuts", names)
-    assert vals[0] == ctypes.sizeof(lib.MomentCuts)
-    assert vals[1:] == [getattr(lib.MomentCuts, f).offset for f in names]
+@pytest.mark.parametrize("struct,cls", [("kb_moment_cuts", "MomentCuts"), ("kb_cluster_params", "ClusterParams")])
+def test_parameter_struct_layouts_match_binding(tmp_path, lib, struct, cls):
+    c = getattr(lib, cls)
+    names = [f[0] for f in c._fields_]
+    vals = _c_layout(tmp_path, struct, names)
+    assert vals[0] == ctypes.sizeof(c)
+    assert vals[1:] == [getattr(c, f).offset for f in names]
 
 
 def test_offsets_bit_exact_against_oracle(lib):
