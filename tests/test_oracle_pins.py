@@ -753,3 +753,22 @@ def test_cluster_permutation_relabels_consistently():
         m = {}
         for u, w in zip(a, b):
             assert m.setdefault(u, w) == w
+
+
+def test_elongated_psfs_are_normalised_and_not_separable():
+    """The bench's non-separable PSFs: unit sum, the Gaussian's major-axis width kept, and a
+    second singular value far above rounding (so the single-pass path is exercised)."""
+    import synth
+    base = np.stack([synth.gaussian_psf(17, s) for s in (1.5, 1.7, 1.9)])
+    el = synth.elongate_psfs(base, seed=3)
+    for e in range(3):
+        p = el[e].astype(np.float64)
+        assert abs(p.sum() - 1.0) < 1e-6
+        sv = np.linalg.svd(p, compute_uv=False)
+        assert sv[1] / sv[0] > 1e-4
+        # the largest second moment along any axis is the base width (sampled, truncated at 8 px)
+        d = np.arange(-8, 9, dtype=np.float64)
+        yy, xx = np.meshgrid(d, d, indexing="ij")
+        cov = np.array([[np.sum(p * xx * xx), np.sum(p * xx * yy)], [np.sum(p * xx * yy), np.sum(p * yy * yy)]])
+        sig = math.sqrt(float(np.sum(base[e].astype(np.float64).sum(axis=0) * d ** 2)))
+        assert np.linalg.eigvalsh(cov).max() == pytest.approx(sig ** 2, rel=2e-3)
