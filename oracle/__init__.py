@@ -69,6 +69,9 @@ def _load():
             lib.kbo_stamp.argtypes = [P, P, i32, i32, i32, P, P, i32, i32, i32, i32, P]
             lib.kbo_moments.argtypes = [P, i32, P, P, P, P, P, P]
             lib.kbo_cluster.argtypes = [P, P, P, P, P, P, ctypes.c_long, f64, f64, f64, i32, P, P, P]
+            lib.kbo_snr2_span_max.argtypes = [P, P, i32, i32, i32, i32, P]
+            lib.kbo_span_bound.argtypes = [P, i32, i32, i32, i32, P, P, i32, i32]
+            lib.kbo_span_bound.restype = f64
             lib.kbo_search_pixels.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64, P, P, i64, P]
             lib.kbo_search_region.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64,
                                               i32, i32, i32, i32, P]
@@ -239,6 +242,28 @@ def cluster(x0, y0, vx, vy, nu, vidx, w_pos, w_vel, eps, min_samples):
     lib.kbo_cluster(_ptr(x0), _ptr(y0), _ptr(vx), _ptr(vy), _ptr(nu), _ptr(vidx), n, float(w_pos), float(w_vel),
                     float(eps), int(min_samples), _ptr(label), _ptr(keep), _ptr(core))
     return label, keep.astype(bool), core.astype(bool)
+
+
+def snr2_span_max(psi, phi, span):
+    """Sec. 5.3 bound planes (reading in kb_oracle.c): [N][H][W + span - 1], entry x + span - 1
+    holding the largest max(psi, 0)^2 / phi over the columns [x, x + span) in the image."""
+    lib = _load()
+    psi = _c(psi, np.float64)
+    phi = _c(phi, np.float64)
+    N, H, W = psi.shape
+    r = np.empty((N, H, W + span - 1), np.float64)
+    lib.kbo_snr2_span_max(_ptr(psi), _ptr(phi), N, H, W, int(span), _ptr(r))
+    return r
+
+
+def span_bound(r, W, span, dx_v, dy_v, x0, y0):
+    """Upper bound on nu^2 of the trajectories starting in [x0, x0 + span) of row y0 (Psi > 0)."""
+    lib = _load()
+    r = _c(r, np.float64)
+    N, H = r.shape[0], r.shape[1]
+    dx_v = _c(dx_v, np.int32)
+    dy_v = _c(dy_v, np.int32)
+    return lib.kbo_span_bound(_ptr(r), N, H, int(W), int(span), _ptr(dx_v), _ptr(dy_v), int(x0), int(y0))
 
 
 def search_region(psi, phi, times, dx, dy, k, nu_min=-np.inf, region=None):

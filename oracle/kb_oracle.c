@@ -22,6 +22,8 @@
  *                      a trajectory, and the stamp's central moments
  *   de-duplication     Sec. 3.3: DBSCAN over (x0, y0, vx, vy), the highest-likelihood
  *                      trajectory of each group kept (reading below)
+ *   likelihood bound   Sec. 5.3 (searching low-likelihood trajectories less): an upper
+ *                      bound on nu over a span of start pixels (derivation below)
  *
  * Readings of points the paper leaves open:
  *   - a pixel is masked when its mask byte is non-zero, when n or sigma^2 is not
@@ -620,4 +622,52 @@ void kbo_cluster(const int32_t *x0, const int32_t *y0, const float *vx, const fl
             if (j != i && label[j] == label[i] && (nu[j] > nu[i] || (nu[j] == nu[i] && j < i))) best = 0;
         keep[i] = (uint8_t)best;
     }
+}
+
+/* ---- Sec. 5.3: an upper bound on nu over a span of start pixels ------------
+ *
+ * For one trajectory, over the epochs whose pixel is in the image, the
+ * Cauchy-Schwarz inequality gives
+ *     Psi^2 = (sum_t psi_t)^2 <= (sum_t psi_t^2 / phi_t) (sum_t phi_t)
+ * (an epoch with phi_t = 0 has psi_t = 0: every weight of its PSF window is 0).
+ * With Psi > 0 only the positive psi_t can raise it, so
+ *     nu^2 = Psi^2 / Phi <= sum_t max(psi_t, 0)^2 / phi_t,
+ * a sum of single-epoch SNRs squared, with equality when psi_t / phi_t is the
+ * same for every epoch (a noiseless source).  kbo_snr2_span_max stores, per
+ * epoch and row, the largest such term over the columns [x, x + span) that lie
+ * in the image (0 if none), for x = -(span - 1) .. W - 1 at index
+ * x + span - 1: r is [N][H][W + span - 1].  kbo_span_bound adds one r value
+ * per epoch at the span's position shifted by the trajectory's offsets (epochs
+ * whose row is outside add 0); it bounds nu^2 of every trajectory that starts
+ * in the span [x0, x0 + span) of row y0 with those offsets and has Psi > 0.
+ */
+void kbo_snr2_span_max(const double *psi, const double *phi, int N, int H, int W, int span, double *r) {
+    const int RW = W + span - 1;
+    for (int t = 0; t < N; ++t)
+        for (int y = 0; y < H; ++y)
+            for (int xi = 0; xi < RW; ++xi) {
+                const int x = xi - (span - 1);
+                const int lo = x < 0 ? 0 : x, hi = x + span < W ? x + span : W;
+                double m = 0.0;
+                for (int xx = lo; xx < hi; ++xx) {
+                    const size_t i = ((size_t)t * H + y) * W + xx;
+                    if (phi[i] > 0.0 && psi[i] > 0.0) {
+                        const double q = psi[i] * psi[i] / phi[i];
+                        if (q > m) m = q;
+                    }
+                }
+                r[((size_t)t * H + y) * RW + xi] = m;
+            }
+}
+
+double kbo_span_bound(const double *r, int N, int H, int W, int span, const int32_t *dx, const int32_t *dy, int x0,
+                      int y0) {
+    const int RW = W + span - 1;
+    double s = 0.0;
+    for (int t = 0; t < N; ++t) {
+        const int x = x0 + dx[t], y = y0 + dy[t];
+        if (y < 0 || y >= H || x <= -span || x >= W) continue;
+        s += r[((size_t)t * H + y) * RW + (x + span - 1)];
+    }
+    return s;
 }

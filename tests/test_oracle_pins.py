@@ -772,3 +772,81 @@ def test_elongated_psfs_are_normalised_and_not_separable():
         cov = np.array([[np.sum(p * xx * xx), np.sum(p * xx * yy)], [np.sum(p * xx * yy), np.sum(p * yy * yy)]])
         sig = math.sqrt(float(np.sum(base[e].astype(np.float64).sum(axis=0) * d ** 2)))
         assert np.linalg.eigvalsh(cov).max() == pytest.approx(sig ** 2, rel=2e-3)
+
+
+# ------------------------------------------------------------ Sec. 5.3 likelihood bound over a span
+
+def _traj_sums(psi, phi, dxv, dyv, x, y):
+    N, H, W = psi.shape
+    P = F = 0.0
+    for t in range(N):
+        xx, yy = x + dxv[t], y + dyv[t]
+        if 0 <= xx < W and 0 <= yy < H:
+            P += psi[t, yy, xx]
+            F += phi[t, yy, xx]
+    return P, F
+
+
+@pytest.mark.parametrize("span", [1, 7, 64])
+def test_span_bound_exceeds_every_nu_in_the_span(span):
+    """Brute force on a masked noise stack with a source: for random rows, span starts (also
+    partly off the image) and velocities, the bound is at least nu^2 of every trajectory of the
+    span with Psi > 0."""
+    st = synth.small_stack(71, 6, 40, 90, K=5, var_lo=1.0, var_hi=3.0, nan_frac=0.02, mask_frac=0.02,
+                           n_angles=6, n_speeds=5, s_lo=2.0, s_hi=15.0, n_sources=2, flux=30.0)
+    psi, phi = oracle.psi_phi(st.sci, st.var, st.mask, st.psf)
+    dx, dy = oracle.offsets(st.times, st.vx, st.vy)
+    N, H, W = psi.shape
+    r = oracle.snr2_span_max(psi, phi, span)
+    rng = np.random.default_rng(span)
+    checked = 0
+    for _ in range(150):
+        v = int(rng.integers(0, dx.shape[0]))
+        y0 = int(rng.integers(0, H))
+        x0 = int(rng.integers(-span + 1, W))
+        b = oracle.span_bound(r, W, span, dx[v], dy[v], x0, y0)
+        for x in range(max(x0, 0), min(x0 + span, W)):
+            P, F = _traj_sums(psi, phi, dx[v], dy[v], x, y0)
+            if P > 0 and F > 0:
+                assert P * P / F <= b * (1 + 1e-12), (v, x, y0, P * P / F, b)
+                checked += 1
+    assert checked > 40
+
+
+def test_span_bound_is_tight_for_a_noiseless_source():
+    """Equality in Cauchy-Schwarz: psi_t / phi_t the same for every epoch (a noiseless source on
+    its own trajectory, unit variance, one PSF) gives bound = nu^2 with a one-pixel span."""
+    N, H, W = 5, 40, 60
+    times = np.array([0.0, 0.5, 1.0, 1.5, 2.0])
+    vx, vy = np.array([6.0]), np.array([-4.0])
+    dx, dy = oracle.offsets(times, vx, vy)
+    psf = np.stack([synth.gaussian_psf(5, 1.0)] * N)
+    sci = np.zeros((N, H, W), np.float32)
+    for t in range(N):
+        sci[t, 25 + dy[0, t], 12 + dx[0, t]] = 16.0          # a delta at the trajectory pixel
+    var = np.ones((N, H, W), np.float32)
+    psi, phi = oracle.psi_phi(sci, var, None, psf)
+    r = oracle.snr2_span_max(psi, phi, 1)
+    P, F = _traj_sums(psi, phi, dx[0], dy[0], 12, 25)
+    assert oracle.span_bound(r, W, 1, dx[0], dy[0], 12, 25) == pytest.approx(P * P / F, rel=1e-12)
+    # a single epoch and a one-pixel span: the bound is that pixel's psi^2 / phi
+    r1 = oracle.snr2_span_max(psi[:1], phi[:1], 1)
+    assert oracle.span_bound(r1, W, 1, dx[0, :1], dy[0, :1], 12, 25) == pytest.approx(
+        psi[0, 25, 12] ** 2 / phi[0, 25, 12], rel=1e-15)
+
+
+def test_span_bound_of_pure_noise_prunes_at_ten_sigma():
+    """Unit-variance noise, no source: every 64-pixel span's bound stays below 10^2 (the single-
+    epoch SNRs are N(0, 1), so each epoch's span maximum is a few units)."""
+    rng = np.random.default_rng(72)
+    N, H, W = 12, 24, 256
+    sci = rng.standard_normal((N, H, W)).astype(np.float32)
+    var = np.ones((N, H, W), np.float32)
+    psf = np.stack([synth.gaussian_psf(7, 1.3)] * N)
+    psi, phi = oracle.psi_phi(sci, var, None, psf)
+    r = oracle.snr2_span_max(psi, phi, 64)
+    times = np.linspace(0.0, 2.0, N)
+    dx, dy = oracle.offsets(times, np.array([20.0, -35.0]), np.array([3.0, 8.0]))
+    worst = max(oracle.span_bound(r, W, 64, dx[v], dy[v], x0, y0)
+                for v in range(2) for y0 in range(H) for x0 in range(-63, W, 32))
+    assert worst < 100.0
