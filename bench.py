@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--rescore", action="store_true")
     ap.add_argument("--size", type=int, default=4096, help="image side (4096 = the DECam workload)")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-records", default="compact", choices=["compact", "full"],
+                    help="records read back every end-to-end step: 16-byte kb_result_compact or 48-byte kb_result")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--variant", type=int, default=0, help="search kernel shape (0 = automatic)")
@@ -212,6 +214,34 @@ def measured_peaks():
         return {}
 
 
+def search_span(storage, variant):
+    """Pixels per warp span of the register-gather search shape (the library's search_span)."""
+    p32, p16 = [2, 4, 2, 4, 2], [1, 2, 1, 2, 1]
+    v = variant if 1 <= variant <= 4 else 0
+    return 32 * p32[v] if storage == "f32" else 64 * p16[v]
+
+
+def recorded_levels(kernel_tag):
+    """Per-level bytes of one search launch (L2 -> L1, DRAM) from the ncu summary in
+    profiles/, scaled from the captured case to this workload by the gathered
+    evaluations, when the kernel source is unchanged since (matching sha256 prefix)."""
+    src = os.path.join(ROOT, "paper_1901_02492_gb300", "csrc", "kb_search.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    pdir = os.path.join(ROOT, "profiles")
+    for fn in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        if not fn.endswith(".md"):
+            continue
+        for line in open(os.path.join(pdir, fn)):
+            m = re.match(r"levels\s+%s\s+(.*)\s+source_sha=([0-9a-f]+)$" % re.escape(kernel_tag), line.strip())
+            if m and m.group(2) == sha:
+                out = {"source": fn}
+                for kv in m.group(1).split():
+                    key, val = kv.split("=")
+                    out[key] = float(val)
+                return out
+    return None
+
+
 def recorded_traffic(kernel_tag):
     """DRAM bytes per launch recorded by an ncu capture in profiles/, if the kernel
     source has not changed since (matching sha256 prefix)."""
@@ -226,6 +256,49 @@ def recorded_traffic(kernel_tag):
             if m and m.group(2) == sha:
                 return int(m.group(1))
     return None
+
+
+def search_byte_classes(binding, times, vx, vy, H, W, bytes_per_eval, span):
+    """The search's trajectory-epoch evaluations split by where their (psi, phi) pair
+    comes from, counted on the host from the library's own offset table:
+      ref      epochs at the reference time (offset 0 for every velocity): loaded once
+               per start pixel, then reused for every velocity;
+      off      trajectory pixel outside the image: nothing to gather (the kernel reads
+               a zero block that stays in L1);
+      gathered trajectory pixel inside the image: one pair gathered per evaluation.
+    Algorithmic bytes per launch = gathered evaluations + one load per pixel and
+    reference epoch, times the pair size.  `issued` counts what the kernel loads: whole
+    warp spans of `span` pixels whose row is inside the image and whose columns overlap
+    it (their off-image pixels read the zero columns beside every row)."""
+    dx, dy = binding.offsets(times, vx, vy)              # [V][N], the caller's epoch order
+    times = np.asarray(times, np.float64)
+    V, N = dx.shape
+    ref = (times == times.min()) & np.all(dx == 0, axis=0) & np.all(dy == 0, axis=0)
+    nref = int(ref.sum())
+    inx = np.maximum(0, W - np.abs(dx[:, ~ref])).astype(np.int64)
+    iny = np.maximum(0, H - np.abs(dy[:, ~ref])).astype(np.int64)
+    gathered = int((inx * iny).sum())
+    total = H * W * V * N
+    evals_ref = H * W * V * nref
+    off = total - evals_ref - gathered
+    # spans: tiles of `span` columns starting at multiples of span; overlap after the shift
+    ntile = (W + span - 1) // span
+    xs = np.arange(ntile, dtype=np.int64) * span
+    issued = 0
+    for v in range(V):
+        for j in np.nonzero(~ref)[0]:
+            ox, oy = int(dx[v, j]), int(dy[v, j])
+            rows = max(0, H - abs(oy))
+            if rows == 0:
+                continue
+            tiles = int(np.count_nonzero((xs + ox + span > 0) & (xs + ox < W)))
+            issued += rows * tiles * span
+    alg = (gathered + H * W * nref) * bytes_per_eval
+    return {"evals_total": int(total), "evals_ref_epoch": int(evals_ref), "evals_off_image": int(off),
+            "evals_gathered": gathered, "ref_epochs": nref,
+            "alg_bytes_per_launch": int(alg),
+            "issued_bytes_per_launch": int((issued + H * W * nref) * bytes_per_eval),
+            "delivered_bytes_per_launch": int(total * bytes_per_eval)}
 
 
 # ----------------------------------------------------------------------------- reference arm (oracle)
@@ -318,7 +391,12 @@ def run_ours(args):
     sci = sci_h.to(dev)
     var = var_h.to(dev)
     stream = torch.cuda.current_stream(dev)
-    gather_peak = ctx.measure_gather_peak()   # GB/s, before the timed region
+    # roofline denominators, before the timed region: the L2-to-SM rate of the search's own
+    # access form (warp spans of 512 B in FP32, 256 B in 16-bit storage, at any 8-byte offset),
+    # and of line-aligned spans for reference
+    span_bytes = 512 if args.storage == "f32" else 256
+    gather_peak = ctx.measure_gather_peak(span_bytes, 8)
+    gather_peak_aligned = ctx.measure_gather_peak(span_bytes, 256)
     launches_per_step = 2 + (1 if args.storage != "f32" else 0) + (2 if args.rescore else 0)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -358,7 +436,8 @@ def run_ours(args):
     # search -> all H*W*k records to pinned host memory.  Steps are pipelined over three
     # streams: step i+1's inputs go up (s_in) and step i's records come back (s_out, with
     # kb_results_async) while the GPU computes; inputs and jobs are double-buffered.
-    nrec_bytes = H * W * k * kb.RESULT_DTYPE.itemsize
+    rec_dtype = kb.COMPACT_DTYPE if args.e2e_records == "compact" else kb.RESULT_DTYPE
+    nrec_bytes = H * W * k * rec_dtype.itemsize
     res_h = [torch.empty(nrec_bytes, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
     jobs = [job, kb.Job(ctx, H, W, N, V, k, flags)]
     sci_d, var_d = [sci, torch.empty_like(sci)], [var, torch.empty_like(var)]
@@ -385,7 +464,10 @@ def run_ours(args):
         jobs[b].search(stack, st.times, st.vx, st.vy, k, -math.inf, flags, stream=stream)
         if timed:
             comp_ev[-1][1].record(stream)
-        jobs[b].results_async(res_h[b], stream=s_out)
+        if args.e2e_records == "compact":
+            jobs[b].results_compact_async(res_h[b], stream=s_out)
+        else:
+            jobs[b].results_async(res_h[b], stream=s_out)
 
     n_e2e = max(args.e2e_steps, 2)
     for i in range(2):
@@ -400,7 +482,10 @@ def run_ours(args):
     e2e_comp_ms = float(np.mean([t0.elapsed_time(t1) for t0, t1 in comp_ev]))
     for j in jobs:
         j.wait()
-    res_np = res_h[(1 + n_e2e) % 2].numpy().view(kb.RESULT_DTYPE)   # the last step's records
+    if args.e2e_records == "compact" and (args.stamps > 0 or args.cluster > 0):
+        res_np = job.results()      # full records of the last search, for the post-search legs
+    elif args.e2e_records != "compact":
+        res_np = res_h[(1 + n_e2e) % 2].numpy().view(kb.RESULT_DTYPE)   # the last step's records
 
     # the slowest rank's times (replicas: every rank searched its own copy of the stack)
     ms, e2e_ms = replicas.max_over_ranks([ms, e2e_ms], device=dev)
@@ -412,9 +497,13 @@ def run_ours(args):
     # gathers are served by L2 (L1 catches the early epochs' reuse, HBM sees little:
     # the planes stay L2-resident), so the denominator is the L2-to-SM bandwidth of
     # exactly this access form, measured on this device by the library.
-    alg_bytes = evals * BYTES_PER_EVAL[args.storage]
+    span = search_span(args.storage, args.variant)
+    classes = search_byte_classes(kb, st.times, st.vx, st.vy, H, W, BYTES_PER_EVAL[args.storage], span)
+    alg_bytes = classes["alg_bytes_per_launch"]
     achieved = alg_bytes / (ms_search * 1e-3) / 1e9
+    delivered = classes["delivered_bytes_per_launch"] / (ms_search * 1e-3) / 1e9
     traffic = recorded_traffic("search_%s" % args.storage)
+    levels = recorded_levels("search_%s" % args.storage)
     hbm = peaks.get("hbm_gbs", 6800.0)
     psiphi_bytes = N * H * W * (8 + 8 + (4 + 8 if args.storage != "f32" else 0))
     cfg = workload_config(args, st, world)
@@ -425,17 +514,30 @@ def run_ours(args):
             "dtype": args.storage, "data": "synthetic", "config": cfg,
             "roofline": {"bound": "l2", "kernel": "search_kernel", "achieved": achieved, "peak": gather_peak,
                          "unit": "GB/s", "frac": achieved / gather_peak, "traffic": traffic,
-                         "peak_source": "measured in this run by kb_measure_gather_peak: L2-resident 256-byte "
-                                        "warp-span loads (the search's access form), no HBM or L1 term",
-                         "ms_per_launch": ms_search, "alg_bytes_per_launch": alg_bytes},
+                         "peak_source": "measured in this run by kb_measure_gather_peak(%d, 8): L2-resident "
+                                        "%d-byte warp spans at any 8-byte offset (the search's access form), "
+                                        "not cached in L1" % (span_bytes, span_bytes),
+                         "ms_per_launch": ms_search, "alg_bytes_per_launch": alg_bytes,
+                         "alg_bytes_note": "gathered (in-image, non-reference-epoch) evaluations + one load per "
+                                           "pixel and reference epoch, x %d B" % BYTES_PER_EVAL[args.storage],
+                         "byte_classes": classes,
+                         "frac_issued": classes["issued_bytes_per_launch"] / (ms_search * 1e-3) / 1e9 / gather_peak,
+                         "frac_delivered": delivered / gather_peak,
+                         "frac_delivered_note": "every trajectory-epoch evaluation counted as a gather (the "
+                                                "figure an evals/s rate implies)",
+                         "peak_aligned_spans": gather_peak_aligned,
+                         "levels": levels},
             "roofline_psi_phi": roofline_psi_phi(args, st, ms_psiphi, psiphi_bytes, hbm, clocks),
             "clocks": clocks,
             "e2e": {"value": world * evals / (e2e_ms * 1e-3), "unit": "evals/s",
                     "h2d_bytes_per_step": int(sci_h.numel() * 4 + var_h.numel() * 4),
-                    "d2h_bytes_per_step": int(H * W * k * kb.RESULT_DTYPE.itemsize), "ms_per_step": e2e_ms,
+                    "d2h_bytes_per_step": int(nrec_bytes), "ms_per_step": e2e_ms,
                     "steps": n_e2e, "compute_ms_per_step": e2e_comp_ms,
+                    "records": "%s (%d B each, all H*W*k every step)" % (args.e2e_records, rec_dtype.itemsize),
                     "pipeline": "host clock over %d steps; inputs and jobs double-buffered, uploads, "
-                                               "compute and kb_results_async reads on three streams" % n_e2e},
+                                "compute and %s reads on three streams"
+                                % (n_e2e, "kb_results_compact_async" if args.e2e_records == "compact"
+                                   else "kb_results_async")},
             "gpu_launches": launches_per_step * args.steps}
     if args.filter:
         # the Sec. 3.3 outlier filter of every kept trajectory (two FP64 passes over its epochs)
@@ -568,7 +670,7 @@ def run_batch(args):
     batch = kb.Batch(ctx, searches, autotune=True)
     t_tune = time.perf_counter() - t_tune
     groups = batch.groups()
-    gather_peak = ctx.measure_gather_peak()
+    gather_peak = ctx.measure_gather_peak(512 if args.storage == "f32" else 256, 8)
     for _ in range(args.warmup):
         batch.run(stream)
     torch.cuda.synchronize(dev)
@@ -613,7 +715,8 @@ def run_batch(args):
             "single_search_loop": {"value": world * evals / (ms_loop * 1e-3), "unit": "evals/s", "ms": ms_loop},
             "roofline": {"bound": "l2", "kernel": "search_batch_kernel", "achieved": achieved, "peak": gather_peak,
                          "unit": "GB/s", "frac": achieved / gather_peak, "traffic": None,
-                         "peak_source": "measured in this run by kb_measure_gather_peak"},
+                         "peak_source": "measured in this run by kb_measure_gather_peak (the search's span form)",
+                         "frac_note": "every trajectory-epoch evaluation counted as a gather (delivered)"},
             "clocks": clk.summary(), "e2e": None,
             "e2e_note": "inputs of the 64 stacks are drawn on the device; the end-to-end number is on the "
                         "single-stack line",

@@ -145,11 +145,14 @@ int kb_set_search_swizzle(kb_ctx *ctx, int cols);
 int kb_set_search_order(kb_ctx *ctx, int order);
 
 /* Measurement helper (no counterpart in the paper): the L2-to-SM bandwidth, in
- * GB/s, of the search's own access form -- warp-contiguous 8-byte loads of
- * 256-byte spans at scattered offsets of an L2-resident 64 MB buffer, from every
- * SM, not cached in L1.  It is the denominator of the search's roofline.  Takes
- * about 100 ms; allocates and frees 64 MB on the context's device. */
-int kb_measure_gather_peak(kb_ctx *ctx, double *gb_per_s);
+ * GB/s, of the search's own access form -- each warp reads warp_bytes (256, 512
+ * or 1024) contiguous bytes as lane-contiguous 8-byte loads, starting at a
+ * scattered multiple of align_bytes (a power of two >= 8; 8 is the search's
+ * form, whose shifted spans start at any pixel) of an L2-resident 64 MB buffer,
+ * from every SM, not cached in L1.  It is the denominator of the search's
+ * roofline.  Takes about 100 ms; allocates and frees 64 MB on the context's
+ * device.  KB_EINVAL for other sizes. */
+int kb_measure_gather_peak(kb_ctx *ctx, int warp_bytes, int align_bytes, double *gb_per_s);
 
 /* ---- stage (a): likelihood images --------------------------------------- */
 
@@ -196,12 +199,17 @@ int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8
  * device and in stream order.  The per-epoch PSF taps it needs are kept in a
  * static device array of 256 KB (65536 floats) that every GPU loading the
  * library holds until exit: separable PSFs need N * 4K floats, other PSFs
- * N * 2K^2 floats, and a call that needs more returns KB_EINVAL.  The first
- * call on a device looks up the array's device address (set-up, once per
- * device); make that call before any stream capture.  All calls share the
- * array, so calls that overlap on the GPU (e.g. on different streams) race and
- * must be ordered by the caller.  Returns KB_OK, KB_EINVAL (bad sizes or
- * pointers, or too many taps) or KB_ECUDA. */
+ * N * 2K^2 floats, and a call that needs more returns KB_EINVAL.  Every call
+ * looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing).  The taps are staged through
+ * one host buffer that every call rewrites, so a call on a stream that is being
+ * captured into a CUDA graph is refused with KB_EINVAL before any other work: a
+ * captured copy would read the buffer at replay, after other calls changed it.
+ * All calls share the array, so calls that overlap on the GPU (e.g. on
+ * different streams) race and must be ordered by the caller.  The library
+ * cannot check the sizes of the caller's buffers: sci, var (and mask) must hold
+ * N*H*W elements and out 2*N*H*W floats.  Returns KB_OK, KB_EINVAL (bad sizes
+ * or pointers, too many taps, or a capturing stream) or KB_ECUDA. */
 int kb_make_psi_phi_static(const float *sci, const float *var, const uint8_t *mask, const float *psf, int N, int H,
                            int W, int K, float bright_max, float *out, void *stream);
 
@@ -283,6 +291,32 @@ int kb_results(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, 
  * of one job can be copied out while another job searches.  The search's
  * device status is read with kb_job_wait. */
 int kb_results_async(kb_job *job, kb_result *out, size_t capacity, size_t *n_written, void *stream);
+
+/* One kept trajectory in 16 bytes, as written by kb_results_compact_async: the
+ * fields of kb_result that cannot be derived from the record's position
+ * ([H][W][topk], row-major start pixels, best first) and the caller's velocity
+ * grid.  Little-endian layout; static_assert-checked against the search's own
+ * device record. */
+typedef struct kb_result_compact {
+    float psi, phi;   /* coadded Psi and Phi (Sec. 2.1.5); FP64 values rounded to FP32 after rescoring */
+    float nu;         /* Psi / sqrt(Phi) as ranked (rounded to FP32 after rescoring); -inf when empty */
+    uint16_t vidx;    /* index into the caller's velocity arrays; 0xFFFF = empty slot */
+    uint8_t nobs;     /* epochs whose trajectory pixel lies inside the image */
+    uint8_t reserved; /* 0 */
+} kb_result_compact;
+
+/* kb_results_async with compact records (not a step of the paper: a transfer
+ * format).  Writes H*W*topk kb_result_compact records into out (device or
+ * page-locked host memory), stream-ordered, without a host wait, and with the
+ * ordering guarantees of kb_results_async.  A search without rescoring already
+ * holds its records in this form on the device, so they are copied as they are
+ * (one copy, no kernel): a third of the bytes of kb_result, which matters where
+ * the records cross the host link every step.  Rescored jobs convert their FP64
+ * records with one kernel first (through job-owned staging for host
+ * destinations).  KB_ERANGE (with *n_written = H*W*topk) if capacity (in
+ * records) is too small; KB_EINVAL for pageable host memory. */
+int kb_results_compact_async(kb_job *job, kb_result_compact *out, size_t capacity, size_t *n_written,
+                             void *stream);
 
 /* ---- light-curve outlier filter of kept trajectories (Sec. 3.3) ---------- */
 

@@ -19,6 +19,7 @@ Functions and the paper passages they follow:
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
 import subprocess
 import threading
@@ -35,15 +36,32 @@ REC_DTYPE = np.dtype([("x0", "<i4"), ("y0", "<i4"), ("vidx", "<i4"), ("nobs", "<
                       ("psi", "<f8"), ("phi", "<f8"), ("nu", "<f8"), ("alpha", "<f8")])
 
 
+_CMD = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off"]
+
+
+def _digest() -> str:
+    """sha256 of the source and the compiler command (not file times, which a copied
+    tree does not keep in order)."""
+    h = hashlib.sha256(" ".join(_CMD).encode())
+    with open(_SRC, "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
 def build(force: bool = False) -> str:
     """Compile kb_oracle.c into libkb_oracle.so (gcc, OpenMP, no FP contraction)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
+    stamp = _LIB + ".sha256"
+    digest = _digest()
+    if not force and os.path.exists(_LIB) and os.path.exists(stamp):
+        with open(stamp) as f:
+            if f.read().strip() == digest:
+                return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    subprocess.run(_CMD + ["-o", tmp, _SRC, "-lm"], check=True)
     os.replace(tmp, _LIB)
+    with open(stamp + ".tmp%d" % os.getpid(), "w") as f:
+        f.write(digest + "\n")
+    os.replace(stamp + ".tmp%d" % os.getpid(), stamp)
     return _LIB
 
 

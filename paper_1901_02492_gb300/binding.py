@@ -27,6 +27,11 @@ RESULT_DTYPE = np.dtype([("x0", "<i4"), ("y0", "<i4"), ("vidx", "<i4"), ("nobs",
                          ("nu", "<f8"), ("alpha", "<f8")])
 assert RESULT_DTYPE.itemsize == 48
 
+# kb_result_compact: start pixel and velocity implied by the position and the caller's grid
+COMPACT_DTYPE = np.dtype([("psi", "<f4"), ("phi", "<f4"), ("nu", "<f4"), ("vidx", "<u2"), ("nobs", "u1"),
+                          ("reserved", "u1")])
+assert COMPACT_DTYPE.itemsize == 16
+
 FILTERED_DTYPE = np.dtype([("x0", "<i4"), ("y0", "<i4"), ("vidx", "<i4"), ("nobs", "<i4"), ("nrejected", "<i4"),
                            ("reserved", "<i4"), ("rejected", "<u4", (4,)), ("psi", "<f8"), ("phi", "<f8"),
                            ("nu", "<f8"), ("alpha", "<f8")])
@@ -62,7 +67,7 @@ _kb_set_search_carveout = _sig("kb_set_search_carveout", _i32, [_P, _i32])
 _kb_set_search_waves = _sig("kb_set_search_waves", _i32, [_P, _i32])
 _kb_set_search_swizzle = _sig("kb_set_search_swizzle", _i32, [_P, _i32])
 _kb_set_search_order = _sig("kb_set_search_order", _i32, [_P, _i32])
-_kb_measure_gather_peak = _sig("kb_measure_gather_peak", _i32, [_P, ctypes.POINTER(ctypes.c_double)])
+_kb_measure_gather_peak = _sig("kb_measure_gather_peak", _i32, [_P, _i32, _i32, ctypes.POINTER(ctypes.c_double)])
 _kb_stack_create = _sig("kb_stack_create", _i32, [_P, _i32, _i32, _i32, _i32, ctypes.POINTER(_P)])
 _kb_stack_free = _sig("kb_stack_free", None, [_P])
 _kb_make_psi_phi = _sig("kb_make_psi_phi", _i32, [_P, _P, _P, _P, _P, _i32, _f32, _P])
@@ -84,6 +89,7 @@ _kb_filter_lightcurves = _sig("kb_filter_lightcurves", _i32, [_P, _P, ctypes.c_d
 _kb_stamps = _sig("kb_stamps", _i32, [_P, _P, _P, _i32, _i32, _i32, _P, _P, _P, _i32, _i32, _i32, _P, _P, _P,
                                       _P])
 _kb_results_async = _sig("kb_results_async", _i32, [_P, _P, _sz, ctypes.POINTER(_sz), _P])
+_kb_results_compact_async = _sig("kb_results_compact_async", _i32, [_P, _P, _sz, ctypes.POINTER(_sz), _P])
 _kb_cluster = _sig("kb_cluster", _i32, [_P, _P, _sz, _P, _P, _P, _P, ctypes.POINTER(_sz), _P])
 _kb_batch_create = _sig("kb_batch_create", _i32, [_P, _i32, _P, _i32, ctypes.POINTER(_P)])
 _kb_batch_run = _sig("kb_batch_run", _i32, [_P, _P])
@@ -95,7 +101,7 @@ EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_s
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
             "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static",
             "kb_batch_create", "kb_batch_run", "kb_batch_groups", "kb_batch_free", "kb_estimate_bytes",
-            "kb_filter_lightcurves", "kb_stamps", "kb_cluster", "kb_results_async"]
+            "kb_filter_lightcurves", "kb_stamps", "kb_cluster", "kb_results_async", "kb_results_compact_async"]
 
 
 class ClusterParams(ctypes.Structure):
@@ -176,10 +182,11 @@ class Context:
         """Launch the search in bands of `waves` resident waves of CTAs (-1 automatic, 0 one launch)."""
         self.check(_kb_set_search_waves(self.h, int(waves)))
 
-    def measure_gather_peak(self) -> float:
-        """L2-to-SM GB/s of the search's access form on this device (roofline denominator)."""
+    def measure_gather_peak(self, warp_bytes: int = 512, align_bytes: int = 8) -> float:
+        """L2-to-SM GB/s of the search's access form on this device (roofline denominator): warps
+        reading warp_bytes contiguous bytes at scattered multiples of align_bytes."""
         v = ctypes.c_double()
-        self.check(_kb_measure_gather_peak(self.h, ctypes.byref(v)))
+        self.check(_kb_measure_gather_peak(self.h, int(warp_bytes), int(align_bytes), ctypes.byref(v)))
         return v.value
 
     @property
@@ -257,12 +264,48 @@ class Stack:
             pass
 
 
+def _check_device_tensor(name, t, dtype, numel, device):
+    """The C entry point gets raw pointers and no buffer sizes, so the wrapper checks each
+    buffer before the call: a CUDA tensor on the given device, contiguous, of the given
+    dtype and element count."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.device != device:
+        raise ValueError("%s is on %s, not on %s" % (name, t.device, device))
+    if t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+
+
 def make_psi_phi_static(sci, var, mask, psf, out, bright_max=math.inf, stream=None):
     """psi/phi planes into the caller's device buffer `out` (float32 [N][H][W][2]) without any
-    allocation: the PSF taps go to the library's static device scratch (see include/kb.h)."""
+    allocation: the PSF taps go to the library's static device scratch (see include/kb.h).
+    sci, var: float32 CUDA tensors [N][H][W]; mask: uint8 [N][H][W] or None; psf: host
+    [N][K][K]; all on the current CUDA device.  Nothing is launched unless every buffer
+    matches (N, H, W)."""
+    import torch
     psf = np.ascontiguousarray(psf, dtype=np.float32)
+    if psf.ndim != 3 or psf.shape[1] != psf.shape[2]:
+        raise ValueError("psf must be [N][K][K], got shape %s" % (psf.shape,))
+    if not isinstance(sci, torch.Tensor) or sci.dim() != 3:
+        raise ValueError("sci must be a [N][H][W] tensor")
     N, K = psf.shape[0], psf.shape[-1]
     H, W = sci.shape[-2], sci.shape[-1]
+    if sci.shape[0] != N:
+        raise ValueError("sci has %d epochs, the psf %d" % (sci.shape[0], N))
+    for name, t in (("sci", sci), ("var", var), ("mask", mask), ("out", out)):
+        if t is not None and not (isinstance(t, torch.Tensor) and t.is_cuda):
+            raise ValueError("%s must be a CUDA tensor" % name)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    _check_device_tensor("sci", sci, torch.float32, N * H * W, dev)
+    _check_device_tensor("var", var, torch.float32, N * H * W, dev)
+    if mask is not None:
+        _check_device_tensor("mask", mask, torch.uint8, N * H * W, dev)
+    _check_device_tensor("out", out, torch.float32, 2 * N * H * W, dev)
     rc = _kb_make_psi_phi_static(_ptr(sci), _ptr(var), _ptr(mask), psf.ctypes.data, N, H, W, K,
                                  float(bright_max), _ptr(out), _stream(stream))
     if rc != KB_OK:
@@ -343,6 +386,14 @@ class Job:
         cap = (out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes) // RESULT_DTYPE.itemsize
         written = _sz()
         self.ctx.check(_kb_results_async(self.h, _ptr(out), cap, ctypes.byref(written), _stream(stream)))
+        return out
+
+    def results_compact_async(self, out, stream=None):
+        """Enqueue the compact records [H][W][k] (COMPACT_DTYPE, 16 bytes each) into `out` (a CUDA
+        uint8 tensor or page-locked host memory) on `stream` without waiting."""
+        cap = (out.numel() * out.element_size() if hasattr(out, "numel") else out.nbytes) // COMPACT_DTYPE.itemsize
+        written = _sz()
+        self.ctx.check(_kb_results_compact_async(self.h, _ptr(out), cap, ctypes.byref(written), _stream(stream)))
         return out
 
     def filter_lightcurves(self, stack: Stack, nsigma=5.0, out=None, stream=None):

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
 import subprocess
 
@@ -15,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkb.so")
+STAMP = LIB + ".sha256"     # digest of the sources and flags the library was built from
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -31,17 +33,31 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(INCLUDE, "kb.h"), __file__]
 
 
+def source_digest() -> str:
+    """sha256 over every input of the build (sources, headers, this script) and the
+    compiler flags.  File times are not used: a copied tree keeps the times of the
+    copy, so a library newer than changed sources would otherwise be reused."""
+    h = hashlib.sha256()
+    h.update(" ".join([NVCC] + ARCH + FLAGS).encode())
+    for d in sorted(set(_deps())):
+        h.update(os.path.relpath(d, os.path.dirname(HERE)).encode())
+        with open(d, "rb") as f:
+            h.update(hashlib.sha256(f.read()).digest())
+    return h.hexdigest()
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    with open(STAMP) as f:
+        return f.read().strip() == source_digest()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link libkb.so; returns its path."""
     if not force and up_to_date():
         return LIB
+    digest = source_digest()
     os.makedirs(BUILD, exist_ok=True)
     srcs = _sources()
 
@@ -67,6 +83,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    with open(STAMP + ".tmp%d" % os.getpid(), "w") as f:
+        f.write(digest + "\n")
+    os.replace(STAMP + ".tmp%d" % os.getpid(), STAMP)
     return LIB
 
 

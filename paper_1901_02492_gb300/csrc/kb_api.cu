@@ -1294,6 +1294,61 @@ int kb_results_async(kb_job *job, kb_result *out, size_t capacity, size_t *n_wri
     return enqueue_results(job, out, need, dev, true, (cudaStream_t)stream);
 }
 
+int kb_results_compact_async(kb_job *job, kb_result_compact *out, size_t capacity, size_t *n_written,
+                             void *stream) {
+    if (!job) return KB_EINVAL;
+    kb_ctx *ctx = job->ctx;
+    if (job->k == 0) return fail(ctx, KB_EINVAL, "kb_results_compact_async: no search has run on this job");
+    const size_t need = (size_t)job->H * job->W * job->k;
+    if (n_written) *n_written = need;
+    if (!out) return fail(ctx, KB_EINVAL, "kb_results_compact_async: out is NULL");
+    if (capacity < need)
+        return fail(ctx, KB_ERANGE, "kb_results_compact_async: capacity %zu < %zu records", capacity, need);
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, out) != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    const bool dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (!dev && at.type != cudaMemoryTypeHost)
+        return fail(ctx, KB_EINVAL, "kb_results_compact_async: out must be device or page-locked host memory");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamWaitEvent(st, job->done, 0);   // the job's last search
+    const size_t bytes = need * sizeof(kb_result_compact);
+    cudaError_t e = cudaSuccess;
+    if (!job->rescored && job->kkeep == job->k) {
+        // the search's own records: [H*W][k] of the same 16-byte layout
+        e = cudaMemcpyAsync(out, job->recs, bytes, cudaMemcpyDefault, st);
+    } else if (!job->rescored) {
+        return fail(ctx, KB_EINVAL, "kb_results_compact_async: the job kept %d candidates for %d results",
+                    job->kkeep, job->k);
+    } else if (dev) {
+        e = kb::launch_compact(job->recs64, (long long)need, out, st);
+    } else {
+        // through the job's staging buffer (counted in kb_result units)
+        const size_t cap = (bytes + sizeof(kb_result) - 1) / sizeof(kb_result);
+        if (job->expand_cap < cap) {
+            cudaStreamWaitEvent(ctx->astream, job->done, 0);
+            cudaStreamWaitEvent(ctx->astream, job->rdone, 0);
+            dev_free(ctx, job->expand);
+            dev_release(ctx, job->expand_cap * sizeof(kb_result));
+            job->bytes -= std::min(job->bytes, job->expand_cap * sizeof(kb_result));
+            job->expand = nullptr;
+            job->expand_cap = 0;
+            int rc = dev_alloc(ctx, cap * sizeof(kb_result), (void **)&job->expand, &job->bytes);
+            if (rc != KB_OK) return rc;
+            job->expand_cap = cap;
+        }
+        kb_result_compact *stage = reinterpret_cast<kb_result_compact *>(job->expand);
+        e = kb::launch_compact(job->recs64, (long long)need, stage, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, stage, bytes, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(job->rdone, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_results_compact_async");
+    return KB_OK;
+}
+
 int kb_filter_lightcurves(kb_job *job, const kb_stack *s, double nsigma, kb_filtered *out, size_t capacity,
                           size_t *n_written, void *stream) {
     if (!job) return KB_EINVAL;

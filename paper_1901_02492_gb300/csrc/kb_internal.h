@@ -44,6 +44,7 @@ struct Rec {
     uint32_t meta;  // vidx (bits 0-15, 0xFFFF = empty) | nobs (bits 16-23) | flags (24-31)
 };
 constexpr uint32_t kEmptyVidx = 0xFFFFu;
+static_assert(sizeof(Rec) == sizeof(kb_result_compact), "the device record is the compact transfer record");
 
 // Device record after FP64 rescoring (32 bytes).
 struct Rec64 {
@@ -225,6 +226,8 @@ struct ExpandArgs {
     kb_result *out;          // device
 };
 cudaError_t launch_expand(const ExpandArgs &a, cudaStream_t st);
+// FP64 records of a rescored job to kb_result_compact [H*W][k]
+cudaError_t launch_compact(const Rec64 *recs64, long long count, kb_result_compact *out, cudaStream_t st);
 
 // Sec. 3.3 light-curve filter of kept trajectories
 struct FilterArgs {

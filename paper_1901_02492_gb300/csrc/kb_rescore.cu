@@ -514,6 +514,32 @@ cudaError_t launch_stamps(const StampArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void compact_kernel(const Rec64 *recs64, long long count, kb_result_compact *out) {
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < count;
+         r += (long long)gridDim.x * blockDim.x) {
+        const Rec64 q = recs64[r];
+        kb_result_compact o;
+        const bool empty = q.vidx == kEmptyVidx;
+        o.psi = empty ? 0.0f : (float)q.psi;
+        o.phi = empty ? 0.0f : (float)q.phi;
+        o.nu = empty ? -INFINITY : (float)q.nu;
+        o.vidx = (uint16_t)q.vidx;
+        o.nobs = empty ? 0 : (uint8_t)q.nobs;
+        o.reserved = 0;
+        out[r] = o;
+    }
+}
+}  // namespace
+
+cudaError_t launch_compact(const Rec64 *recs64, long long count, kb_result_compact *out, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    long long blocks = (count + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    compact_kernel<<<(int)blocks, 256, 0, st>>>(recs64, count, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_expand(const ExpandArgs &a, cudaStream_t st) {
     if (a.count <= 0) return cudaSuccess;
     long long blocks = (a.count + 255) / 256;

@@ -14,6 +14,14 @@
 // calls share it.  A call overwrites the part it uses before its kernel runs,
 // so nothing in it has to start at zero; calls that overlap on the GPU (for
 // example on two streams) race on it and must be ordered by the caller.
+//
+// The taps reach the array through a host staging buffer that every call
+// rewrites, so a call on a stream that is being captured into a CUDA graph is
+// refused (KB_EINVAL): a captured copy would read that buffer when the graph is
+// replayed, by then holding another call's taps.  The array's device address is
+// looked up on every call (cudaGetSymbolAddress allocates nothing and is cheap),
+// so it stays right when the device's context is destroyed and created again
+// and the module is loaded at another address.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -26,13 +34,11 @@
 namespace {
 
 constexpr size_t kStaticTapFloats = 65536;   // 256 KB of PSF taps
-constexpr int kMaxDevices = 64;
 
 // the scratch: per-epoch taps in the layout documented in kb_psiphi.cu
 static __device__ __align__(256) float g_static_taps[kStaticTapFloats];
 
 std::mutex g_mu;
-float *g_taps_dev[kMaxDevices] = {};     // device address of g_static_taps, per device
 float g_taps_host[kStaticTapFloats];     // host staging of one call's taps (guarded by g_mu)
 
 bool is_device(const void *p) {
@@ -48,14 +54,20 @@ bool is_device(const void *p) {
 
 extern "C" int kb_make_psi_phi_static(const float *sci, const float *var, const uint8_t *mask, const float *psf,
                                       int N, int H, int W, int K, float bright_max, float *out, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    // first, before any other CUDA call: a capturing stream is refused (see above)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return KB_EINVAL;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return KB_EINVAL;
     if (!sci || !var || !psf || !out) return KB_EINVAL;
     if (N < 1 || N > KB_MAX_EPOCHS || H < 1 || W < 1 || H > KB_MAX_SIDE || W > KB_MAX_SIDE) return KB_EINVAL;
     if (K < 1 || K > KB_MAX_PSF || (K % 2) == 0) return KB_EINVAL;
     for (size_t i = 0; i < (size_t)N * K * K; ++i)
         if (!std::isfinite(psf[i])) return KB_EINVAL;
     if (!is_device(sci) || !is_device(var) || !is_device(out) || (mask && !is_device(mask))) return KB_EINVAL;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return KB_ECUDA;
 
     // separable PSFs for every epoch take the two-pass kernel, as in kb_make_psi_phi
     bool sep = true;
@@ -65,14 +77,12 @@ extern "C" int kb_make_psi_phi_static(const float *sci, const float *var, const 
     if (nt > kStaticTapFloats) return KB_EINVAL;   // more taps than the static scratch holds
 
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_taps_dev[dev]) {
-        // once per device, with that device current: the device address of the array
-        float *p = nullptr;
-        if (cudaGetSymbolAddress((void **)&p, g_static_taps) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return KB_ECUDA;
-        }
-        g_taps_dev[dev] = p;
+    // the device address of the array on the current device (the host-side name
+    // g_static_taps is only a stand-in, not an address a kernel may use)
+    float *taps_dev = nullptr;
+    if (cudaGetSymbolAddress((void **)&taps_dev, g_static_taps) != cudaSuccess || !taps_dev) {
+        cudaGetLastError();
+        return KB_ECUDA;
     }
     for (int e = 0; e < N; ++e) {
         const float *T = psf + (size_t)e * K * K;
@@ -92,9 +102,8 @@ extern "C" int kb_make_psi_phi_static(const float *sci, const float *var, const 
             }
         }
     }
-    cudaStream_t st = (cudaStream_t)stream;
     // from pageable memory: the staging is consumed before this call returns
-    if (cudaMemcpyAsync(g_taps_dev[dev], g_taps_host, nt * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (cudaMemcpyAsync(taps_dev, g_taps_host, nt * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return KB_ECUDA;
 
     kb::PsiPhiArgs a;
@@ -110,7 +119,7 @@ extern "C" int kb_make_psi_phi_static(const float *sci, const float *var, const 
     a.origin = 0;
     a.K = K;
     a.separable = sep;
-    a.taps = g_taps_dev[dev];
+    a.taps = taps_dev;
     a.out = reinterpret_cast<float2 *>(out);
     a.maxbits = nullptr;
     return kb::launch_psi_phi(a, st) == cudaSuccess ? KB_OK : KB_ECUDA;

@@ -126,3 +126,29 @@ def test_offsets_reject_out_of_range(lib):
     with pytest.raises(lib.KBError):
         lib.offsets(np.array([0.0, np.nan]), np.array([1.0]), np.array([0.0]))
     lib.offsets(np.array([0.0, 63.9]), np.array([4095.9]), np.array([-4095.9]))
+
+
+def test_static_psi_phi_wrapper_refuses_host_buffers_before_the_call(lib):
+    """kb_make_psi_phi_static gets raw pointers and no buffer sizes, so the binding checks
+    every buffer first; host tensors and mismatched shapes never reach the library."""
+    import torch
+    N, H, W, K = 2, 5, 6, 3
+    psf = np.full((N, K, K), 1.0 / 9, np.float32)
+    sci = torch.zeros((N, H, W))
+    var = torch.ones((N, H, W))
+    out = torch.zeros((N, H, W, 2))
+    with pytest.raises(ValueError):
+        lib.make_psi_phi_static(sci, var, None, psf, out)
+    with pytest.raises(ValueError):
+        lib.make_psi_phi_static(sci[0], var, None, psf, out)          # not [N][H][W]
+    with pytest.raises(ValueError):
+        lib.make_psi_phi_static(sci, var, None, psf[:, :2, :], out)   # psf not square
+    assert torch.all(out == 0)
+
+
+def test_build_digest_follows_the_sources(tmp_path, lib):
+    """build.up_to_date() compares a digest of the sources, not file times."""
+    from paper_1901_02492_gb300 import build
+    assert build.up_to_date()
+    with open(build.STAMP) as f:
+        assert f.read().strip() == build.source_digest()

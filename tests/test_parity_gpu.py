@@ -333,6 +333,52 @@ def test_results_async_overlaps_and_orders_reads(kb, ctx):
     s.free()
 
 
+def _compact_from_full(kb, full):
+    """The compact records a kb_result array implies (FP32 rounding of the FP64 fields)."""
+    f = full.reshape(-1)
+    c = np.zeros(f.size, kb.COMPACT_DTYPE)
+    empty = f["vidx"] < 0
+    c["psi"] = np.where(empty, 0.0, f["psi"])
+    c["phi"] = np.where(empty, 0.0, f["phi"])
+    c["nu"] = np.where(empty, -np.inf, f["nu"].astype(np.float32))
+    c["vidx"] = np.where(empty, 0xFFFF, f["vidx"]).astype(np.uint16)
+    c["nobs"] = np.where(empty, 0, f["nobs"]).astype(np.uint8)
+    return c
+
+
+@pytest.mark.parametrize("storage,flags", [("f32", 0), ("bf16", 1), ("f16", 1)])
+def test_results_compact_equal_full_records(kb, ctx, storage, flags):
+    """kb_results_compact_async (16-byte records, pinned host and device destinations) carries
+    the same values as kb_results, bit for bit: FP32 searches copy their device records as they
+    are, rescored ones round the FP64 fields to FP32 as kb_results does for psi and phi."""
+    st = synth.small_stack(92, 6, 70, 150, K=5, nan_frac=0.01, n_angles=8, n_speeds=8, s_hi=12.0, n_sources=3,
+                           flux=40.0)
+    N, H, W = st.sci.shape
+    s = gpu_planes(kb, ctx, st, storage)
+    job = kb.Job(ctx, H, W, N, st.vx.size, st.k, flags)
+    job.search(s, st.times, st.vx, st.vy, st.k, -math.inf, flags)
+    full = job.results()
+    n = H * W * st.k * kb.COMPACT_DTYPE.itemsize
+    pinned = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    dev = torch.empty(n, dtype=torch.uint8, device=DEV)
+    job.results_compact_async(pinned, stream=torch.cuda.Stream())
+    job.results_compact_async(dev)
+    torch.cuda.synchronize()
+    got = pinned.numpy().view(kb.COMPACT_DTYPE)
+    assert got.tobytes() == dev.cpu().numpy().tobytes()
+    want = _compact_from_full(kb, full)
+    for f in ("psi", "phi", "nu"):   # FP64 -> FP32 rounds to nearest on both sides
+        assert np.array_equal(got[f].view(np.uint32), want[f].view(np.uint32)), f
+    for f in ("vidx", "nobs", "reserved"):
+        assert np.array_equal(got[f], want[f]), f
+    with pytest.raises(kb.KBError):
+        job.results_compact_async(np.empty(H * W * st.k, kb.COMPACT_DTYPE))
+    with pytest.raises(kb.KBError):
+        job.results_compact_async(torch.empty(n - 16, dtype=torch.uint8, device=DEV))
+    job.free()
+    s.free()
+
+
 @pytest.mark.parametrize("cols", [1, 3, 5])
 def test_tile_order_swizzle_equals_row_order(kb, ctx, cols):
     """kb_set_search_swizzle: tiles dealt out in super-columns (the last one narrower: 7 tile
