@@ -214,11 +214,20 @@ def measured_peaks():
         return {}
 
 
-def search_span(storage, variant):
+def search_span(storage, variant, k):
     """Pixels per warp span of the register-gather search shape (the library's search_span)."""
-    p32, p16 = [2, 4, 2, 4, 2], [1, 2, 1, 2, 1]
+    p32, p16 = [2, 4, 2, 4, 2], [2, 2, 1, 2, 1]
     v = variant if 1 <= variant <= 4 else 0
+    if storage != "f32" and v == 0 and k > 8:
+        return 64
     return 32 * p32[v] if storage == "f32" else 64 * p16[v]
+
+
+def job_kkeep(k, rescore, storage):
+    """Candidates per pixel the search keeps (the library's job_kkeep)."""
+    if not rescore:
+        return k
+    return k + (max(2, k // 2) if storage == "bf16" else max(2, k // 4))
 
 
 def recorded_levels(kernel_tag):
@@ -392,9 +401,10 @@ def run_ours(args):
     var = var_h.to(dev)
     stream = torch.cuda.current_stream(dev)
     # roofline denominators, before the timed region: the L2-to-SM rate of the search's own
-    # access form (warp spans of 512 B in FP32, 256 B in 16-bit storage, at any 8-byte offset),
+    # access form (the warp span of the launch shape, 512 B for the default shapes, at any 8-byte offset),
     # and of line-aligned spans for reference
-    span_bytes = 512 if args.storage == "f32" else 256
+    span = search_span(args.storage, args.variant, job_kkeep(k, args.rescore, args.storage))
+    span_bytes = span * BYTES_PER_EVAL[args.storage]
     gather_peak = ctx.measure_gather_peak(span_bytes, 8)
     gather_peak_aligned = ctx.measure_gather_peak(span_bytes, 256)
     launches_per_step = 2 + (1 if args.storage != "f32" else 0) + (2 if args.rescore else 0)
@@ -497,7 +507,6 @@ def run_ours(args):
     # gathers are served by L2 (L1 catches the early epochs' reuse, HBM sees little:
     # the planes stay L2-resident), so the denominator is the L2-to-SM bandwidth of
     # exactly this access form, measured on this device by the library.
-    span = search_span(args.storage, args.variant)
     classes = search_byte_classes(kb, st.times, st.vx, st.vy, H, W, BYTES_PER_EVAL[args.storage], span)
     alg_bytes = classes["alg_bytes_per_launch"]
     achieved = alg_bytes / (ms_search * 1e-3) / 1e9
@@ -597,7 +606,7 @@ def run_ours(args):
                            "ms_per_call": cms, "candidates_per_s": M / (cms * 1e-3), "groups": groups}
         del cand
     if args.rescore:
-        line["rescore"] = {"candidates_per_pixel": k + (max(2, k // 2) if args.storage == "bf16" else max(2, k // 4)),
+        line["rescore"] = {"candidates_per_pixel": job_kkeep(k, True, args.storage),
                            "repaired_pixels": repaired,
                            "repaired_fraction": repaired / float(H * W)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

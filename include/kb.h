@@ -117,15 +117,6 @@ int kb_set_search_variant(kb_ctx *ctx, int variant);
  * gathers of the early epochs reuse.  Results do not depend on it. */
 int kb_set_search_carveout(kb_ctx *ctx, int percent);
 
-/* Tuning knob: launch the register-gather search kernel in bands of start rows,
- * each `waves` times the CTAs the device holds at once (0: the whole image in
- * one launch; -1: automatic, which is 0).  The CTAs of one band start together
- * and move through the velocities roughly in step, which keeps the late epochs'
- * rows they read within a narrower window; measured on the 12 x 4096^2 stack,
- * the launch tails cost more than that saves (1 wave: 137 ms against 118 ms).
- * Results do not depend on it. */
-int kb_set_search_waves(kb_ctx *ctx, int waves);
-
 /* Tuning knob: the order in which the register-gather search kernel's CTAs
  * take their start-pixel tiles.  cols > 0: the tiles are dealt out in
  * super-columns `cols` tiles wide, row by row within each (so the CTAs resident

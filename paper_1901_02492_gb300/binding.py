@@ -64,7 +64,6 @@ _kb_last_error = _sig("kb_last_error", ctypes.c_char_p, [_P])
 _kb_hbm_in_use = _sig("kb_hbm_in_use", _sz, [_P])
 _kb_set_search_variant = _sig("kb_set_search_variant", _i32, [_P, _i32])
 _kb_set_search_carveout = _sig("kb_set_search_carveout", _i32, [_P, _i32])
-_kb_set_search_waves = _sig("kb_set_search_waves", _i32, [_P, _i32])
 _kb_set_search_swizzle = _sig("kb_set_search_swizzle", _i32, [_P, _i32])
 _kb_set_search_order = _sig("kb_set_search_order", _i32, [_P, _i32])
 _kb_measure_gather_peak = _sig("kb_measure_gather_peak", _i32, [_P, _i32, _i32, ctypes.POINTER(ctypes.c_double)])
@@ -97,7 +96,7 @@ _kb_batch_groups = _sig("kb_batch_groups", _i32, [_P, _P, _i32, ctypes.POINTER(_
 _kb_batch_free = _sig("kb_batch_free", None, [_P])
 
 EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_search_variant",
-            "kb_set_search_carveout", "kb_set_search_waves", "kb_set_search_swizzle", "kb_set_search_order", "kb_measure_gather_peak", "kb_stack_create", "kb_stack_free",
+            "kb_set_search_carveout", "kb_set_search_swizzle", "kb_set_search_order", "kb_measure_gather_peak", "kb_stack_create", "kb_stack_free",
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
             "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static",
             "kb_batch_create", "kb_batch_run", "kb_batch_groups", "kb_batch_free", "kb_estimate_bytes",
@@ -177,10 +176,6 @@ class Context:
     def set_search_order(self, order: int):
         """Velocity order: 0 by latest (dy, dx), 1 Hilbert over latest offsets, 2 the caller's, -1 automatic."""
         self.check(_kb_set_search_order(self.h, int(order)))
-
-    def set_search_waves(self, waves: int):
-        """Launch the search in bands of `waves` resident waves of CTAs (-1 automatic, 0 one launch)."""
-        self.check(_kb_set_search_waves(self.h, int(waves)))
 
     def measure_gather_peak(self, warp_bytes: int = 512, align_bytes: int = 8) -> float:
         """L2-to-SM GB/s of the search's access form on this device (roofline denominator): warps

@@ -265,13 +265,6 @@ const char *kb_last_error(const kb_ctx *ctx) { return ctx ? ctx->err.c_str() : "
 
 size_t kb_hbm_in_use(const kb_ctx *ctx) { return ctx ? ctx->in_use : 0; }
 
-int kb_set_search_waves(kb_ctx *ctx, int waves) {
-    if (!ctx) return KB_EINVAL;
-    if (waves < -1 || waves > 1024) return fail(ctx, KB_EINVAL, "waves %d not in -1..1024", waves);
-    ctx->search_waves = waves;
-    return KB_OK;
-}
-
 int kb_set_search_order(kb_ctx *ctx, int order) {
     if (!ctx) return KB_EINVAL;
     if (order < -1 || order > 2) return fail(ctx, KB_EINVAL, "order %d not in -1..2", order);
@@ -812,7 +805,6 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
     a.status = job->status;
     a.by0 = 0;
     a.nby = 0;
-    a.waves = ctx->search_waves < 0 ? 0 : ctx->search_waves;
     // automatic tile order: super-columns of 8 tiles (12 x 4096^2, FP32, k = 8: 97.7 ms
     // against 117.4 ms row by row; 6 and 12 tiles within 1 %)
     a.swz = ctx->search_swizzle < 0 ? 8 : ctx->search_swizzle;
@@ -863,7 +855,7 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     if (a.variant >= 5)
         e = kb::launch_search_tma(a, st);
     else
-        e = kb::launch_search(a, st, ctx->sm_count);
+        e = kb::launch_search(a, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "search kernel");
     if (rescore) {
         e = cudaMemsetAsync(job->ucount, 0, sizeof(int), st);
@@ -922,7 +914,7 @@ int index_bits(const kb::SearchArgs &a) {
 // about `frac` of each search's rows from its middle.
 void make_items(const kb_batch *b, int g, int variant, double frac, std::vector<int4> &out) {
     out.clear();
-    const int span = kb::search_span(b->groups[g].storage, variant), R = kb::kTileRows;
+    const int span = kb::search_span(b->groups[g].storage, variant, b->groups[g].kmax), R = kb::kTileRows;
     for (int j : b->group_jobs[g]) {
         const kb::SearchArgs &a = b->args[j];
         const int tx = (a.W + span - 1) / span, ty = (a.H + R - 1) / R;
@@ -963,7 +955,7 @@ cudaError_t launch_group(const kb_batch *b, int g, int variant, int schedule, in
             a.nby = std::max(1, std::min(ty, (int)std::ceil(ty * frac)));
             a.by0 = (ty - a.nby) / 2;
         }
-        e = kb::launch_search(a, (n++ & 1) ? st2 : st, b->ctx->sm_count);
+        e = kb::launch_search(a, (n++ & 1) ? st2 : st);
         if (e != cudaSuccess) break;
     }
     return e;
@@ -1046,7 +1038,7 @@ int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flag
             memset(&G, 0, sizeof G);
             G.storage = a.storage;
             G.index_bits = bits;
-            G.variant = 4;
+            G.variant = kb::default_variant(a.storage, a.k);
             G.kmax = a.k;
             b->groups.push_back(G);
             b->group_jobs.emplace_back();

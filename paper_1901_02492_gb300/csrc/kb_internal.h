@@ -66,7 +66,6 @@ struct kb_ctx {
     int search_carveout = -1; // -1 = automatic
     int search_order = -1;    // velocity processing order: 0 by latest (dy, dx), 1 Hilbert, 2 the caller's
     int search_swizzle = -1;  // register-gather search: tile order in super-columns of this many tiles (0: rows)
-    int search_waves = -1;    // register-gather search launched in bands of this many resident waves (0 and -1: one launch)
     std::string err;
     std::mutex mu;
     // Stream-ordered device memory: a pool that keeps freed blocks for reuse and
@@ -179,11 +178,10 @@ struct SearchArgs {
     const uint32_t *ptab;    // [V][N - n0] packed (dx, dy) int16 in processing order (pipelined kernel)
     int *status;             // device status word: KB_ETIMEOUT if a bounded wait gave up
     int by0, nby;            // register-gather kernel: row tiles by0 .. by0 + nby - 1 (nby 0: all)
-    int waves;               // launch in bands of this many resident waves of CTAs (0: one launch)
     int swz;                 // tile order: super-columns of this many tiles (0: row by row)
 };
 // register-gather kernel (variant 0 = its default shape, 1..4)
-cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, int sm_count);
+cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
 // TMA-pipelined kernel (variants 5..8)
 cudaError_t launch_search_tma(const SearchArgs &a, cudaStream_t st);
 // persistent batch kernel over (job, tile) items {job, tile x, tile y, 0}; all jobs of
@@ -191,8 +189,10 @@ cudaError_t launch_search_tma(const SearchArgs &a, cudaStream_t st);
 // carve = shared-memory carveout percent (-1: the automatic rule)
 cudaError_t launch_search_batch(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int storage,
                                 int variant, int kmax, int carve, bool idx64, int sm_count, cudaStream_t st);
-// pixels per CTA row segment of a register-gather shape (tile width)
-int search_span(int storage, int variant);
+// pixels per CTA row segment of a register-gather shape (tile width) for lists of k
+int search_span(int storage, int variant, int k);
+// the explicit shape (1..4) that the automatic choice (variant 0) takes for lists of k
+int default_variant(int storage, int k);
 // rows per CTA tile of the register-gather kernel
 constexpr int kTileRows = 8;
 

@@ -8,18 +8,7 @@
 // Work decomposition (GB300-first, not the paper's 32x16 thread blocks):
 //   - a CTA owns 8 rows x SPAN columns of start pixels, one warp per row; a lane
 //     owns P loads' worth of pixels (FP32: pixel lane + 32 p; 16-bit: the pixel
-//     pair 2 lane + 64 p, + 1) and runs the whole velocity loop for them.  The
-//     admission threshold of each pixel's top-k (its k-th (nu, vidx)) is in
-//     registers, the list of (nu, 16-bit velocity index) in shared memory.
-//     Shared memory per CTA is kept small: the kernel is latency-bound (resident
-//     warps set its throughput) and the SRAM left to L1 serves the early epochs'
-//     gathers, which neighbouring velocities share;
-//   - k <= 8: slot-major lists, each lane inserting into its own pixels' lists.
-//     k > 8: pixel-major lists with an odd stride (k | 1), and when at most
-//     kCoopMax lanes of a warp have a candidate for one pixel slot the warp
-//     inserts each cooperatively (lane j holds slot j: one load, one ballot, one
-//     shifted store) instead of one lane walking a long list while the others
-//     wait; the epochs' last, partial load batch is predicated (one round trip);
+//     pair 2 lane + 64 p, + 1) and runs the whole velocity loop for them;
 //   - for one (velocity, epoch) a warp's loads cover SPAN consecutive pixels of
 //     one plane row: fully coalesced 8-byte loads.  16-bit pairs are 8-byte
 //     aligned because the planes also exist shifted by one pixel (the "phase 1"
@@ -27,14 +16,16 @@
 //   - the (velocity, epoch) table is staged per CTA in shared memory and checked
 //     there once: each entry holds the element offset of the shifted row start
 //     (epoch plane and phase included), a mask of the CTA's warps whose shifted
-//     span overlaps the image, and the epoch's power-of-two scale exponents.
-//     The inner loop is one broadcast load (a 16-byte pair of entries for FP32
-//     and k > 8), one bit test, a select, the gathers and one packed f32x2
-//     accumulate per pixel (16-bit: one mixed-precision FMA per value);
+//     span overlaps the image, and for 16-bit storage the epoch's two
+//     power-of-two scales as bf16 bit patterns (the FMA's scale operand).  The
+//     inner loop per entry is one broadcast load, one mask test selecting the
+//     entry's offset or the offset of a zero block, one wide multiply-add for
+//     the address, the gathers and one packed f32x2 add per pixel (16-bit: one
+//     mixed-precision FMA per value);
 //   - spans that overlap the image only partly read the zero columns the planes
-//     carry left and right of every row (kSpan wide); spans that miss it read a
-//     small zero block that stays in L1, so off-image steps cost no memory
-//     traffic and "outside contributes nothing" holds exactly;
+//     carry left and right of every row (kSpan wide); spans that miss it read the
+//     zero columns left of row 0 of plane 0, which stay in L1, so off-image steps
+//     cost no memory traffic and "outside contributes nothing" holds exactly;
 //   - epochs at t = t_min have offset 0 for every velocity: their contribution is
 //     loaded once per pixel before the velocity loop;
 //   - velocities are processed in the order the host planner gives (sorted by
@@ -43,8 +34,18 @@
 //     result;
 //   - CTAs take their tiles in super-columns a few tiles wide, row by row within
 //     each, so the CTAs resident at one time cover a compact block of start
-//     pixels and the late epochs' rows they read stay in L2 (row-by-row order
-//     makes them span whole image rows, whose late-epoch windows fall out).
+//     pixels and the late epochs' rows they read stay in L2;
+//   - top-k: each pixel's list of (nu, 16-bit velocity index), best first, is in
+//     shared memory (slot-major: slot i of list column c at c + i * LS, so the
+//     lanes of a warp touch distinct banks); the k-th entry is mirrored in
+//     registers as the admission threshold.  A trajectory that beats its pixel's
+//     threshold is not inserted at once: the warp appends it to a queue in
+//     shared memory (ballot + popc), and when 32 or more are pending every lane
+//     inserts one.  Candidates arrive at scattered velocities for the 64-128
+//     pixels of a warp, so inserting on arrival keeps the warp busy for one
+//     lane's insertion at almost every velocity; batched, the lanes insert
+//     together.  Lists up to 8 long insert by rank (all slots loaded at once,
+//     then the tail shifted); longer ones walk up from the last slot.
 // The Psi/Phi of each kept trajectory are recomputed at the end by the same
 // sequence of operations (bit-identical) together with nobs.
 #include <cuda_runtime.h>
@@ -61,17 +62,25 @@ using namespace dev;
 
 constexpr int WARPS = 8;
 constexpr int THREADS = WARPS * 32;
-constexpr int TAB = 512;    // (velocity, epoch) entries staged per chunk (small: occupancy)
 constexpr uint16_t kNoV = 0xFFFF;   // empty list slot (velocity indices are < 65535)
+constexpr int kRankMax = 8;         // lists up to this long insert by rank, longer ones by walking
 
-// zero block read by spans that miss the image (static device memory is zero-initialised)
-__device__ __align__(16) float2 g_zero_block[4 * 32];
+// (velocity, epoch) entries staged per chunk (small: occupancy); the 16-bit
+// entries are twice as large and their CTAs hold twice the pixels
+template <int STORAGE>
+__host__ __device__ constexpr int tab_entries() { return STORAGE == KB_F32 ? 512 : 256; }
 
 __device__ __forceinline__ float2 exp_scale(int e) {
     return make_float2(__int_as_float((e & 0xff) << 23), __int_as_float(((e >> 8) & 0xff) << 23));
 }
 __device__ __forceinline__ int scale_exp(float2 s) {
     return (int)((__float_as_uint(s.x) >> 23) & 0xff) | (int)(((__float_as_uint(s.y) >> 23) & 0xff) << 8);
+}
+// Scale operand of a 16-bit load: the bf16 bit patterns of the epoch's two
+// power-of-two scales, psi in the low half and phi in the high half (a power of
+// two is exactly a bf16).  Unused for FP32.
+__device__ __forceinline__ uint32_t sc_of(float2 s) {
+    return (__float_as_uint(s.x) >> 16) | (__float_as_uint(s.y) & 0xffff0000u);
 }
 
 // per-load traits: FP32 loads one pixel's (psi, phi), 16-bit loads two adjacent pixels' codes
@@ -81,50 +90,67 @@ template <>
 struct Gather<KB_F32> {
     typedef float2 LT;
     static constexpr int PIX = 1;
-    __device__ __forceinline__ static void acc(float2 *a, LT v, float2) { a[0] = add2(a[0], v); }
+    __device__ __forceinline__ static void acc(float2 *a, LT v, uint32_t) { a[0] = add2(a[0], v); }
 };
-template <int STORAGE>
-struct Gather16 {
-    typedef uint2 LT;
-    static constexpr int PIX = 2;
-    __device__ __forceinline__ static void acc(float2 *a, LT v, float2 s) {
-        a[0] = Store<STORAGE>::acc(a[0], v.x, s);
-        a[1] = Store<STORAGE>::acc(a[1], v.y, s);
-    }
-};
-// BF16: mixed-precision fma.rn.f32.bf16 takes each code straight from its register
-// half; the scale is a power of two (exactly a bf16), so code * scale is exact and
-// the sum is rounded once -- the same FP32 result as unpacking and fma.rn.f32x2.
-__device__ __forceinline__ void bf16_acc(float2 &a, uint32_t code, uint32_t sp16, uint32_t sf16) {
+// BF16: mixed-precision fma.rn.f32.bf16 takes each code and each scale straight from
+// its register half; the scale is a power of two, so code * scale is exact and the
+// sum is rounded once -- the same FP32 result as unpacking and fma.rn.f32x2.
+__device__ __forceinline__ void bf16_acc(float2 &a, uint32_t code, uint32_t sc) {
     asm("{\n\t.reg .b16 lo, hi, sp, sf;\n\t"
         "mov.b32 {lo, hi}, %2;\n\t"
-        "cvt.u16.u32 sp, %3;\n\t"
-        "cvt.u16.u32 sf, %4;\n\t"
+        "mov.b32 {sp, sf}, %3;\n\t"
         "fma.rn.f32.bf16 %0, lo, sp, %0;\n\t"
         "fma.rn.f32.bf16 %1, hi, sf, %1;\n\t}"
         : "+f"(a.x), "+f"(a.y)
-        : "r"(code), "r"(sp16), "r"(sf16));
+        : "r"(code), "r"(sc));
 }
 template <>
 struct Gather<KB_BF16> {
     typedef uint2 LT;
     static constexpr int PIX = 2;
-    __device__ __forceinline__ static void acc(float2 *a, LT v, float2 s) {
-        // bf16 bit patterns of the two scales: the high halves of their float bits
-        const uint32_t sp = __float_as_uint(s.x) >> 16, sf = __float_as_uint(s.y) >> 16;
-        bf16_acc(a[0], v.x, sp, sf);
-        bf16_acc(a[1], v.y, sp, sf);
+    __device__ __forceinline__ static void acc(float2 *a, LT v, uint32_t sc) {
+        bf16_acc(a[0], v.x, sc);
+        bf16_acc(a[1], v.y, sc);
     }
 };
+// FP16: the codes converted to FP32 and fused with the scales (fma.rn.f32x2)
 template <>
-struct Gather<KB_F16> : Gather16<KB_F16> {};
+struct Gather<KB_F16> {
+    typedef uint2 LT;
+    static constexpr int PIX = 2;
+    __device__ __forceinline__ static void acc(float2 *a, LT v, uint32_t sc) {
+        const float2 s = make_float2(__uint_as_float(sc << 16), __uint_as_float(sc & 0xffff0000u));
+        a[0] = Store<KB_F16>::acc(a[0], v.x, s);
+        a[1] = Store<KB_F16>::acc(a[1], v.y, s);
+    }
+};
 
-// staged table entry: element offset (32 or 64 bit) and (warp mask | scale exponents << 16)
+// staged table entry: element offset (32 or 64 bit), the mask of the CTA's warps
+// whose shifted span overlaps the image, and for 16-bit storage the epoch's scale
+// operand (16 bytes: one shared load)
+template <typename I, bool SC>
+struct Entry;
 template <typename I>
-struct Entry {
+struct Entry<I, false> {
     I idx;
     int info;
 };
+template <>
+struct Entry<int, true> {
+    int idx;
+    int info;
+    uint32_t sc, pad;
+};
+template <>
+struct Entry<long long, true> {
+    long long idx;
+    int info;
+    uint32_t sc;
+};
+template <typename I>
+__device__ __forceinline__ uint32_t entry_sc(const Entry<I, false> &) { return 0u; }
+template <typename I>
+__device__ __forceinline__ uint32_t entry_sc(const Entry<I, true> &e) { return e.sc; }
 
 // two consecutive table entries (the first at an even index) in one 16-byte load
 template <typename E>
@@ -141,43 +167,122 @@ __device__ __forceinline__ void load_pair(const E *t, E &a, E &b) {
     }
 }
 
-// with k > 8, a warp's list insertions for one pixel slot are done cooperatively
-// (the whole warp per candidate) when at most this many of its lanes insert, else
-// by each lane alone
-constexpr int kCoopMax = 3;
+// Insert (cn, cv) into the list of column `col` (slot i at col + i * LS), if it
+// beats the list's last entry.  Lists up to kRankMax long: every slot is loaded
+// at once, the candidate's rank is the number of entries better than it, and the
+// entries below it move down one slot.  Longer lists: a walk up from the last slot.
+template <bool LONG>
+__device__ __forceinline__ void list_insert(float *s_ln, uint16_t *s_lv, int col, int k, int LS, float cn, int cv) {
+    float *ln = s_ln + col;
+    uint16_t *lv = s_lv + col;
+    if constexpr (!LONG) {
+        float en[kRankMax];
+        int ev[kRankMax];
+        int pos = 0;
+#pragma unroll
+        for (int i = 0; i < kRankMax; ++i) {
+            en[i] = -INFINITY;
+            ev[i] = kNoV;
+            if (i < k) {
+                en[i] = ln[i * LS];
+                ev[i] = lv[i * LS];
+            }
+            pos += (i < k && better(en[i], ev[i], cn, cv)) ? 1 : 0;
+        }
+        if (pos < k) {
+#pragma unroll
+            for (int i = kRankMax - 1; i > 0; --i)
+                if (i < k && i > pos) {
+                    ln[i * LS] = en[i - 1];
+                    lv[i * LS] = (uint16_t)ev[i - 1];
+                }
+            ln[pos * LS] = cn;
+            lv[pos * LS] = (uint16_t)cv;
+        }
+    } else {
+        int i = k - 1;
+        if (!better(cn, cv, ln[i * LS], lv[i * LS])) return;
+        while (i > 0) {
+            const float pn = ln[(i - 1) * LS];
+            const int pv = lv[(i - 1) * LS];
+            if (!better(cn, cv, pn, pv)) break;
+            ln[i * LS] = pn;
+            lv[i * LS] = (uint16_t)pv;
+            --i;
+        }
+        ln[i * LS] = cn;
+        lv[i * LS] = (uint16_t)cv;
+    }
+}
+
+// Insert the warp's n pending candidates {nu bits, vidx | (p * 32 + lane) << 16}
+// into their pixels' lists, then reload every lane's register thresholds.  Each
+// round takes 32 entries, one per lane; entries of one pixel are inserted one
+// after the other (match_any groups them), so a list is written by one lane at a
+// time.  A candidate that no longer beats its list's last entry is dropped.  The
+// result does not depend on the order of insertion: a list ends as the k best of
+// everything offered to it under (nu desc, vidx asc).
+template <int PX, bool LONG>
+__device__ __forceinline__ void flush_queue(const uint2 *q, int n, float *s_ln, uint16_t *s_lv, int k, int LS,
+                                            int warp, int lane, float *thn, int *thv) {
+    for (int b = 0; b < n; b += 32) {
+        bool pend = b + lane < n;
+        uint2 e = make_uint2(0u, 0u);
+        if (pend) e = q[b + lane];
+        const float cn = __uint_as_float(e.x);
+        const int cv = (int)(e.y & 0xffffu);
+        const int pc = (int)(e.y >> 16);
+        const int col = (pc >> 5) * THREADS + warp * 32 + (pc & 31);
+        // at most 32 sub-rounds: each inserts at least the lowest pending lane of every group
+        for (;;) {
+            if (!__any_sync(0xffffffffu, pend)) break;
+            const unsigned grp = __match_any_sync(0xffffffffu, pend ? pc : 256 + lane);
+            if (pend && lane == __ffs(grp) - 1) {
+                pend = false;
+                list_insert<LONG>(s_ln, s_lv, col, k, LS, cn, cv);
+            }
+            __syncwarp();
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PX; ++p) {
+        const int c = p * THREADS + warp * 32 + lane;
+        thn[p] = s_ln[c + (k - 1) * LS];
+        thv[p] = s_lv[c + (k - 1) * LS];
+    }
+}
 
 // One CTA tile (rows by * 8 .. +7, columns bx * SPAN .. +SPAN-1) of one search:
 // the body of both the one-search kernel and the persistent batch kernel.
-template <int STORAGE, int P, int C, bool PT, typename I>
+// LONG: lists longer than kRankMax (walk insertion, predicated last load batch).
+template <int STORAGE, int P, int C, bool LONG, typename I>
 __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by, float2 *s_scale, int4 *s_dyn4) {
     typedef Store<STORAGE> St;
     typedef typename St::T T;         // one pixel's (psi, phi)
     typedef Gather<STORAGE> G;
     typedef typename G::LT LT;        // one load
-    typedef Entry<I> E;
+    typedef Entry<I, STORAGE != KB_F32> E;
+    constexpr int TAB = tab_entries<STORAGE>();
     constexpr int PX = P * G::PIX;    // pixels per lane
     constexpr int SPAN = 32 * PX;     // pixels per warp row segment
     constexpr int LS = THREADS * PX;  // list columns (pixels) of the CTA
+    constexpr int QCAP = 32 * (PX + 1);   // < 32 pending after a flush, + one velocity's candidates
 
     // s_scale: per time-ordered epoch.  s_dyn4: table E [TAB] | velocity ids [TAB] |
-    // list nu float [KP * LS] | list vidx u16 [KP * LS].  Column c = p * THREADS +
-    // thread holds one pixel's list, best first; slot i of column c is at c * CS + i * IS.
-    //   k <= 8 (PT false): slot-major, CS = 1, IS = LS, KP = k: each lane walks its
-    //     own lists, consecutive lanes in consecutive banks.
-    //   k > 8 (PT true): column-major with an odd stride, CS = KP = k | 1, IS = 1: a
-    //     pixel's slots are contiguous for the warp-cooperative insertion, and lanes
-    //     walking their own lists still hit distinct banks.
+    // list nu float [k * LS] | list vidx u16 [k * LS] | (8-byte aligned) per-warp
+    // queues uint2 [WARPS][QCAP].
     E *s_tab = reinterpret_cast<E *>(s_dyn4);
     int *s_vid = reinterpret_cast<int *>(s_tab + TAB);
     const int N = a.N, n0 = a.n0, NJ = N - n0, k = a.k;
-    const int KP = PT ? (a.k | 1) : a.k, CS = PT ? KP : 1, IS = PT ? 1 : LS;
     const int NJP = (NJ + 1) & ~1;   // table row stride: even, so entries pair into 16-byte loads
     float *s_ln = reinterpret_cast<float *>(s_vid + TAB);
-    uint16_t *s_lv = reinterpret_cast<uint16_t *>(s_ln + KP * LS);
+    uint16_t *s_lv = reinterpret_cast<uint16_t *>(s_ln + k * LS);
+    uint2 *s_q = reinterpret_cast<uint2 *>(s_dyn4) +
+                 ((TAB * (sizeof(E) + sizeof(int)) + (size_t)k * LS * (sizeof(float) + sizeof(uint16_t)) + 7) / 8);
 
     for (int j = threadIdx.x; j < N; j += THREADS)
         s_scale[j] = (STORAGE == KB_F32) ? make_float2(1.0f, 1.0f) : exp_scale(scale_exp(a.scales[a.epoch_of[j]]));
-    for (int i = threadIdx.x; i < KP * LS; i += THREADS) {
+    for (int i = threadIdx.x; i < k * LS; i += THREADS) {
         s_ln[i] = -INFINITY;
         s_lv[i] = kNoV;
     }
@@ -190,7 +295,15 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     const T *planes = reinterpret_cast<const T *>(a.planes);
     // element index of this lane's first pixel within a plane (even for 16-bit storage)
     const I tb = (I)(a.origin + (long long)y * a.pitch + xw + lane * G::PIX);
-    const LT *zero = reinterpret_cast<const LT *>(g_zero_block) + lane;
+    // per-thread base: an entry's loads start at planes_t + idx; zidx instead lands on
+    // this lane's pixels among the zero columns left of row 0 of plane 0 (kSpan >= the
+    // 128 elements a lane reads there)
+    const T *planes_t = planes + tb;
+    const I zidx = (I)(lane * G::PIX) - tb;
+    const unsigned wbit = 1u << warp;
+    uint2 *q = s_q + warp * QCAP;
+    int qn = 0;                       // pending candidates of this warp (warp-uniform)
+    const unsigned lt_mask = (1u << lane) - 1u;
 
     float thn[PX];
     int thv[PX];
@@ -209,7 +322,7 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
         for (int j = 0; j < n0; ++j) {
             const LT *src = reinterpret_cast<const LT *>(planes + (long long)a.epoch_of[j] * a.plane_elems + tb);
 #pragma unroll
-            for (int p = 0; p < P; ++p) G::acc(acc0 + p * G::PIX, __ldg(src + 32 * p), s_scale[j]);
+            for (int p = 0; p < P; ++p) G::acc(acc0 + p * G::PIX, __ldg(src + 32 * p), sc_of(s_scale[j]));
         }
     }
 
@@ -234,7 +347,8 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             if (STORAGE != KB_F32 && (ox & 1)) g += a.phase1 - 1;   // odd shift: the phase-1 copy
             E e;
             e.idx = (I)g;
-            e.info = mask | ((STORAGE == KB_F32 ? 0 : scale_exp(a.scales[ep])) << 16);
+            e.info = mask;
+            if constexpr (STORAGE != KB_F32) e.sc = sc_of(exp_scale(scale_exp(a.scales[ep])));
             s_tab[vi * NJP + jj] = e;
         }
         __syncthreads();
@@ -245,47 +359,42 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             float2 acc[PX];
 #pragma unroll
             for (int p = 0; p < PX; ++p) acc[p] = acc0[p];
-            if constexpr (!PT) {
+            if constexpr (!LONG) {
                 // epochs in batches of C loads in flight, then one at a time
                 int jj = 0;
                 for (; jj + C <= NJ; jj += C) {
                     LT val[C][P];
-                    int sx[C];
+                    uint32_t sx[C];
 #pragma unroll
-                    for (int q = 0; q < C; q += 2) {
-                        // entries in pairs (one 16-byte shared load) for FP32; the 16-bit
-                        // kernels, held to 48 registers, spill with the pair live and load singly
+                    for (int q2 = 0; q2 < C; q2 += 2) {
                         E t[2];
                         if constexpr (STORAGE == KB_F32) {
-                            load_pair(tab + jj + q, t[0], t[1]);
+                            load_pair(tab + jj + q2, t[0], t[1]);   // one 16-byte shared load
                         } else {
-                            t[0] = tab[jj + q];
-                            t[1] = tab[jj + q + 1];
+                            t[0] = tab[jj + q2];
+                            t[1] = tab[jj + q2 + 1];
                         }
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            sx[q + h] = t[h].info >> 16;
-                            const LT *src = ((t[h].info >> warp) & 1)
-                                                ? reinterpret_cast<const LT *>(planes + (t[h].idx + tb)) : zero;
+                            sx[q2 + h] = entry_sc(t[h]);
+                            const LT *src = reinterpret_cast<const LT *>(planes_t + ((t[h].info & wbit) ? t[h].idx : zidx));
 #pragma unroll
-                            for (int p = 0; p < P; ++p) val[q + h][p] = __ldg(src + 32 * p);
+                            for (int p = 0; p < P; ++p) val[q2 + h][p] = __ldg(src + 32 * p);
                         }
                     }
 #pragma unroll
-                    for (int q = 0; q < C; ++q) {
-                        const float2 sc = exp_scale(sx[q]);
+                    for (int q2 = 0; q2 < C; ++q2) {
 #pragma unroll
-                        for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[q][p], sc);
+                        for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[q2][p], sx[q2]);
                     }
                 }
                 for (; jj < NJ; ++jj) {
                     const E t = tab[jj];
-                    const LT *src =
-                        ((t.info >> warp) & 1) ? reinterpret_cast<const LT *>(planes + (t.idx + tb)) : zero;
+                    const LT *src = reinterpret_cast<const LT *>(planes_t + ((t.info & wbit) ? t.idx : zidx));
                     LT val[P];
 #pragma unroll
                     for (int p = 0; p < P; ++p) val[p] = __ldg(src + 32 * p);
-                    const float2 sc = exp_scale(t.info >> 16);
+                    const uint32_t sc = entry_sc(t);
 #pragma unroll
                     for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[p], sc);
                 }
@@ -294,36 +403,36 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
                 // round trip instead of one per epoch, for more registers
                 for (int jj = 0; jj < NJ; jj += C) {
                     LT val[C][P];
-                    int sx[C];
+                    uint32_t sx[C];
 #pragma unroll
-                    for (int q = 0; q < C; q += 2) {
-                        if (jj + q < NJ) {
+                    for (int q2 = 0; q2 < C; q2 += 2) {
+                        if (jj + q2 < NJ) {
                             E t[2];
-                            load_pair(tab + jj + q, t[0], t[1]);   // the second may be row padding
+                            load_pair(tab + jj + q2, t[0], t[1]);   // the second may be row padding
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
-                                if (jj + q + h < NJ) {
-                                    sx[q + h] = t[h].info >> 16;
-                                    const LT *src = ((t[h].info >> warp) & 1)
-                                                        ? reinterpret_cast<const LT *>(planes + (t[h].idx + tb))
-                                                        : zero;
+                                if (jj + q2 + h < NJ) {
+                                    sx[q2 + h] = entry_sc(t[h]);
+                                    const LT *src = reinterpret_cast<const LT *>(
+                                        planes_t + ((t[h].info & wbit) ? t[h].idx : zidx));
 #pragma unroll
-                                    for (int p = 0; p < P; ++p) val[q + h][p] = __ldg(src + 32 * p);
+                                    for (int p = 0; p < P; ++p) val[q2 + h][p] = __ldg(src + 32 * p);
                                 }
                             }
                         }
                     }
 #pragma unroll
-                    for (int q = 0; q < C; ++q) {
-                        if (jj + q < NJ) {
-                            const float2 sc = exp_scale(sx[q]);
+                    for (int q2 = 0; q2 < C; ++q2) {
+                        if (jj + q2 < NJ) {
 #pragma unroll
-                            for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[q][p], sc);
+                            for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[q2][p], sx[q2]);
                         }
                     }
                 }
             }
-            // scoring: one warp-uniform test gates the (divergent, rarer) list insertions
+            // scoring, then this velocity's candidates appended to the warp's queue; the
+            // lists are updated when 32 or more are pending (the register thresholds stay
+            // conservative meanwhile: a stale threshold only admits more candidates)
             float nu[PX];
             bool cand[PX];
             bool any = false;
@@ -337,83 +446,39 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             if (!__any_sync(0xffffffffu, any)) continue;
 #pragma unroll
             for (int p = 0; p < PX; ++p) {
-                unsigned m = 0;
-                if constexpr (PT) {
-                    m = __ballot_sync(0xffffffffu, cand[p]);
-                    if (m == 0) continue;
-                }
-                if (!PT || __popc(m) > kCoopMax) {
-                    // each lane inserts into its own list, walking up from the last slot
-                    if (cand[p]) {
-                        float *ln = s_ln + (p * THREADS + threadIdx.x) * CS;
-                        uint16_t *lv = s_lv + (p * THREADS + threadIdx.x) * CS;
-                        int i = k - 1;
-                        while (i > 0) {
-                            const float pn = ln[(i - 1) * IS];
-                            const int pv = lv[(i - 1) * IS];
-                            if (!better(nu[p], v, pn, pv)) break;
-                            ln[i * IS] = pn;
-                            lv[i * IS] = (uint16_t)pv;
-                            --i;
-                        }
-                        ln[i * IS] = nu[p];
-                        lv[i * IS] = (uint16_t)v;
-                        thn[p] = ln[(k - 1) * IS];
-                        thv[p] = lv[(k - 1) * IS];
-                    }
-                } else {
-                    // few lanes: the warp inserts their candidates one at a time, lane j
-                    // holding slot j of the list (one load, one ballot, one store)
-                    do {
-                        const int src = __ffs(m) - 1;
-                        m &= m - 1;
-                        const float nn = __shfl_sync(0xffffffffu, nu[p], src);
-                        const int col = p * THREADS + warp * 32 + src;
-                        float *ln = s_ln + col * KP;
-                        uint16_t *lv = s_lv + col * KP;
-                        float en = -INFINITY;
-                        int ev = kNoV;
-                        if (lane < k) {
-                            en = ln[lane];
-                            ev = lv[lane];
-                        }
-                        // first slot the candidate beats (exists: it beats the last slot)
-                        const unsigned bm = __ballot_sync(0xffffffffu, lane < k && better(nn, v, en, ev));
-                        const int pos = __ffs(bm) - 1;
-                        const float upn = __shfl_up_sync(0xffffffffu, en, 1);
-                        const int upv = __shfl_up_sync(0xffffffffu, ev, 1);
-                        const float wn = lane == pos ? nn : (lane > pos ? upn : en);
-                        const int wv = lane == pos ? v : (lane > pos ? upv : ev);
-                        if (lane >= pos && lane < k) {
-                            ln[lane] = wn;
-                            lv[lane] = (uint16_t)wv;
-                        }
-                        const float tn = __shfl_sync(0xffffffffu, wn, k - 1);
-                        const int tv = __shfl_sync(0xffffffffu, wv, k - 1);
-                        if (lane == src) {
-                            thn[p] = tn;
-                            thv[p] = tv;
-                        }
-                    } while (m);
-                }
-                if constexpr (PT) __syncwarp();   // lists written above are read by other lanes later
+                const unsigned m = __ballot_sync(0xffffffffu, cand[p]);
+                if (cand[p])
+                    q[qn + __popc(m & lt_mask)] =
+                        make_uint2(__float_as_uint(nu[p]), (unsigned)v | ((unsigned)(p * 32 + lane) << 16));
+                qn += __popc(m);
+            }
+            if (qn >= 32) {
+                __syncwarp();
+                flush_queue<PX, LONG>(q, qn, s_ln, s_lv, k, LS, warp, lane, thn, thv);
+                qn = 0;
             }
         }
     }
     if (!active) return;
+    if (qn > 0) {
+        __syncwarp();
+        flush_queue<PX, LONG>(q, qn, s_ln, s_lv, k, LS, warp, lane, thn, thv);
+    }
+    __syncwarp();
 
     // epilogue: recompute Psi, Phi (same operation sequence) and nobs of the kept entries;
-    // every off-image epoch added a zero in the main loop, so it adds a zero here too
+    // every off-image epoch added a zero in the main loop, so it adds a zero here too.
+    // Four epochs at a time: their offsets, then their gathers, then the sums in order.
 #pragma unroll
     for (int p = 0; p < PX; ++p) {
         const int x = xw + (G::PIX == 1 ? lane + 32 * p : 2 * lane + 64 * (p / 2) + (p & 1));
         if (x >= a.W) continue;
         Rec *out = a.out + ((long long)y * a.W + x) * k;
-        const float *ln = s_ln + (p * THREADS + threadIdx.x) * CS;
-        const uint16_t *lv = s_lv + (p * THREADS + threadIdx.x) * CS;
+        const float *ln = s_ln + p * THREADS + threadIdx.x;
+        const uint16_t *lv = s_lv + p * THREADS + threadIdx.x;
         for (int i = 0; i < k; ++i) {
             Rec r;
-            const int v = lv[i * IS];
+            const int v = lv[i * LS];
             if (v == kNoV) {
                 r.psi = 0.0f;
                 r.phi = 0.0f;
@@ -423,7 +488,24 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
                 const int2 *ov = a.offs + (long long)v * N;
                 float2 acc = acc0[p];
                 int nobs = n0;
-                for (int j = n0; j < N; ++j) {
+                int j = n0;
+                for (; j + 4 <= N; j += 4) {
+                    T val[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int2 o = __ldg(ov + j + u);
+                        const int xx = x + o.x, yy = y + o.y;
+                        val[u] = St::zero();
+                        if ((unsigned)xx < (unsigned)a.W && (unsigned)yy < (unsigned)a.H) {
+                            val[u] = St::load(planes + (long long)a.epoch_of[j + u] * a.plane_elems + a.origin +
+                                              (long long)yy * a.pitch + xx);
+                            ++nobs;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc = St::acc(acc, val[u], s_scale[j + u]);
+                }
+                for (; j < N; ++j) {
                     const int2 o = __ldg(ov + j);
                     const int xx = x + o.x, yy = y + o.y;
                     T val = St::zero();
@@ -436,7 +518,7 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
                 }
                 r.psi = acc.x;
                 r.phi = acc.y;
-                r.nu = ln[i * IS];
+                r.nu = ln[i * LS];
                 r.meta = (uint32_t)v | ((uint32_t)nobs << 16);
             }
             reinterpret_cast<uint4 *>(out)[i] = *reinterpret_cast<uint4 *>(&r);
@@ -444,22 +526,22 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     }
 }
 
-// Resident CTAs per SM the register allocation is held to (0: no hold).  The
-// shapes with one 8-byte load per lane and epoch, with the plain remainder loop
-// (used for k <= 8, where registers decide how many CTAs an SM holds): the
-// 16-bit one is held to 5 (48 registers), which measured faster than 4 despite
-// the L1 the fifth CTA displaces; the FP32 one reaches 48 registers by itself
-// and spills when held to it.  With the predicated remainder (k > 8, where the
-// lists' shared memory limits the SM to 2-3 CTAs): 3 (85 registers).  The wider
-// shapes: 2.  The batch kernel, which keeps its search's arguments in shared
-// memory rather than the parameter bank and so needs more registers, is held to
-// 3 for the narrow shapes and 2 for the wide ones.
-template <int STORAGE, int P, bool PT>
+// Resident CTAs per SM the register allocation is held to (0: no hold), by
+// shape.  Lists up to 8 long (plain remainder loop): the narrow shapes (FP32 with
+// two pixels per lane, 16-bit with one pixel pair) are held to 5 CTAs (48
+// registers; shared memory allows 5 at k = 8); 16-bit with two pixel pairs per
+// lane to 3 with 4-epoch batches (80 registers; the k = 8 lists of its 1024-pixel
+// CTAs allow 3) and 2 with 8-epoch batches.  Longer lists (predicated remainder,
+// shared memory for 2-3 CTAs): 3.  The wide FP32 shapes: 2.  The batch kernel,
+// which keeps its search's arguments in shared memory rather than the parameter
+// bank and so needs more registers, is held to 3 for the narrow shapes and 2 for
+// the others.
+template <int STORAGE, int P, int C, bool LONG>
 constexpr int min_ctas() {
     constexpr bool narrow = STORAGE == KB_F32 ? P <= 2 : P <= 1;
+    if (STORAGE != KB_F32 && P == 2) return (C <= 4 && !LONG) ? 3 : 2;
     if (!narrow) return 2;
-    if (PT) return 3;
-    return STORAGE == KB_F32 ? 0 : 5;
+    return LONG ? 3 : 5;
 }
 
 template <int STORAGE, int P>
@@ -467,8 +549,8 @@ constexpr int min_ctas_batch() {
     return (STORAGE == KB_F32 ? P <= 2 : P <= 1) ? 3 : 2;
 }
 
-template <int STORAGE, int P, int C, bool PT, typename I>
-__global__ void __launch_bounds__(THREADS, min_ctas<STORAGE, P, PT>()) search_kernel(SearchArgs a) {
+template <int STORAGE, int P, int C, bool LONG, typename I>
+__global__ void __launch_bounds__(THREADS, min_ctas<STORAGE, P, C, LONG>()) search_kernel(SearchArgs a) {
     __shared__ float2 s_scale[KB_MAX_EPOCHS];
     extern __shared__ int4 s_dyn4[];
     int bx = blockIdx.x, by = blockIdx.y;
@@ -481,16 +563,16 @@ __global__ void __launch_bounds__(THREADS, min_ctas<STORAGE, P, PT>()) search_ke
         by = r / w;
         bx = s * a.swz + (r - by * w);
     }
-    search_tile<STORAGE, P, C, PT, I>(a, bx, a.by0 + by, s_scale, s_dyn4);
+    search_tile<STORAGE, P, C, LONG, I>(a, bx, a.by0 + by, s_scale, s_dyn4);
 }
 
 // Persistent batch search: CTAs take (job, tile) work items from an atomic
 // counter until the list is exhausted, copying the item's job descriptor into
 // shared memory first.  The item list is ordered by cost (largest first), so
 // uneven stacks, grids and epoch counts balance across the SMs.
-template <int STORAGE, int P, int C, bool PT, typename I>
-__global__ void __launch_bounds__(THREADS, min_ctas_batch<STORAGE, P>()) search_batch_kernel(const SearchArgs *jobs, const int4 *items, int n_items,
-                                                             int *counter) {
+template <int STORAGE, int P, int C, bool LONG, typename I>
+__global__ void __launch_bounds__(THREADS, min_ctas_batch<STORAGE, P>())
+    search_batch_kernel(const SearchArgs *jobs, const int4 *items, int n_items, int *counter) {
     __shared__ float2 s_scale[KB_MAX_EPOCHS];
     __shared__ SearchArgs s_job;
     __shared__ int s_it;
@@ -504,89 +586,85 @@ __global__ void __launch_bounds__(THREADS, min_ctas_batch<STORAGE, P>()) search_
         for (int i = threadIdx.x; i < (int)(sizeof(SearchArgs) / sizeof(int)); i += THREADS)
             reinterpret_cast<int *>(&s_job)[i] = reinterpret_cast<const int *>(jobs + w.x)[i];
         __syncthreads();
-        search_tile<STORAGE, P, C, PT, I>(s_job, w.y, w.z, s_scale, s_dyn4);
+        search_tile<STORAGE, P, C, LONG, I>(s_job, w.y, w.z, s_scale, s_dyn4);
         __syncthreads();
     }
 }
 
-template <int STORAGE, int P, int C, bool PT, typename I>
-cudaError_t launch_pt(const SearchArgs &a, cudaStream_t st, int sm_count) {
-    constexpr int SPAN = 32 * P * Gather<STORAGE>::PIX;
-    static_assert(SPAN <= kSpan, "warp span wider than the zero columns");
-    auto kern = search_kernel<STORAGE, P, C, PT, I>;
-    dim3 grid((a.W + SPAN - 1) / SPAN, a.nby > 0 ? a.nby : (a.H + WARPS - 1) / WARPS);
-    size_t smem = (size_t)TAB * (sizeof(Entry<I>) + sizeof(int)) +
-                  (size_t)(PT ? (a.k | 1) : a.k) * THREADS * P * Gather<STORAGE>::PIX * (sizeof(float) + sizeof(uint16_t));
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    // Shared-memory carveout: it trades resident CTAs against the L1 that the early
-    // epochs' gathers reuse across velocities.  Automatic: the driver's choice up to
-    // k = 8; longer lists take 58 % (measured on the 12 x 4096^2 workload: k = 12
-    // runs 1.25x faster than with the driver's choice).
-    int carve = a.carveout;
-    if (carve < 0 && a.k > 8) carve = 58;
-    if (err == cudaSuccess && carve >= 0)
-        err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
-    if (err != cudaSuccess) return err;
-    int per_sm = 0;
-    if (a.waves > 0) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
-    if (err != cudaSuccess) return err;
-    // bands of `waves` resident waves of CTAs, one launch each (see kb_set_search_waves)
-    const int band = per_sm > 0 ? max(1, (int)((long long)a.waves * per_sm * sm_count / grid.x)) : (int)grid.y;
-    const int by_end = a.by0 + (int)grid.y;
-    for (int b0 = a.by0; b0 < by_end; b0 += band) {
-        SearchArgs ab = a;
-        ab.by0 = b0;
-        ab.nby = min(band, by_end - b0);
-        kern<<<dim3(grid.x, ab.nby), THREADS, smem, st>>>(ab);
-        err = cudaGetLastError();
-        if (err != cudaSuccess) return err;
-    }
-    return cudaSuccess;
+// dynamic shared memory of a CTA with lists of k entries: the table, the lists and the queues
+template <int STORAGE, int P, typename I>
+size_t tile_smem(int k) {
+    constexpr int PX = P * Gather<STORAGE>::PIX;
+    const size_t base = (size_t)tab_entries<STORAGE>() * (sizeof(Entry<I, STORAGE != KB_F32>) + sizeof(int)) +
+                        (size_t)k * THREADS * PX * (sizeof(float) + sizeof(uint16_t));
+    return (base + 7) / 8 * 8 + (size_t)WARPS * 32 * (PX + 1) * sizeof(uint2);
 }
 
-// lists longer than 8 take the predicated-remainder form (see min_ctas)
+template <int STORAGE, int P, int C, bool LONG, typename I>
+cudaError_t launch_pt(const SearchArgs &a, cudaStream_t st) {
+    constexpr int SPAN = 32 * P * Gather<STORAGE>::PIX;
+    static_assert(SPAN <= kSpan, "warp span wider than the zero columns");
+    auto kern = search_kernel<STORAGE, P, C, LONG, I>;
+    dim3 grid((a.W + SPAN - 1) / SPAN, a.nby > 0 ? a.nby : (a.H + WARPS - 1) / WARPS);
+    const size_t smem = tile_smem<STORAGE, P, I>(a.k);
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // Shared-memory carveout: the driver's choice unless the caller sets one
+    // (kb_set_search_carveout); it trades resident CTAs against the L1 that the
+    // early epochs' gathers reuse across velocities.
+    if (err == cudaSuccess && a.carveout >= 0)
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, a.carveout);
+    if (err != cudaSuccess) return err;
+    kern<<<grid, THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// lists longer than kRankMax take the walking insertion and the predicated remainder
 template <int STORAGE, int P, int C, typename I>
-cudaError_t launch_one(const SearchArgs &a, cudaStream_t st, int sm_count) {
-    if (a.k > 8) return launch_pt<STORAGE, P, C, true, I>(a, st, sm_count);
-    return launch_pt<STORAGE, P, C, false, I>(a, st, sm_count);
+cudaError_t launch_one(const SearchArgs &a, cudaStream_t st) {
+    if (a.k > kRankMax) return launch_pt<STORAGE, P, C, true, I>(a, st);
+    return launch_pt<STORAGE, P, C, false, I>(a, st);
 }
 
 template <int STORAGE, int P, int C>
-cudaError_t launch_idx(const SearchArgs &a, cudaStream_t st, int sm_count) {
+cudaError_t launch_idx(const SearchArgs &a, cudaStream_t st) {
     // 32-bit element offsets when every plane of both phases fits
     const long long span = (STORAGE == KB_F32 ? 1LL : 2LL) * a.N * a.plane_elems;
-    if (span < (1LL << 31) - 1) return launch_one<STORAGE, P, C, int>(a, st, sm_count);
-    return launch_one<STORAGE, P, C, long long>(a, st, sm_count);
+    if (span < (1LL << 31) - 1) return launch_one<STORAGE, P, C, int>(a, st);
+    return launch_one<STORAGE, P, C, long long>(a, st);
 }
 
 // Shapes: (loads per lane P, epochs per load batch C); a 16-bit load is two pixels.
+// Defaults (variant 0), measured on the 12 x 4096^2 stack at k = 8: FP32 (2, 8)
+// 88 ms against 89 for (2, 4); 16-bit (2, 4): BF16 80 ms against 91 for (1, 4),
+// 96 for (2, 8) and 112 for (1, 8).
 template <int STORAGE>
-cudaError_t launch_storage(const SearchArgs &a, cudaStream_t st, int sm_count) {
+cudaError_t launch_storage(const SearchArgs &a, cudaStream_t st) {
     if constexpr (STORAGE == KB_F32) {
         switch (a.variant) {
-            case 1: return launch_idx<STORAGE, 4, 4>(a, st, sm_count);
-            case 2: return launch_idx<STORAGE, 2, 4>(a, st, sm_count);
-            case 3: return launch_idx<STORAGE, 4, 8>(a, st, sm_count);
-            default: return launch_idx<STORAGE, 2, 8>(a, st, sm_count);
+            case 1: return launch_idx<STORAGE, 4, 4>(a, st);
+            case 2: return launch_idx<STORAGE, 2, 4>(a, st);
+            case 3: return launch_idx<STORAGE, 4, 8>(a, st);
+            default: return launch_idx<STORAGE, 2, 8>(a, st);
         }
     } else {
         switch (a.variant) {
-            case 1: return launch_idx<STORAGE, 2, 4>(a, st, sm_count);
-            case 2: return launch_idx<STORAGE, 1, 4>(a, st, sm_count);
-            case 3: return launch_idx<STORAGE, 2, 8>(a, st, sm_count);
-            default: return launch_idx<STORAGE, 1, 8>(a, st, sm_count);
+            case 2: return launch_idx<STORAGE, 1, 4>(a, st);
+            case 3: return launch_idx<STORAGE, 2, 8>(a, st);
+            case 4: return launch_idx<STORAGE, 1, 8>(a, st);
+            case 1: return launch_idx<STORAGE, 2, 4>(a, st);
+            // automatic: lists longer than kRankMax take the one-pair shape, whose 512-pixel
+            // CTAs keep their lists' shared memory within what 3 CTAs per SM can hold
+            default: return a.k > kRankMax ? launch_idx<STORAGE, 1, 4>(a, st) : launch_idx<STORAGE, 2, 4>(a, st);
         }
     }
 }
 
-template <int STORAGE, int P, int C, bool PT, typename I>
+template <int STORAGE, int P, int C, bool LONG, typename I>
 cudaError_t launch_batch_pt(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int kmax,
                             int carve, int sm_count, cudaStream_t st) {
-    size_t smem = (size_t)TAB * (sizeof(Entry<I>) + sizeof(int)) +
-                  (size_t)(PT ? (kmax | 1) : kmax) * THREADS * P * Gather<STORAGE>::PIX * (sizeof(float) + sizeof(uint16_t));
-    auto kern = search_batch_kernel<STORAGE, P, C, PT, I>;
+    const size_t smem = tile_smem<STORAGE, P, I>(kmax);
+    auto kern = search_batch_kernel<STORAGE, P, C, LONG, I>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (carve < 0 && kmax > 8) carve = 58;   // the rule of the one-search launch
     if (err == cudaSuccess && carve >= 0)
         err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
     int per_sm = 0;
@@ -601,7 +679,8 @@ cudaError_t launch_batch_pt(const SearchArgs *jobs, const int4 *items, int n_ite
 template <int STORAGE, int P, int C, typename I>
 cudaError_t launch_batch_one(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int kmax,
                              int carve, int sm_count, cudaStream_t st) {
-    if (kmax > 8) return launch_batch_pt<STORAGE, P, C, true, I>(jobs, items, n_items, counter, kmax, carve, sm_count, st);
+    if (kmax > kRankMax)
+        return launch_batch_pt<STORAGE, P, C, true, I>(jobs, items, n_items, counter, kmax, carve, sm_count, st);
     return launch_batch_pt<STORAGE, P, C, false, I>(jobs, items, n_items, counter, kmax, carve, sm_count, st);
 }
 
@@ -625,21 +704,27 @@ cudaError_t launch_batch_storage(const SearchArgs *jobs, const int4 *items, int 
         }
     } else {
         switch (variant) {
-            case 1: return launch_batch_idx<STORAGE, 2, 4>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
             case 2: return launch_batch_idx<STORAGE, 1, 4>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
             case 3: return launch_batch_idx<STORAGE, 2, 8>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
-            default: return launch_batch_idx<STORAGE, 1, 8>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
+            case 4: return launch_batch_idx<STORAGE, 1, 8>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
+            default: return launch_batch_idx<STORAGE, 2, 4>(jobs, items, n_items, counter, kmax, carve, idx64, sm_count, st);
         }
     }
 }
 
 }  // namespace
 
-int search_span(int storage, int variant) {
+int search_span(int storage, int variant, int k) {
     // loads per lane P of the shape, times 32 lanes, times pixels per load
-    static const int p32[5] = {2, 4, 2, 4, 2}, p16[5] = {1, 2, 1, 2, 1};
+    static const int p32[5] = {2, 4, 2, 4, 2}, p16[5] = {2, 2, 1, 2, 1};
     const int v = (variant >= 1 && variant <= 4) ? variant : 0;
+    if (storage != KB_F32 && v == 0 && k > kRankMax) return 64;
     return storage == KB_F32 ? 32 * p32[v] : 64 * p16[v];
+}
+
+int default_variant(int storage, int k) {
+    if (storage == KB_F32) return 4;       // (2, 8)
+    return k > kRankMax ? 2 : 1;           // (1, 4) / (2, 4)
 }
 
 cudaError_t launch_search_batch(const SearchArgs *jobs, const int4 *items, int n_items, int *counter, int storage,
@@ -652,11 +737,11 @@ cudaError_t launch_search_batch(const SearchArgs *jobs, const int4 *items, int n
     }
 }
 
-cudaError_t launch_search(const SearchArgs &a, cudaStream_t st, int sm_count) {
+cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
     switch (a.storage) {
-        case KB_F32: return launch_storage<KB_F32>(a, st, sm_count);
-        case KB_BF16: return launch_storage<KB_BF16>(a, st, sm_count);
-        case KB_F16: return launch_storage<KB_F16>(a, st, sm_count);
+        case KB_F32: return launch_storage<KB_F32>(a, st);
+        case KB_BF16: return launch_storage<KB_BF16>(a, st);
+        case KB_F16: return launch_storage<KB_F16>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }

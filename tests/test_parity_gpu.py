@@ -281,20 +281,6 @@ def test_every_kernel_variant(kb, ctx, variant, storage):
     check_topk(res, ref, nu_of)
 
 
-@pytest.mark.parametrize("k", [4, 12])
-def test_banded_launch_equals_single_launch(kb, ctx, k):
-    """kb_set_search_waves: the search launched in bands of one resident wave of CTAs gives the
-    one-launch records byte for byte (a 12800-row image needs several bands)."""
-    st = synth.small_stack(77, 3, 12800, 64, K=3, n_angles=4, n_speeds=4, s_lo=5.0, s_hi=60.0, k=k)
-    ref = gpu_search(kb, ctx, st, k=k)
-    ctx.set_search_waves(1)
-    try:
-        got = gpu_search(kb, ctx, st, k=k)
-    finally:
-        ctx.set_search_waves(-1)
-    assert got.tobytes() == ref.tobytes()
-
-
 def test_results_async_overlaps_and_orders_reads(kb, ctx):
     """kb_results_async into pinned host memory on a second stream equals kb_results; a search
     enqueued right after the read (same job, other velocities) waits for the read, so the
