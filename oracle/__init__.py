@@ -85,7 +85,7 @@ def _load():
             lib.kbo_sums_one_velocity.argtypes = [P, P, P, i32, i32, i32, P, P, P, P, P]
             lib.kbo_filter_lightcurve.argtypes = [P, P, P, i32, i32, i32, P, P, i32, i32, f64, P, P, P, P, P]
             lib.kbo_stamp.argtypes = [P, P, i32, i32, i32, P, P, i32, i32, i32, i32, P]
-            lib.kbo_moments.argtypes = [P, i32, P, P, P, P, P, P]
+            lib.kbo_moments.argtypes = [P, i32, f64, P, P, P, P, P, P]
             lib.kbo_cluster.argtypes = [P, P, P, P, P, P, ctypes.c_long, f64, f64, f64, i32, P, P, P]
             lib.kbo_snr2_span_max.argtypes = [P, P, i32, i32, i32, i32, P]
             lib.kbo_span_bound.argtypes = [P, i32, i32, i32, i32, P, P, i32, i32]
@@ -233,13 +233,14 @@ def stamp(sci, mask, dx_v, dy_v, x0, y0, r, median=False):
     return out
 
 
-def moments(st):
-    """(m00, mx, my, mu20, mu02, mu11) of a stamp, coordinates relative to its centre."""
+def moments(st, aperture=0.0):
+    """(m00, mx, my, mu20, mu02, mu11) of a stamp over the central aperture x^2 + y^2 <=
+    aperture^2 (the whole stamp when aperture <= 0), coordinates relative to its centre."""
     lib = _load()
     st = _c(st, np.float32)
     r = (st.shape[0] - 1) // 2
     vals = [ctypes.c_double() for _ in range(6)]
-    lib.kbo_moments(_ptr(st), r, *[ctypes.byref(v) for v in vals])
+    lib.kbo_moments(_ptr(st), r, float(aperture), *[ctypes.byref(v) for v in vals])
     return tuple(v.value for v in vals)
 
 

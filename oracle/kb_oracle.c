@@ -502,21 +502,35 @@ void kbo_stamp(const float *sci, const uint8_t *mask, int N, int H, int W, const
 }
 
 /*
- * Central moments of a stamp, pixel values as weights, coordinates relative to
- * the stamp centre: m00 = sum I, centroid (mx, my) = sum (x, y) I / m00, and
- * mu20, mu02, mu11 = sum (x - mx)^2 I, (y - my)^2 I, (x - mx)(y - my) I over m00.
- * All zero when m00 == 0.
+ * Central moments of a stamp over a central aperture, pixel values as weights,
+ * coordinates relative to the stamp centre.  The pixels taken are those with
+ * x^2 + y^2 <= aperture^2 (every pixel of the stamp when aperture <= 0):
+ * m00 = sum I, centroid (mx, my) = sum (x, y) I / m00, and mu20, mu02, mu11 =
+ * sum (x - mx)^2 I, (y - my)^2 I, (x - mx)(y - my) I over m00.  All zero when
+ * m00 == 0.
+ *
+ * Reading of Sec. 3.3 (the paper takes "the central moments of the images" of
+ * the coadded stamps and compares them with those of a Gaussian centred in the
+ * stamp).  Over the whole stamp, the moments of a faint source are dominated by
+ * the sky noise of the surrounding pixels: the noise's contribution to the
+ * second moments grows with the fourth power of the stamp radius.  An aperture
+ * of about two PSF widths keeps the source's light and little noise, so a
+ * source's moments come out near those of its PSF and a stamp of pure noise
+ * (whose m00 is as likely negative as positive) rarely does.
  */
-void kbo_moments(const float *stamp, int r, double *m00, double *mx, double *my, double *mu20, double *mu02,
-                 double *mu11) {
+void kbo_moments(const float *stamp, int r, double aperture, double *m00, double *mx, double *my, double *mu20,
+                 double *mu02, double *mu11) {
     int S = 2 * r + 1;
+    double a2 = aperture * aperture;
     double s = 0.0, sx = 0.0, sy = 0.0;
     for (int j = 0; j < S; ++j)
         for (int i = 0; i < S; ++i) {
+            double x = i - r, y = j - r;
+            if (aperture > 0.0 && x * x + y * y > a2) continue;
             double v = stamp[(size_t)j * S + i];
             s += v;
-            sx += (i - r) * v;
-            sy += (j - r) * v;
+            sx += x * v;
+            sy += y * v;
         }
     *m00 = s;
     *mx = *my = *mu20 = *mu02 = *mu11 = 0.0;
@@ -524,7 +538,9 @@ void kbo_moments(const float *stamp, int r, double *m00, double *mx, double *my,
     double cx = sx / s, cy = sy / s, a = 0.0, b = 0.0, c = 0.0;
     for (int j = 0; j < S; ++j)
         for (int i = 0; i < S; ++i) {
-            double v = stamp[(size_t)j * S + i], x = i - r - cx, y = j - r - cy;
+            double x0 = i - r, y0 = j - r;
+            if (aperture > 0.0 && x0 * x0 + y0 * y0 > a2) continue;
+            double v = stamp[(size_t)j * S + i], x = x0 - cx, y = y0 - cy;
             a += x * x * v;
             b += y * y * v;
             c += x * y * v;

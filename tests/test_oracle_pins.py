@@ -541,6 +541,95 @@ def test_moments_of_hand_stamps():
     assert oracle.moments(np.zeros((5, 5), np.float32)) == (0.0,) * 6
 
 
+def test_moments_over_an_aperture_by_hand():
+    """Unit pixels at (-1, 0) and (1, 0) and 100 at (3, 3).  Aperture 2 leaves the 100 out (it is
+    4.24 px from the centre): the moments of the pair.  Aperture 5 takes it: m00 = 102, centroid
+    (50/17, 50/17) and, worked out by hand with the deviations -67/17, -33/17, 1/17 in x and
+    -50/17, -50/17, 1/17 in y, mu20 = 5678/29478, mu02 = mu11 = 5100/29478."""
+    r = 4
+    s = np.zeros((9, 9), np.float32)
+    s[r, r - 1] = s[r, r + 1] = 1.0
+    s[r + 3, r + 3] = 100.0
+    assert oracle.moments(s, 2.0) == (2.0, 0.0, 0.0, 1.0, 0.0, 0.0)
+    m = oracle.moments(s, 5.0)
+    assert m[0] == 102.0
+    assert m[1] == pytest.approx(50.0 / 17.0, rel=1e-14) and m[2] == pytest.approx(50.0 / 17.0, rel=1e-14)
+    assert m[3] == pytest.approx(5678.0 / 29478.0, rel=1e-12)
+    assert m[4] == pytest.approx(5100.0 / 29478.0, rel=1e-12)
+    assert m[5] == pytest.approx(5100.0 / 29478.0, rel=1e-12)
+    # an aperture at least the stamp's corner distance takes every pixel: aperture 0's moments
+    assert oracle.moments(s, 6.0) == oracle.moments(s, 0.0)
+
+
+def test_moments_of_a_gaussian_in_an_aperture_follow_the_truncated_closed_form():
+    """A centred isotropic Gaussian of width sigma inside a disk of radius R: r^2 / (2 sigma^2)
+    is exponential, so <x^2> = sigma^2 (1 - u e^-u / (1 - e^-u)) with u = R^2 / (2 sigma^2).
+    The sampled Gaussian on the pixel grid (sigma = 4 px) follows it to 3.5 % (the disk of pixel
+    centres is jagged at its edge, more so for small R); centroid and mu11 are zero by symmetry."""
+    sigma, r = 4.0, 12
+    yy, xx = np.mgrid[-r:r + 1, -r:r + 1]
+    g = np.exp(-(xx ** 2 + yy ** 2) / (2 * sigma ** 2)).astype(np.float32)
+    for R in (5.0, 8.0, 11.0):
+        u = R * R / (2 * sigma ** 2)
+        want = sigma ** 2 * (1.0 - u * math.exp(-u) / (1.0 - math.exp(-u)))
+        m00, mx, my, mu20, mu02, mu11 = oracle.moments(g, R)
+        assert abs(mx) < 1e-12 and abs(my) < 1e-12 and abs(mu11) < 1e-12
+        assert mu20 == pytest.approx(want, rel=0.035) and mu02 == pytest.approx(mu20, rel=1e-12)
+
+
+def _c1_like_stamp(rng, source, snr=2.5, r=10):
+    """A mean stamp of 12 DECam-shaped epochs (variance 80-120, PSF FWHM 3.5-4.5 px) along a
+    trajectory, with a source of per-epoch PSF-fit SNR `snr` moving exactly along it, or none.
+    Returns the stamp and the epochs' PSF sigmas."""
+    times = synth.decam_times()
+    N, H, W, K = times.size, 96, 96, 17
+    var_t = rng.uniform(80.0, 120.0, N)
+    sig = rng.uniform(3.5, 4.5, N) / synth.FWHM_PER_SIGMA
+    sci = (rng.standard_normal((N, H, W)) * np.sqrt(var_t)[:, None, None]).astype(np.float32)
+    x0, y0 = rng.uniform(30.0, 34.0), rng.uniform(40.0, 44.0)
+    speed, ang = rng.uniform(4.5, 27.5), rng.uniform(-math.pi / 4, math.pi / 4)
+    vx, vy = speed * math.cos(ang), speed * math.sin(ang)
+    if source:
+        flux = snr * math.sqrt(4.0 * math.pi * float(np.mean(sig ** 2)) * float(np.mean(var_t)))
+        for e in range(N):
+            synth.render_source(sci[e], x0 + vx * times[e], y0 + vy * times[e], flux, sig[e], K // 2)
+    dx, dy = oracle.offsets(times, np.array([vx]), np.array([vy]))
+    st = oracle.stamp(sci, None, dx[0], dy[0], int(math.floor(x0 + 0.5)), int(math.floor(y0 + 0.5)), r)
+    return st, sig
+
+
+def psf_moment_cuts(sig, aperture):
+    """Cuts of a centred PSF seen through the aperture: the truncated second moment of each
+    epoch's Gaussian (closed form above) averaged, plus 1/12 px^2 of pixel rounding; the variances
+    within [0.4, 1.8] of it, |mu11| within half of it, the centroid within 1 px."""
+    u = aperture ** 2 / (2 * sig ** 2)
+    v0 = float(np.mean(sig ** 2 * (1 - u * np.exp(-u) / (1 - np.exp(-u))))) + 1.0 / 12.0
+    return {"max_offset": 1.0, "min_var": 0.4 * v0, "max_var": 1.8 * v0, "max_mu11": 0.5 * v0}
+
+
+def _passes(m, c):
+    m00, mx, my, mu20, mu02, mu11 = m
+    return (m00 > 0 and abs(mx) <= c["max_offset"] and abs(my) <= c["max_offset"] and
+            c["min_var"] <= mu20 <= c["max_var"] and c["min_var"] <= mu02 <= c["max_var"] and
+            abs(mu11) <= c["max_mu11"])
+
+
+def test_aperture_moment_filter_keeps_faint_sources_and_drops_noise():
+    """Sec. 3.3 reading: moments over a 3 px aperture with cuts from the PSF widths.  Seeded
+    DECam-like mean stamps: at least 90 % of sources of per-epoch SNR 2.5 on their trajectory
+    pass, and at most 6 % of pure-noise stamps.  Over the whole 21 x 21 stamp (aperture 0) the
+    same sources pass at most 20 % of the time: the sky noise of the outer pixels dominates."""
+    rng = np.random.default_rng(31)
+    src = [_c1_like_stamp(rng, True) for _ in range(150)]
+    noise = [_c1_like_stamp(rng, False) for _ in range(150)]
+    ok_src = np.mean([_passes(oracle.moments(st, 3.0), psf_moment_cuts(sig, 3.0)) for st, sig in src])
+    ok_noise = np.mean([_passes(oracle.moments(st, 3.0), psf_moment_cuts(sig, 3.0)) for st, sig in noise])
+    ok_whole = np.mean([_passes(oracle.moments(st, 0.0), psf_moment_cuts(sig, 20.0)) for st, sig in src])
+    assert ok_src >= 0.9, ok_src
+    assert ok_noise <= 0.06, ok_noise
+    assert ok_whole <= 0.2, ok_whole
+
+
 def _moving_gaussian_stack(N, H, W, sigma, x0, y0, dx, dy, amp=100.0):
     """A noiseless Gaussian of width sigma centred on the integer trajectory pixels."""
     yy, xx = np.mgrid[0:H, 0:W]
