@@ -59,6 +59,9 @@ extern "C" {
 /* ---- search flags -------------------------------------------------------- */
 #define KB_RESCORE_FP64 1 /* re-rank the kept candidates with FP64 sums of the FP32 planes;
                            * pixels the certificate cannot clear are re-searched in FP64 */
+#define KB_PRUNE 2        /* kb_search with nu_min > 0: skip the gathers of a warp's span of
+                           * start pixels for a velocity when a bound on nu over the span
+                           * cannot reach nu_min (Sec. 5.3); the results are unchanged */
 
 /* ---- limits -------------------------------------------------------------- */
 #define KB_MAX_EPOCHS 128   /* N */
@@ -239,7 +242,16 @@ void kb_job_free(kb_job *j);
  *   nu_min  only trajectories with nu >= nu_min are kept (-inf keeps all valid)
  *   flags   KB_RESCORE_FP64: search the stack's planes keeping extra
  *           candidates, then recompute each candidate's sums in FP64 from the
- *           FP32 planes, re-rank in FP64 and keep the top-k
+ *           FP32 planes, re-rank in FP64 and keep the top-k.
+ *           KB_PRUNE (with nu_min > 0 and the automatic kernel shape): by
+ *           Cauchy-Schwarz, nu^2 <= sum_t max(psi_t, 0)^2 / phi_t over a
+ *           trajectory's in-image epochs; per epoch the largest such term over
+ *           each warp span of the shifted start pixels is precomputed (a stack
+ *           cache of N * H * (W + span - 1) floats, allocated under the budget
+ *           and rebuilt after kb_make_psi_phi), and a velocity whose span bound
+ *           (rounded upwards, with a 2^-14 relative margin) is below nu_min^2 is
+ *           skipped for that span.  The records equal those of the same search
+ *           without the flag, byte for byte.  Ignored otherwise (and by batches).
  * Every start pixel of the earliest epoch is searched.  Epochs whose trajectory
  * pixel is outside the image contribute nothing; trajectories with Phi == 0 are
  * not kept; ranking is by (nu descending, vidx ascending); empty slots have
@@ -349,15 +361,16 @@ int kb_filter_lightcurves(kb_job *job, const kb_stack *s, double nsigma, kb_filt
 /* Central moments of one coadded stamp (coordinates relative to its centre,
  * pixel values as weights) and the result of the Gaussian-similarity cut. */
 typedef struct kb_moments {
-    double m00;            /* sum of the stamp */
+    double m00;            /* sum of the stamp over the aperture */
     double mx, my;         /* centroid */
     double mu20, mu02, mu11; /* central second moments over m00 */
     int32_t passed;        /* 1: passed the cuts (or no cuts given), 0: rejected */
     int32_t reserved;
 } kb_moments;
 
-/* Cuts of the moment filter: a stamp passes when m00 > 0, |mx|, |my| <=
- * max_offset, min_var <= mu20, mu02 <= max_var and |mu11| <= max_mu11. */
+/* Cuts of the moment filter (moments over the aperture): a stamp passes when
+ * m00 > 0, |mx|, |my| <= max_offset, min_var <= mu20, mu02 <= max_var and
+ * |mu11| <= max_mu11.  The caller derives them from the epochs' PSF widths. */
 typedef struct kb_moment_cuts {
     double max_offset, min_var, max_var, max_mu11;
 } kb_moment_cuts;
@@ -369,17 +382,19 @@ typedef struct kb_moment_cuts {
  * the image, finite and not masked, with the search's own trajectory offsets,
  * combined as their mean (KB_STAMP_MEAN, FP64 sum) or median (KB_STAMP_MEDIAN:
  * the middle value, the mean of the two middle ones for an even count); 0 where
- * no epoch contributes.  Then the stamp's central moments and, with `cuts`, the
- * moment filter.
+ * no epoch contributes.  Then the stamp's central moments over the aperture
+ * sx^2 + sy^2 <= aperture^2 (the whole stamp when aperture <= 0; about two PSF
+ * widths keeps a faint source's light and little of the sky noise around it)
+ * and, with `cuts`, the moment filter.
  *   sci, mask  DEVICE [N][H][W] science images (and mask or NULL), the job's N, H, W
  *   x0, y0, vidx  HOST [n] candidates
  *   stamps     DEVICE float [n][2r+1][2r+1]; moments DEVICE [n] or NULL
- * KB_EINVAL (no search yet, shapes, r outside 0..KB_MAX_STAMP_RADIUS, a
- * candidate outside the image or velocity range, pointers).  Stream-ordered;
- * the host arrays are read before the call returns. */
+ * KB_EINVAL (no search yet, shapes, r outside 0..KB_MAX_STAMP_RADIUS, a NaN
+ * aperture, a candidate outside the image or velocity range, pointers).
+ * Stream-ordered; the host arrays are read before the call returns. */
 int kb_stamps(kb_job *job, const float *sci, const uint8_t *mask, int N, int H, int W, const int32_t *x0,
-              const int32_t *y0, const int32_t *vidx, int n, int radius, int mode, const kb_moment_cuts *cuts,
-              float *stamps, kb_moments *moments, void *stream);
+              const int32_t *y0, const int32_t *vidx, int n, int radius, int mode, double aperture,
+              const kb_moment_cuts *cuts, float *stamps, kb_moments *moments, void *stream);
 
 /* ---- de-duplication of candidates (Sec. 3.3) ------------------------------ */
 

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libkb.so")
 KB_OK, KB_EINVAL, KB_ENOMEM, KB_ECUDA, KB_ETIMEOUT, KB_ERANGE = 0, 1, 2, 3, 4, 5
 KB_F32, KB_BF16, KB_F16 = 0, 1, 2
 KB_RESCORE_FP64 = 1
+KB_PRUNE = 2
 KB_BATCH_AUTOTUNE = 1
 STORAGE = {"f32": KB_F32, "bf16": KB_BF16, "f16": KB_F16}
 
@@ -85,7 +86,8 @@ _kb_make_psi_phi_static = _sig("kb_make_psi_phi_static", _i32,
 _kb_estimate_bytes = _sig("kb_estimate_bytes", _i32, [_i32, _i32, _i32, _i32, _i32, _i32, _i32, _i32,
                                                        ctypes.POINTER(_sz), ctypes.POINTER(_sz)])
 _kb_filter_lightcurves = _sig("kb_filter_lightcurves", _i32, [_P, _P, ctypes.c_double, _P, _sz, ctypes.POINTER(_sz), _P])
-_kb_stamps = _sig("kb_stamps", _i32, [_P, _P, _P, _i32, _i32, _i32, _P, _P, _P, _i32, _i32, _i32, _P, _P, _P,
+_kb_stamps = _sig("kb_stamps", _i32, [_P, _P, _P, _i32, _i32, _i32, _P, _P, _P, _i32, _i32, _i32, ctypes.c_double,
+                                      _P, _P, _P,
                                       _P])
 _kb_results_async = _sig("kb_results_async", _i32, [_P, _P, _sz, ctypes.POINTER(_sz), _P])
 _kb_results_compact_async = _sig("kb_results_compact_async", _i32, [_P, _P, _sz, ctypes.POINTER(_sz), _P])
@@ -407,10 +409,12 @@ class Job:
             return dev.cpu().numpy().view(FILTERED_DTYPE).reshape(self.H, self.W, self.k or self.topk)
         return out
 
-    def stamps(self, sci, mask, x0, y0, vidx, radius, median=False, cuts=None, moments=True, stream=None):
+    def stamps(self, sci, mask, x0, y0, vidx, radius, median=False, cuts=None, moments=True, stream=None,
+               aperture=0.0):
         """Sec. 3.3 coadded stamps of candidates (x0, y0, vidx) of the last search from the device
         science images sci [N][H][W] (float32) and mask (uint8 or None).  Returns the device
-        stamps [n][2r+1][2r+1] (float32) and, with moments, a MOMENTS_DTYPE numpy array [n].
+        stamps [n][2r+1][2r+1] (float32) and, with moments, a MOMENTS_DTYPE numpy array [n] of the
+        moments over the central aperture (radius `aperture` px; <= 0: the whole stamp).
         cuts: None or a MomentCuts (or a dict of its fields)."""
         import torch
         x0 = np.ascontiguousarray(x0, np.int32)
@@ -431,7 +435,7 @@ class Job:
         if isinstance(cuts, dict):
             cuts = MomentCuts(**cuts)
         self.ctx.check(_kb_stamps(self.h, _ptr(sci), _ptr(mask), N, H, W, _ptr(x0), _ptr(y0), _ptr(vidx), n,
-                                  int(radius), KB_STAMP_MEDIAN if median else KB_STAMP_MEAN,
+                                  int(radius), KB_STAMP_MEDIAN if median else KB_STAMP_MEAN, float(aperture),
                                   None if cuts is None else ctypes.byref(cuts), _ptr(st), _ptr(mo), _stream(stream)))
         if mo is None:
             return st, None

@@ -3,11 +3,22 @@
 //
 // Rescoring: the reduced-precision search keeps kc >= k candidates per start
 // pixel.  For each candidate the coadd of Sec. 2.1.5 is recomputed from the
-// FP32 psi/phi planes with FP64 accumulation (epochs in time order), scored
-// nu = Psi / sqrt(Phi), alpha = Psi / Phi in FP64, and the k best by
-// (nu desc, vidx asc) are kept.  A per-pixel certificate decides whether a
-// trajectory outside the candidate list could still belong to the top-k; the
-// pixels it cannot clear are searched again exhaustively in FP64.
+// FP32 psi/phi planes, scored nu = Psi / sqrt(Phi), alpha = Psi / Phi in FP64,
+// and the k best by (nu desc, vidx asc) are kept.  A per-pixel certificate
+// decides whether a trajectory outside the candidate list could still belong to
+// the top-k; the pixels it cannot clear are searched again exhaustively.
+//
+// The coadds are summed exactly, in 64-bit fixed point on the integer pipe, and
+// rounded once to FP64: this GPU's FP64 pipe is a small fraction of its FP32
+// and integer pipes, and an FP64 sum of FP32 values spends two FP64 operations
+// (a conversion and an add) per value.  Each plane type (psi, phi) of a stack
+// gets one binary point 2^L with L = E - 56, where every |value| of the stack is
+// below 2^E (from the per-epoch maxima the psi/phi kernel records): a value is
+// taken as round(value * 2^-L), exact for every value of magnitude 2^(E-33) or
+// more (its last mantissa bit is at least 2^L) and within 2^(L-1) below that, and
+// a sum of up to 128 such integers stays below 2^63.  The error of a coadd is
+// therefore at most N * 2^(E-57), below the N * 2^-53 * 2^(E+7) bound of FP64
+// summation, and it does not depend on the order of the epochs.
 #include <cuda_runtime.h>
 #include <limits.h>
 #include <math.h>
@@ -18,14 +29,47 @@ namespace kb {
 
 namespace {
 
-// FP64 coadd of one trajectory from the FP32 planes, epochs in time order.  Four
-// epochs at a time: their offsets, then their four plane gathers, then the sums,
-// so that the scattered loads overlap instead of forming one dependent chain.
-__device__ __forceinline__ void traj64(const RescoreArgs &a, int x, int y, int v, double &P, double &F, int &nobs) {
+// Binary points of the exact coadd sums (see above): the float factors that
+// take a value to units of 2^L (2^-L, exact) and the double factors back (2^L).
+struct FixedPoint {
+    float to_p, to_f;
+    double from_p, from_f;
+};
+
+// one plane type: every |value| < 2^E, E from the largest per-epoch maximum (bits of
+// a non-negative float order like the float); E kept in [-60, 100] so that 2^-L and
+// 2^L stay normal floats and doubles
+__device__ __forceinline__ void fixed_point_of(unsigned maxbits, float &to, double &from) {
+    int E = maxbits == 0u ? -60 : (int)((maxbits >> 23) & 0xff) - 126;   // floor(log2 m) + 1
+    E = max(-60, min(100, E));
+    const int L = E - 56;
+    to = __int_as_float((127 - L) << 23);
+    from = __longlong_as_double((long long)(1023 + L) << 52);
+}
+
+// The binary points of a stack, from its 2N per-epoch maxima [max |psi|, max phi]
+// (every thread of the block calls it; uses one barrier)
+__device__ __forceinline__ FixedPoint stack_fixed_point(const RescoreArgs &a) {
+    __shared__ unsigned s_m[2];
+    if (threadIdx.x < 2) s_m[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * a.N; i += blockDim.x) atomicMax(&s_m[i & 1], a.maxbits[i]);
+    __syncthreads();
+    FixedPoint fp;
+    fixed_point_of(s_m[0], fp.to_p, fp.from_p);
+    fixed_point_of(s_m[1], fp.to_f, fp.from_f);
+    return fp;
+}
+
+// Exact coadd of one trajectory from the FP32 planes (fixed point, see above),
+// rounded once to FP64.  Four epochs at a time: their offsets, then their four
+// plane gathers, then the sums, so that the scattered loads overlap instead of
+// forming one dependent chain.
+__device__ __forceinline__ void traj_exact(const RescoreArgs &a, const FixedPoint &fp, int x, int y, int v, double &P,
+                                           double &F, int &nobs) {
     const int2 *ov = a.offs + (long long)v * a.N;
     const float2 *base = a.f32 + a.origin;
-    P = 0.0;
-    F = 0.0;
+    long long p = 0, f = 0;
     nobs = 0;
     int j = 0;
     for (; j + 4 <= a.N; j += 4) {
@@ -42,23 +86,24 @@ __device__ __forceinline__ void traj64(const RescoreArgs &a, int x, int y, int v
                           : make_float2(0.0f, 0.0f);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (in[q]) {
-                P += (double)pp[q].x;
-                F += (double)pp[q].y;
-                ++nobs;
-            }
+        for (int q = 0; q < 4; ++q) {
+            p += __float2ll_rn(pp[q].x * fp.to_p);
+            f += __float2ll_rn(pp[q].y * fp.to_f);
+            nobs += in[q] ? 1 : 0;
+        }
     }
     for (; j < a.N; ++j) {
         const int2 o = __ldg(ov + j);
         const int xx = x + o.x, yy = y + o.y;
         if ((unsigned)xx < (unsigned)a.W && (unsigned)yy < (unsigned)a.H) {
             const float2 pp = __ldg(base + (long long)a.epoch_of[j] * a.plane_elems + (long long)yy * a.pitch + xx);
-            P += (double)pp.x;
-            F += (double)pp.y;
+            p += __float2ll_rn(pp.x * fp.to_p);
+            f += __float2ll_rn(pp.y * fp.to_f);
             ++nobs;
         }
     }
+    P = (double)p * fp.from_p;
+    F = (double)f * fp.from_f;
 }
 
 // (nu desc, vidx asc)
@@ -96,6 +141,7 @@ __device__ __forceinline__ bool betterk(unsigned long long ak, int av, unsigned 
 // The running top-K list lives in registers (K >= k, a compile-time bound).
 template <int K>
 __global__ void rescore_kernel(RescoreArgs a) {
+    const FixedPoint fp = stack_fixed_point(a);
     const long long npix = (long long)a.H * a.W;
     for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix;
          pix += (long long)gridDim.x * blockDim.x) {
@@ -123,7 +169,7 @@ __global__ void rescore_kernel(RescoreArgs a) {
             nu16_last = rc.nu;
             double P, F;
             int nobs;
-            traj64(a, x, y, (int)v, P, F, nobs);
+            traj_exact(a, fp, x, y, (int)v, P, F, nobs);
             if (!(F > 0.0)) continue;
             const double nu = nu64(P, F);
             emax = fmax(emax, fabs(nu - (double)rc.nu));
@@ -191,6 +237,7 @@ __global__ void rescore_kernel(RescoreArgs a) {
 // planes (lanes take velocities lane, lane + 32, ...), a sorted top-k per lane,
 // then k rounds of a warp-shuffle arg-max merge (nu desc, vidx asc).
 __global__ void repair_kernel(RescoreArgs a) {
+    const FixedPoint fp = stack_fixed_point(a);
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -204,7 +251,7 @@ __global__ void repair_kernel(RescoreArgs a) {
         for (int v = lane; v < a.V; v += 32) {
             double P, F;
             int nobs;
-            traj64(a, x, y, v, P, F, nobs);
+            traj_exact(a, fp, x, y, v, P, F, nobs);
             if (!(F > 0.0)) continue;
             const double nu = nu64(P, F);
             if (!(nu >= a.nu_min)) continue;
@@ -458,8 +505,10 @@ __global__ void stamp_kernel(StampArgs a) {
         }
         if (!a.moments) continue;
         // moments: sums of v, x v, y v, then (after the centroid) the central ones
+        // over the central aperture x^2 + y^2 <= aperture^2 (the whole stamp when aperture <= 0)
         const double x = t < npx ? (double)(t % S - a.r) : 0.0, y = t < npx ? (double)(t / S - a.r) : 0.0;
-        const double v = t < npx ? (double)val : 0.0;
+        const bool in_ap = t < npx && (a.aperture <= 0.0 || x * x + y * y <= a.aperture * a.aperture);
+        const double v = in_ap ? (double)val : 0.0;
         double s[6] = {v, x * v, y * v, 0.0, 0.0, 0.0};
         const int lane = t & 31, w = t >> 5, nw = (blockDim.x + 31) >> 5;
         for (int pass = 0; pass < 2; ++pass) {

@@ -75,11 +75,17 @@ def _candidates(st, res, rng, n_kept=60, n_best=0):
     return np.array(x0, np.int32), np.array(y0, np.int32), np.array(vi, np.int32)
 
 
-def _check(kb, job, st, x0, y0, vi, r, median, cuts=None):
+def _aperture_mask(r, aperture):
+    yy, xx = np.mgrid[-r:r + 1, -r:r + 1]
+    return np.ones((2 * r + 1, 2 * r + 1), bool) if aperture <= 0 else (xx * xx + yy * yy <= aperture * aperture)
+
+
+def _check(kb, job, st, x0, y0, vi, r, median, cuts=None, aperture=0.0):
     N, H, W = st.sci.shape
     sci = torch.from_numpy(st.sci).to(DEV)
     mask = torch.from_numpy(st.mask).to(DEV)
-    stamps, mom = job.stamps(sci, mask, x0, y0, vi, r, median=median, cuts=cuts)
+    stamps, mom = job.stamps(sci, mask, x0, y0, vi, r, median=median, cuts=cuts, aperture=aperture)
+    inside = _aperture_mask(r, aperture)
     stamps = stamps.cpu().numpy()
     dx, dy = oracle.offsets(st.times, st.vx, st.vy)
     n_skipped = 0
@@ -90,8 +96,8 @@ def _check(kb, job, st, x0, y0, vi, r, median, cuts=None):
             assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), i
         else:
             assert np.allclose(got, want, rtol=2.0 ** -23, atol=0.0), (i, np.abs(got - want).max())
-        m = oracle.moments(got)
-        absum = float(np.abs(got.astype(np.float64)).sum())
+        m = oracle.moments(got, aperture)
+        absum = float(np.abs(got.astype(np.float64))[inside].sum())
         assert abs(mom["m00"][i] - m[0]) <= 1e-12 * absum, (i, mom["m00"][i], m[0])
         cond = absum / abs(m[0]) if m[0] != 0 else math.inf
         if cond > 1e6:
@@ -119,11 +125,12 @@ def _check(kb, job, st, x0, y0, vi, r, median, cuts=None):
 
 @pytest.mark.parametrize("r", [0, 3, 10, 15])
 @pytest.mark.parametrize("median", [False, True])
-def test_stamps_match_oracle(kb, ctx, r, median):
+@pytest.mark.parametrize("aperture", [0.0, 3.0])
+def test_stamps_match_oracle(kb, ctx, r, median, aperture):
     st = _shuffled(900 + r, 9, 48, 61)
     job, res = _searched(kb, ctx, st)
     x0, y0, vi = _candidates(st, res, np.random.default_rng(r))
-    _check(kb, job, st, x0, y0, vi, r, median)
+    _check(kb, job, st, x0, y0, vi, r, median, aperture=aperture)
     job.free()
 
 
@@ -145,8 +152,10 @@ def test_moment_cuts(kb, ctx):
     x0, y0, vi = _candidates(st, res, np.random.default_rng(2), n_kept=100, n_best=40)
     cuts = {"max_offset": 1.0, "min_var": 0.25, "max_var": 4.0, "max_mu11": 1.0}
     _, mom = _check(kb, job, st, x0, y0, vi, 5, True, cuts=cuts)
-    job.free()
     assert 0 < int(mom["passed"].sum()) < mom.size
+    _, mom = _check(kb, job, st, x0, y0, vi, 8, False, cuts=cuts, aperture=3.0)
+    assert 0 < int(mom["passed"].sum()) < mom.size
+    job.free()
 
 
 def test_stamp_arguments_are_checked(kb, ctx):
