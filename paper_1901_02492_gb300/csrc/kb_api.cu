@@ -349,6 +349,7 @@ void kb_stack_free(kb_stack *s) {
     dev_free(ctx, s->q16);
     dev_free(ctx, s->scales);
     dev_free(ctx, s->maxbits);
+    dev_free(ctx, s->snr2);
     dev_free(ctx, s->taps);
     host_release(ctx, s->taps_host, s->taps_host_cap);
     dev_release(ctx, s->bytes);
@@ -424,7 +425,8 @@ int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->taps, th, nt * sizeof(float), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(s->taps_done, st);
     bool q = s->q16 != nullptr;
-    if (e == cudaSuccess && q) e = cudaMemsetAsync(s->maxbits, 0, 2 * N * sizeof(unsigned), st);
+    // per-epoch maxima: the 16-bit scales and the binary points of the exact rescoring sums
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->maxbits, 0, 2 * N * sizeof(unsigned), st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_make_psi_phi upload");
 
     kb::PsiPhiArgs a;
@@ -442,7 +444,7 @@ int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8
     a.separable = sep;
     a.taps = s->taps;
     a.out = s->f32;
-    a.maxbits = q ? s->maxbits : nullptr;
+    a.maxbits = s->maxbits;
     e = kb::launch_psi_phi(a, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "psi/phi kernel");
     if (q) {
@@ -452,6 +454,7 @@ int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8
     e = cudaEventRecord(s->used, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_make_psi_phi");
     s->filled = true;
+    s->snr2_valid = false;   // the bound planes follow the psi/phi planes
     return KB_OK;
 }
 
@@ -698,7 +701,7 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
                     "topk<=%d)", s->N, s->H, s->W, V, topk, job->H, job->W, job->Ncap, job->Vcap, job->kcap);
     if ((flags & KB_RESCORE_FP64) && !(job->flags & KB_RESCORE_FP64))
         return fail(ctx, KB_EINVAL, "kb_search: rescoring requested but the job was created without it");
-    if (flags & ~KB_RESCORE_FP64) return fail(ctx, KB_EINVAL, "unknown flags 0x%x", flags);
+    if (flags & ~(KB_RESCORE_FP64 | KB_PRUNE)) return fail(ctx, KB_EINVAL, "unknown flags 0x%x", flags);
     if (std::isnan(nu_min)) return fail(ctx, KB_EINVAL, "nu_min is NaN");
     const int N = s->N;
     Plan pl;
@@ -808,6 +811,9 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
     // automatic tile order: super-columns of 8 tiles (12 x 4096^2, FP32, k = 8: 97.7 ms
     // against 117.4 ms row by row; 6 and 12 tiles within 1 %)
     a.swz = ctx->search_swizzle < 0 ? 8 : ctx->search_swizzle;
+    a.cand_only = (flags & KB_RESCORE_FP64) ? 1 : 0;
+    a.snr2 = nullptr;           // set by kb_search for KB_PRUNE
+    a.nu_min2_slack = 0.0f;
     if (rescore) {
         r.f32 = s->f32;
         r.plane_elems = a.plane_elems;
@@ -818,6 +824,7 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
         r.N = N;
         r.epoch_of = job->epoch_of;
         r.offs = job->offs;
+        r.maxbits = s->maxbits;
         r.cand = job->recs;
         r.kc = kkeep;
         r.k = topk;
@@ -852,6 +859,48 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     int rc = prepare_search(job, s, times, vx, vy, V, topk, nu_min, flags, st, a, r, rescore);
     if (rc != KB_OK) return rc;
     cudaError_t e;
+    // KB_PRUNE: the span bound planes for the automatic shape's span, built on first use (and
+    // after every kb_make_psi_phi) on this stream; only a positive nu_min can prune
+    if ((flags & KB_PRUNE) && nu_min > 0.0f && a.variant == 0) {
+        kb_stack *ms = const_cast<kb_stack *>(s);   // the bound planes are a cache of the stack
+        const int span = kb::search_auto_span(a.storage, a.k);
+        const size_t need = (size_t)ms->N * ms->H * (ms->W + span - 1) * sizeof(float);
+        if (ms->snr2 && ms->snr2_bytes != need) {
+            cudaStreamWaitEvent(ctx->astream, ms->used, 0);
+            dev_free(ctx, ms->snr2);
+            dev_release(ctx, ms->snr2_bytes);
+            ms->bytes -= std::min(ms->bytes, ms->snr2_bytes);
+            ms->snr2 = nullptr;
+            ms->snr2_bytes = 0;
+            ms->snr2_valid = false;
+        }
+        if (!ms->snr2) {
+            rc = dev_alloc(ctx, need, (void **)&ms->snr2, &ms->bytes);
+            if (rc != KB_OK) return rc;
+            ms->snr2_bytes = need;
+            ms->snr2_valid = false;
+        }
+        if (!ms->snr2_valid || ms->snr2_span != span) {
+            kb::SnrArgs b;
+            b.planes = a.planes;
+            b.storage = a.storage;
+            b.scales = ms->scales;
+            b.plane_elems = ms->L.plane_elems;
+            b.origin = ms->L.origin;
+            b.N = ms->N;
+            b.H = ms->H;
+            b.W = ms->W;
+            b.pitch = ms->L.pitch;
+            b.span = span;
+            b.out = ms->snr2;
+            e = kb::launch_snr2(b, st);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "span bound kernel");
+            ms->snr2_valid = true;
+            ms->snr2_span = span;
+        }
+        a.snr2 = ms->snr2;
+        a.nu_min2_slack = nu_min * nu_min;
+    }
     if (a.variant >= 5)
         e = kb::launch_search_tma(a, st);
     else
@@ -1379,16 +1428,17 @@ int kb_filter_lightcurves(kb_job *job, const kb_stack *s, double nsigma, kb_filt
 }
 
 int kb_stamps(kb_job *job, const float *sci, const uint8_t *mask, int N, int H, int W, const int32_t *x0,
-              const int32_t *y0, const int32_t *vidx, int n, int radius, int mode, const kb_moment_cuts *cuts,
-              float *stamps, kb_moments *moments, void *stream) {
+              const int32_t *y0, const int32_t *vidx, int n, int radius, int mode, double aperture,
+              const kb_moment_cuts *cuts, float *stamps, kb_moments *moments, void *stream) {
     if (!job) return KB_EINVAL;
     kb_ctx *ctx = job->ctx;
     if (job->k == 0) return fail(ctx, KB_EINVAL, "kb_stamps: no search has run on this job");
     if (N != job->N || H != job->H || W != job->W)
         return fail(ctx, KB_EINVAL, "kb_stamps: images %dx%dx%d are not the searched stack's %dx%dx%d", N, H, W,
                     job->N, job->H, job->W);
-    if (radius < 0 || radius > KB_MAX_STAMP_RADIUS || (mode != KB_STAMP_MEAN && mode != KB_STAMP_MEDIAN) || n < 0)
-        return fail(ctx, KB_EINVAL, "kb_stamps: radius %d, mode %d or count %d out of range", radius, mode, n);
+    if (radius < 0 || radius > KB_MAX_STAMP_RADIUS || (mode != KB_STAMP_MEAN && mode != KB_STAMP_MEDIAN) || n < 0 ||
+        std::isnan(aperture))
+        return fail(ctx, KB_EINVAL, "kb_stamps: radius %d, mode %d, aperture or count %d out of range", radius, mode, n);
     if (n == 0) return KB_OK;
     if (!sci || !stamps || !x0 || !y0 || !vidx || !is_device_ptr(sci) || !is_device_ptr(stamps) ||
         (mask && !is_device_ptr(mask)) || (moments && !is_device_ptr(moments)))
@@ -1418,6 +1468,7 @@ int kb_stamps(kb_job *job, const float *sci, const uint8_t *mask, int N, int H, 
     a.n = n;
     a.r = radius;
     a.mode = mode;
+    a.aperture = aperture;
     a.cut = cuts != nullptr;
     if (cuts) a.cuts = *cuts;
     a.stamps = stamps;

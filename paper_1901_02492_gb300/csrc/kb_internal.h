@@ -95,6 +95,12 @@ struct kb_stack {
     size_t taps_floats = 0;
     cudaEvent_t taps_done = nullptr;  // taps_host may be rewritten once this has completed
     cudaEvent_t used = nullptr;       // recorded after the last kernel that read the planes
+    // likelihood bound planes of the thresholded search (KB_PRUNE), built on first use for
+    // one span width and invalidated by kb_make_psi_phi
+    float *snr2 = nullptr;        // [N][H][W + snr2_span - 1]
+    size_t snr2_bytes = 0;
+    int snr2_span = 0;
+    bool snr2_valid = false;
     size_t bytes = 0;
     bool filled = false;
     bool zeroed = false;          // the FP32 planes (borders included) were cleared on a stream
@@ -179,9 +185,26 @@ struct SearchArgs {
     int *status;             // device status word: KB_ETIMEOUT if a bounded wait gave up
     int by0, nby;            // register-gather kernel: row tiles by0 .. by0 + nby - 1 (nby 0: all)
     int swz;                 // tile order: super-columns of this many tiles (0: row by row)
+    int cand_only;           // candidates for FP64 rescoring: records carry vidx and nu only (the
+                             // rescoring recomputes the sums), so the epilogue gathers nothing
+    const float *snr2;       // KB_PRUNE: span bound planes [N][H][W + span - 1] (stack epochs), else null
+    float nu_min2_slack;     // KB_PRUNE: skip a span when its bound times (1 + 2^-14) is below this (nu_min^2)
 };
 // register-gather kernel (variant 0 = its default shape, 1..4)
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
+// the automatic shape's span for lists of k (pixels per warp, the KB_PRUNE window)
+int search_auto_span(int storage, int k);
+
+// likelihood bound planes of the thresholded search (kb_prune.cu)
+struct SnrArgs {
+    const void *planes;      // FP32 planes or 16-bit phase-0 planes of the stack
+    int storage;
+    const float2 *scales;    // [N] 16-bit scales (device)
+    long long plane_elems, origin;
+    int N, H, W, pitch, span;
+    float *out;              // [N][H][W + span - 1]
+};
+cudaError_t launch_snr2(const SnrArgs &a, cudaStream_t st);
 // TMA-pipelined kernel (variants 5..8)
 cudaError_t launch_search_tma(const SearchArgs &a, cudaStream_t st);
 // persistent batch kernel over (job, tile) items {job, tile x, tile y, 0}; all jobs of
@@ -202,6 +225,7 @@ struct RescoreArgs {
     int H, W, pitch, N, V;
     const int *epoch_of;
     const int2 *offs;        // [V][N] time order
+    const unsigned *maxbits; // [2N] per-epoch max |psi|, max phi (float bits), for the exact sums
     const Rec *cand;         // [H*W][kc]
     int kc;                  // candidates per pixel
     int k;                   // results per pixel
@@ -253,6 +277,7 @@ struct StampArgs {
     const int2 *offs;        // [V][N] time order
     const int4 *cand;        // [n] (x0, y0, vidx, 0)
     int n, r, mode;
+    double aperture;         // moments over x^2 + y^2 <= aperture^2 (<= 0: the whole stamp)
     bool cut;
     kb_moment_cuts cuts;
     float *stamps;           // [n][S][S]

@@ -255,7 +255,10 @@ __device__ __forceinline__ void flush_queue(const uint2 *q, int n, float *s_ln, 
 // One CTA tile (rows by * 8 .. +7, columns bx * SPAN .. +SPAN-1) of one search:
 // the body of both the one-search kernel and the persistent batch kernel.
 // LONG: lists longer than kRankMax (walk insertion, predicated last load batch).
-template <int STORAGE, int P, int C, bool LONG, typename I>
+// PRUNE: before a velocity's gathers, each warp adds its shifted span's bound
+// (one value per epoch from the span bound planes, kb_prune.cu) and skips the
+// velocity when the bound cannot reach nu_min^2 (the results do not change).
+template <int STORAGE, int P, int C, bool LONG, typename I, bool PRUNE>
 __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by, float2 *s_scale, int4 *s_dyn4) {
     typedef Store<STORAGE> St;
     typedef typename St::T T;         // one pixel's (psi, phi)
@@ -268,17 +271,19 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     constexpr int LS = THREADS * PX;  // list columns (pixels) of the CTA
     constexpr int QCAP = 32 * (PX + 1);   // < 32 pending after a flush, + one velocity's candidates
 
-    // s_scale: per time-ordered epoch.  s_dyn4: table E [TAB] | velocity ids [TAB] |
-    // list nu float [k * LS] | list vidx u16 [k * LS] | (8-byte aligned) per-warp
-    // queues uint2 [WARPS][QCAP].
+    // s_scale: per time-ordered epoch.  s_dyn4: table E [TAB] | (PRUNE) bound offsets I [TAB] |
+    // velocity ids [TAB] | list nu float [k * LS] | list vidx u16 [k * LS] | (8-byte aligned)
+    // per-warp queues uint2 [WARPS][QCAP].
     E *s_tab = reinterpret_cast<E *>(s_dyn4);
-    int *s_vid = reinterpret_cast<int *>(s_tab + TAB);
+    I *s_rid = reinterpret_cast<I *>(s_tab + TAB);
+    int *s_vid = reinterpret_cast<int *>(s_rid + (PRUNE ? TAB : 0));
     const int N = a.N, n0 = a.n0, NJ = N - n0, k = a.k;
     const int NJP = (NJ + 1) & ~1;   // table row stride: even, so entries pair into 16-byte loads
     float *s_ln = reinterpret_cast<float *>(s_vid + TAB);
     uint16_t *s_lv = reinterpret_cast<uint16_t *>(s_ln + k * LS);
     uint2 *s_q = reinterpret_cast<uint2 *>(s_dyn4) +
-                 ((TAB * (sizeof(E) + sizeof(int)) + (size_t)k * LS * (sizeof(float) + sizeof(uint16_t)) + 7) / 8);
+                 ((TAB * (sizeof(E) + sizeof(int) + (PRUNE ? sizeof(I) : 0)) +
+                   (size_t)k * LS * (sizeof(float) + sizeof(uint16_t)) + 7) / 8);
 
     for (int j = threadIdx.x; j < N; j += THREADS)
         s_scale[j] = (STORAGE == KB_F32) ? make_float2(1.0f, 1.0f) : exp_scale(scale_exp(a.scales[a.epoch_of[j]]));
@@ -326,6 +331,15 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
         }
     }
 
+    // PRUNE: the bound rows are W + SPAN - 1 long; the reference epochs' share is fixed
+    const long long RW = (long long)a.W + SPAN - 1;
+    float b0 = 0.0f;
+    if constexpr (PRUNE) {
+        if (active)
+            for (int j = 0; j < n0; ++j)
+                b0 = __fadd_ru(b0, __ldg(a.snr2 + ((long long)a.epoch_of[j] * a.H + y) * RW + xw + SPAN - 1));
+    }
+
     const int vchunk = min(a.V, TAB / max(NJP, 1));
     for (int c0 = 0; c0 < a.V; c0 += vchunk) {
         const int nc = min(vchunk, a.V - c0);
@@ -350,12 +364,25 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             e.info = mask;
             if constexpr (STORAGE != KB_F32) e.sc = sc_of(exp_scale(scale_exp(a.scales[ep])));
             s_tab[vi * NJP + jj] = e;
+            if constexpr (PRUNE)   // the CTA's first row; a warp adds warp * RW
+                s_rid[vi * NJP + jj] = mask ? (I)(((long long)ep * a.H + y0 + oy) * RW + xw + ox + SPAN - 1) : (I)0;
         }
         __syncthreads();
         if (!active) continue;
         for (int vi = 0; vi < nc; ++vi) {
             const int v = s_vid[vi];
             const E *tab = s_tab + vi * NJP;
+            if constexpr (PRUNE) {
+                // the span's bound on nu^2, rounded upwards, lane 0's sum for the whole warp
+                float b = 0.0f;
+                const I *rid = s_rid + vi * NJP;
+                for (int jj = lane; jj < NJ; jj += 32)
+                    if (tab[jj].info & wbit) b = __fadd_ru(b, __ldg(a.snr2 + rid[jj] + (long long)warp * RW));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) b = __fadd_ru(b, __shfl_xor_sync(0xffffffffu, b, o));
+                b = __shfl_sync(0xffffffffu, b, 0);
+                if (__fmul_ru(__fadd_ru(b, b0), 1.0f + 0x1p-14f) < a.nu_min2_slack) continue;
+            }
             float2 acc[PX];
 #pragma unroll
             for (int p = 0; p < PX; ++p) acc[p] = acc0[p];
@@ -484,6 +511,11 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
                 r.phi = 0.0f;
                 r.nu = -INFINITY;
                 r.meta = kEmptyVidx;
+            } else if (a.cand_only) {
+                r.psi = 0.0f;
+                r.phi = 0.0f;
+                r.nu = ln[i * LS];
+                r.meta = (uint32_t)v;
             } else {
                 const int2 *ov = a.offs + (long long)v * N;
                 float2 acc = acc0[p];
@@ -549,7 +581,7 @@ constexpr int min_ctas_batch() {
     return (STORAGE == KB_F32 ? P <= 2 : P <= 1) ? 3 : 2;
 }
 
-template <int STORAGE, int P, int C, bool LONG, typename I>
+template <int STORAGE, int P, int C, bool LONG, typename I, bool PRUNE>
 __global__ void __launch_bounds__(THREADS, min_ctas<STORAGE, P, C, LONG>()) search_kernel(SearchArgs a) {
     __shared__ float2 s_scale[KB_MAX_EPOCHS];
     extern __shared__ int4 s_dyn4[];
@@ -563,7 +595,7 @@ __global__ void __launch_bounds__(THREADS, min_ctas<STORAGE, P, C, LONG>()) sear
         by = r / w;
         bx = s * a.swz + (r - by * w);
     }
-    search_tile<STORAGE, P, C, LONG, I>(a, bx, a.by0 + by, s_scale, s_dyn4);
+    search_tile<STORAGE, P, C, LONG, I, PRUNE>(a, bx, a.by0 + by, s_scale, s_dyn4);
 }
 
 // Persistent batch search: CTAs take (job, tile) work items from an atomic
@@ -586,27 +618,28 @@ __global__ void __launch_bounds__(THREADS, min_ctas_batch<STORAGE, P>())
         for (int i = threadIdx.x; i < (int)(sizeof(SearchArgs) / sizeof(int)); i += THREADS)
             reinterpret_cast<int *>(&s_job)[i] = reinterpret_cast<const int *>(jobs + w.x)[i];
         __syncthreads();
-        search_tile<STORAGE, P, C, LONG, I>(s_job, w.y, w.z, s_scale, s_dyn4);
+        search_tile<STORAGE, P, C, LONG, I, false>(s_job, w.y, w.z, s_scale, s_dyn4);
         __syncthreads();
     }
 }
 
 // dynamic shared memory of a CTA with lists of k entries: the table, the lists and the queues
-template <int STORAGE, int P, typename I>
+template <int STORAGE, int P, typename I, bool PRUNE = false>
 size_t tile_smem(int k) {
     constexpr int PX = P * Gather<STORAGE>::PIX;
-    const size_t base = (size_t)tab_entries<STORAGE>() * (sizeof(Entry<I, STORAGE != KB_F32>) + sizeof(int)) +
+    const size_t base = (size_t)tab_entries<STORAGE>() *
+                            (sizeof(Entry<I, STORAGE != KB_F32>) + sizeof(int) + (PRUNE ? sizeof(I) : 0)) +
                         (size_t)k * THREADS * PX * (sizeof(float) + sizeof(uint16_t));
     return (base + 7) / 8 * 8 + (size_t)WARPS * 32 * (PX + 1) * sizeof(uint2);
 }
 
-template <int STORAGE, int P, int C, bool LONG, typename I>
+template <int STORAGE, int P, int C, bool LONG, typename I, bool PRUNE>
 cudaError_t launch_pt(const SearchArgs &a, cudaStream_t st) {
     constexpr int SPAN = 32 * P * Gather<STORAGE>::PIX;
     static_assert(SPAN <= kSpan, "warp span wider than the zero columns");
-    auto kern = search_kernel<STORAGE, P, C, LONG, I>;
+    auto kern = search_kernel<STORAGE, P, C, LONG, I, PRUNE>;
     dim3 grid((a.W + SPAN - 1) / SPAN, a.nby > 0 ? a.nby : (a.H + WARPS - 1) / WARPS);
-    const size_t smem = tile_smem<STORAGE, P, I>(a.k);
+    const size_t smem = tile_smem<STORAGE, P, I, PRUNE>(a.k);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // Shared-memory carveout: the driver's choice unless the caller sets one
     // (kb_set_search_carveout); it trades resident CTAs against the L1 that the
@@ -619,18 +652,19 @@ cudaError_t launch_pt(const SearchArgs &a, cudaStream_t st) {
 }
 
 // lists longer than kRankMax take the walking insertion and the predicated remainder
-template <int STORAGE, int P, int C, typename I>
+template <int STORAGE, int P, int C, typename I, bool PRUNE>
 cudaError_t launch_one(const SearchArgs &a, cudaStream_t st) {
-    if (a.k > kRankMax) return launch_pt<STORAGE, P, C, true, I>(a, st);
-    return launch_pt<STORAGE, P, C, false, I>(a, st);
+    if (a.k > kRankMax) return launch_pt<STORAGE, P, C, true, I, PRUNE>(a, st);
+    return launch_pt<STORAGE, P, C, false, I, PRUNE>(a, st);
 }
 
-template <int STORAGE, int P, int C>
+// 32-bit element offsets when every plane of both phases (and the bound planes) fits
+template <int STORAGE, int P, int C, bool PRUNE = false>
 cudaError_t launch_idx(const SearchArgs &a, cudaStream_t st) {
-    // 32-bit element offsets when every plane of both phases fits
     const long long span = (STORAGE == KB_F32 ? 1LL : 2LL) * a.N * a.plane_elems;
-    if (span < (1LL << 31) - 1) return launch_one<STORAGE, P, C, int>(a, st);
-    return launch_one<STORAGE, P, C, long long>(a, st);
+    const long long rspan = PRUNE ? (long long)a.N * a.H * (a.W + 32 * P * Gather<STORAGE>::PIX) : 0;
+    if (span < (1LL << 31) - 1 && rspan < (1LL << 31) - 1) return launch_one<STORAGE, P, C, int, PRUNE>(a, st);
+    return launch_one<STORAGE, P, C, long long, PRUNE>(a, st);
 }
 
 // Shapes: (loads per lane P, epochs per load batch C); a 16-bit load is two pixels.
@@ -644,7 +678,9 @@ cudaError_t launch_storage(const SearchArgs &a, cudaStream_t st) {
             case 1: return launch_idx<STORAGE, 4, 4>(a, st);
             case 2: return launch_idx<STORAGE, 2, 4>(a, st);
             case 3: return launch_idx<STORAGE, 4, 8>(a, st);
-            default: return launch_idx<STORAGE, 2, 8>(a, st);
+            default:
+                if (a.snr2) return launch_idx<STORAGE, 2, 8, true>(a, st);
+                return launch_idx<STORAGE, 2, 8>(a, st);
         }
     } else {
         switch (a.variant) {
@@ -654,7 +690,10 @@ cudaError_t launch_storage(const SearchArgs &a, cudaStream_t st) {
             case 1: return launch_idx<STORAGE, 2, 4>(a, st);
             // automatic: lists longer than kRankMax take the one-pair shape, whose 512-pixel
             // CTAs keep their lists' shared memory within what 3 CTAs per SM can hold
-            default: return a.k > kRankMax ? launch_idx<STORAGE, 1, 4>(a, st) : launch_idx<STORAGE, 2, 4>(a, st);
+            default:
+                if (a.snr2)
+                    return a.k > kRankMax ? launch_idx<STORAGE, 1, 4, true>(a, st) : launch_idx<STORAGE, 2, 4, true>(a, st);
+                return a.k > kRankMax ? launch_idx<STORAGE, 1, 4>(a, st) : launch_idx<STORAGE, 2, 4>(a, st);
         }
     }
 }
@@ -721,6 +760,8 @@ int search_span(int storage, int variant, int k) {
     if (storage != KB_F32 && v == 0 && k > kRankMax) return 64;
     return storage == KB_F32 ? 32 * p32[v] : 64 * p16[v];
 }
+
+int search_auto_span(int storage, int k) { return search_span(storage, 0, k); }
 
 int default_variant(int storage, int k) {
     if (storage == KB_F32) return 4;       // (2, 8)

@@ -1,7 +1,9 @@
 """Reduced precision on the full 12 x 4096 x 4096 DECam-shaped stack (1024
-velocities, k = 8): nu/alpha error against the FP64 oracle on the 512 x 512
-subregion [0, 512)^2, and top-k agreement over the full image, for BF16 and FP16
-storage with and without FP64 rescoring, beside the FP32 path.
+velocities, k = 8): nu/alpha error against the FP64 oracle on three 512 x 512
+blocks -- the top-left corner [0, 512)^2, the centre [1792, 2304)^2 and the
+bottom-right corner [3584, 4096)^2, where most late-epoch trajectories leave the
+image -- and top-k agreement over the full image, for BF16 and FP16 storage with
+and without FP64 rescoring, beside the FP32 path.
 
 Bars: with rescoring, the subregion's top-k matches the oracle like the FP32
 path (nu within 1e-5 relative, identical lists up to near-ties), and over the
@@ -29,6 +31,7 @@ from _compare import check_topk, nu_tol
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 DEV = torch.device("cuda:0")
 SUB = 512
+BLOCKS = [(0, 0), (1792, 1792), (3584, 3584)]   # (x0, y0) of each compared block
 
 
 @pytest.fixture(scope="module")
@@ -37,9 +40,10 @@ def setup(kb):
     psi, phi = oracle.psi_phi(st.sci, st.var, None, st.psf)
     dx, dy = oracle.offsets(st.times, st.vx, st.vy)
     yy, xx = np.mgrid[0:SUB, 0:SUB]
-    ref = oracle.search_pixels(psi, phi, st.times, dx, dy, st.k, xx.ravel(), yy.ravel())
+    refs = [oracle.search_pixels(psi, phi, st.times, dx, dy, st.k, (xx + bx).ravel(), (yy + by).ravel())
+            .reshape(SUB, SUB, st.k) for bx, by in BLOCKS]
     ctx = kb.Context(0)
-    yield st, psi, phi, dx, dy, ref.reshape(SUB, SUB, st.k), ctx
+    yield st, psi, phi, dx, dy, refs, ctx
     ctx.close()
 
 
@@ -92,7 +96,8 @@ def _run(kb, ctx, st, storage, rescore):
     repaired = job.repaired() if rescore else 0
     sp_max = float(s.scales()[0].max()) if storage != "f32" else 0.0
     rec = out.view(H, W, st.k * kb.RESULT_DTYPE.itemsize)
-    sub = rec[:SUB, :SUB].contiguous().cpu().numpy().view(kb.RESULT_DTYPE).reshape(SUB, SUB, st.k)
+    sub = [rec[by:by + SUB, bx:bx + SUB].contiguous().cpu().numpy().view(kb.RESULT_DTYPE).reshape(SUB, SUB, st.k)
+           for bx, by in BLOCKS]
     vidx = out.view(torch.int32).view(H, W, st.k, kb.RESULT_DTYPE.itemsize // 4)[..., 2].contiguous().cpu().numpy()
     nu = out.view(torch.float64).view(H, W, st.k, kb.RESULT_DTYPE.itemsize // 8)[..., 4].contiguous().cpu().numpy()
     torch.cuda.synchronize()
@@ -103,44 +108,48 @@ def _run(kb, ctx, st, storage, rescore):
 
 
 def test_precision_report_decam(kb, setup):
-    st, psi, phi, dx, dy, ref, ctx = setup
-    report = {"workload": "decam 12x4096x4096, 1024 velocities, k=8", "subregion": "[0,512)^2"}
+    st, psi, phi, dx, dy, refs, ctx = setup
+    report = {"workload": "decam 12x4096x4096, 1024 velocities, k=8",
+              "blocks": ["[%d,%d)x[%d,%d)" % (bx, bx + SUB, by, by + SUB) for bx, by in BLOCKS]}
     sub32, vidx32, nu32, _, _ = _run(kb, ctx, st, "f32", False)
-    nu_of = lambda p, v: _nu64(psi, phi, dx, dy, p % SUB, p // SUB, v)
     for storage, rescore in [("f32", False), ("bf16", False), ("f16", False), ("bf16", True), ("f16", True)]:
         if storage == "f32":
-            sub, vidx, nu, rep, sp_max = sub32, vidx32, nu32, 0, 0.0
+            subs, vidx, nu, rep, sp_max = sub32, vidx32, nu32, 0, 0.0
         else:
-            sub, vidx, nu, rep, sp_max = _run(kb, ctx, st, storage, rescore)
-        valid = ref["vidx"] >= 0
-        same = valid & (sub["vidx"] == ref["vidx"])
-        rel = np.abs(sub["nu"][same] - ref["nu"][same]) / np.maximum(np.abs(ref["nu"][same]), 1.0)
-        sig = 1.0 / np.sqrt(ref["phi"][same])
-        arel = np.abs(sub["alpha"][same] - ref["alpha"][same]) / np.maximum(np.abs(ref["alpha"][same]), sig)
+            subs, vidx, nu, rep, sp_max = _run(kb, ctx, st, storage, rescore)
+        name = storage + ("+fp64 rescore" if rescore else "")
         full_same = float(np.mean(vidx == vidx32))
         # full-image slots that differ from the FP32 lists: near-ties of the FP32 values?
         diff = vidx != vidx32
         tie = np.abs(nu[diff] - nu32[diff]) <= 2 * nu_tol(nu32[diff])
-        name = storage + ("+fp64 rescore" if rescore else "")
-        report[name] = {"sub_slots_same_vidx_as_oracle": float(same.sum() / valid.sum()),
-                        "sub_nu_rel_err_max": float(rel.max()), "sub_nu_rel_err_mean": float(rel.mean()),
-                        "sub_alpha_rel_err_max": float(arel.max()),
-                        "full_slots_same_vidx_as_fp32": full_same,
+        report[name] = {"full_slots_same_vidx_as_fp32": full_same,
                         "full_slots_differing_from_fp32": int(diff.sum()),
                         "full_differing_slots_within_2tol_of_fp32_nu": int(tie.sum()),
-                        "repaired_pixels": int(rep)}
+                        "repaired_pixels": int(rep), "blocks": []}
         if storage == "f32" or rescore:
-            check_topk(sub, ref, nu_of)                    # the FP32 bar against the oracle
-            assert rel.max() <= 1e-5
             assert full_same >= 0.999
-        else:
-            # the 16-bit pass: every compared nu within its unit-roundoff bound
-            py, px, _ = np.nonzero(same)
-            v = sub["vidx"][same]
-            err = np.abs(sub["nu"][same] - ref["nu"][same])
-            bound = _bound16(storage, psi, phi, dx, dy, px, py, v, sp_max)
-            report[name]["sub_nu_err_over_bound_max"] = float((err / bound).max())
-            assert np.all(err <= bound), "max excess %.3g" % (err - bound).max()
+        for (bx, by), sub, ref in zip(BLOCKS, subs, refs):
+            valid = ref["vidx"] >= 0
+            same = valid & (sub["vidx"] == ref["vidx"])
+            rel = np.abs(sub["nu"][same] - ref["nu"][same]) / np.maximum(np.abs(ref["nu"][same]), 1.0)
+            sig = 1.0 / np.sqrt(ref["phi"][same])
+            arel = np.abs(sub["alpha"][same] - ref["alpha"][same]) / np.maximum(np.abs(ref["alpha"][same]), sig)
+            blk = {"origin": [bx, by], "slots_same_vidx_as_oracle": float(same.sum() / valid.sum()),
+                   "valid_slots": int(valid.sum()), "nu_rel_err_max": float(rel.max()),
+                   "nu_rel_err_mean": float(rel.mean()), "alpha_rel_err_max": float(arel.max())}
+            if storage == "f32" or rescore:
+                nu_of = lambda p, v, bx=bx, by=by: _nu64(psi, phi, dx, dy, bx + p % SUB, by + p // SUB, v)
+                check_topk(sub, ref, nu_of)                    # the FP32 bar against the oracle
+                assert rel.max() <= 1e-5
+            else:
+                # the 16-bit pass: every compared nu within its unit-roundoff bound
+                py, px, _ = np.nonzero(same)
+                v = sub["vidx"][same]
+                err = np.abs(sub["nu"][same] - ref["nu"][same])
+                bound = _bound16(storage, psi, phi, dx, dy, px + bx, py + by, v, sp_max)
+                blk["nu_err_over_bound_max"] = float((err / bound).max())
+                assert np.all(err <= bound), "max excess %.3g" % (err - bound).max()
+            report[name]["blocks"].append(blk)
     path = os.environ.get("KB_PRECISION_REPORT")
     if path:
         with open(path, "w") as f:
