@@ -73,6 +73,9 @@ def parse():
                          "the M highest-nu trajectories")
     ap.add_argument("--cluster", type=int, default=0, metavar="M",
                     help="also time Sec. 3.3 DBSCAN de-duplication of the M highest-nu trajectories")
+    ap.add_argument("--threshold", type=float, default=0.0, metavar="NU_MIN",
+                    help="also time the thresholded search (nu >= NU_MIN) with and without likelihood-bound "
+                         "pruning (KB_PRUNE, Sec. 5.3); reported apart from the headline")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-load", type=float, default=0.75,
                     help="arrival rate as a fraction of the capacity measured on a saturated sample")
@@ -562,6 +565,29 @@ def run_ours(args):
                                 % (n_e2e, "kb_results_compact_async" if args.e2e_records == "compact"
                                    else "kb_results_async")},
             "gpu_launches": launches_per_step * args.steps}
+    if args.threshold > 0:
+        # the thresholded search (Sec. 5.2's nu_min), plain and with likelihood-bound pruning: the
+        # same records, the pruned one skipping the gathers of spans whose bound is below nu_min
+        nu_min = float(args.threshold)
+        tout = [torch.empty(H * W * k * kb.COMPACT_DTYPE.itemsize, dtype=torch.uint8, device=dev) for _ in range(2)]
+        tms = {}
+        for i, (name, fl) in enumerate((("plain", flags), ("pruned", flags | kb.KB_PRUNE))):
+            job.search(stack, st.times, st.vx, st.vy, k, nu_min, fl, stream=stream)   # warm-up (builds the bounds)
+            t0, t1 = ev(), ev()
+            t0.record(stream)
+            for _ in range(3):
+                job.search(stack, st.times, st.vx, st.vy, k, nu_min, fl, stream=stream)
+            t1.record(stream)
+            job.results_compact_async(tout[i], stream=stream)
+            torch.cuda.synchronize(dev)
+            tms[name] = t0.elapsed_time(t1) / 3
+        kept = int((tout[1].view(torch.int32).view(-1, 4)[:, 3] & 0xFFFF != 0xFFFF).sum().item())
+        line["thresholded"] = {"nu_min": nu_min, "ms_per_search_plain": tms["plain"],
+                               "ms_per_search_pruned": tms["pruned"], "speedup": tms["plain"] / tms["pruned"],
+                               "records_identical": bool(torch.equal(tout[0], tout[1])), "kept_trajectories": kept,
+                               "nominal_evals_per_s_pruned": evals / (tms["pruned"] * 1e-3),
+                               "note": "nominal: every trajectory-epoch evaluation of the grid, skipped ones included"}
+        del tout
     if args.filter:
         # the Sec. 3.3 outlier filter of every kept trajectory (two FP64 passes over its epochs)
         fout = torch.empty(H * W * k * kb.FILTERED_DTYPE.itemsize, dtype=torch.uint8, device=dev)

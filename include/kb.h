@@ -211,6 +211,11 @@ int kb_make_psi_phi_static(const float *sci, const float *var, const uint8_t *ma
  *   which = 0: FP32 planes, float [N][H][W][2] = (psi, phi), dst_bytes >= N*H*W*8
  *   which = 1: 16-bit planes, uint16 [N][H][W][2] = (psi, phi) codes, dst_bytes >= N*H*W*4
  *              (value = code * scale of that epoch, see kb_stack_scales)
+ *   which = 2: the span bound planes of the last KB_PRUNE search, float
+ *              [N][H][(W + 31) / 32 + span / 32] (entry c + span / 32: the
+ *              largest max(psi, 0)^2 / phi over the image columns
+ *              [32 c, 32 c + span + 32)), dst_bytes >= their size; KB_EINVAL if
+ *              none are built
  * Host destinations make the call synchronous.  KB_EINVAL if the stack has no
  * such planes or dst_bytes is too small. */
 int kb_stack_copy_planes(const kb_stack *s, int which, void *dst, size_t dst_bytes, void *stream);
@@ -245,10 +250,12 @@ void kb_job_free(kb_job *j);
  *           FP32 planes, re-rank in FP64 and keep the top-k.
  *           KB_PRUNE (with nu_min > 0 and the automatic kernel shape): by
  *           Cauchy-Schwarz, nu^2 <= sum_t max(psi_t, 0)^2 / phi_t over a
- *           trajectory's in-image epochs; per epoch the largest such term over
- *           each warp span of the shifted start pixels is precomputed (a stack
- *           cache of N * H * (W + span - 1) floats, allocated under the budget
- *           and rebuilt after kb_make_psi_phi), and a velocity whose span bound
+ *           trajectory's in-image epochs; per epoch and row the largest such
+ *           term over windows [32 c, 32 c + span + 32) that cover a warp span of
+ *           the shifted start pixels is precomputed (a stack cache of
+ *           N * H * ((W + 31) / 32 + span / 32) floats, span = 64 or 128 pixels
+ *           by storage and k, allocated under the budget and rebuilt after
+ *           kb_make_psi_phi), and a velocity whose span bound
  *           (rounded upwards, with a 2^-14 relative margin) is below nu_min^2 is
  *           skipped for that span.  The records equal those of the same search
  *           without the flag, byte for byte.  Ignored otherwise (and by batches).

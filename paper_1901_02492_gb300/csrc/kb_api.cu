@@ -463,6 +463,19 @@ int kb_stack_copy_planes(const kb_stack *s, int which, void *dst, size_t dst_byt
     kb_ctx *ctx = s->ctx;
     if (!dst) return fail(ctx, KB_EINVAL, "kb_stack_copy_planes: dst is NULL");
     if (!s->filled) return fail(ctx, KB_EINVAL, "kb_stack_copy_planes: the stack has no psi/phi yet");
+    if (which == 2) {
+        // the span bound planes of KB_PRUNE, as built (contiguous [N][H][(W + 31) / 32 + span / 32])
+        if (!s->snr2 || !s->snr2_valid) return fail(ctx, KB_EINVAL, "the stack has no span bound planes");
+        if (dst_bytes < s->snr2_bytes) return fail(ctx, KB_EINVAL, "dst_bytes %zu < %zu", dst_bytes, s->snr2_bytes);
+        DeviceGuard g(ctx->device);
+        cudaStream_t st = (cudaStream_t)stream;
+        const bool dev = is_device_ptr(dst);
+        cudaError_t e = cudaMemcpyAsync(dst, s->snr2, s->snr2_bytes, cudaMemcpyDefault, st);
+        if (e == cudaSuccess) e = cudaEventRecord(s->used, st);
+        if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_stack_copy_planes");
+        return KB_OK;
+    }
     const void *src = which == 0 ? (const void *)s->f32 : (const void *)s->q16;
     size_t elem = which == 0 ? sizeof(float2) : sizeof(kb::pair16);
     if ((which != 0 && which != 1) || !src) return fail(ctx, KB_EINVAL, "stack has no planes of kind %d", which);
@@ -864,7 +877,7 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     if ((flags & KB_PRUNE) && nu_min > 0.0f && a.variant == 0) {
         kb_stack *ms = const_cast<kb_stack *>(s);   // the bound planes are a cache of the stack
         const int span = kb::search_auto_span(a.storage, a.k);
-        const size_t need = (size_t)ms->N * ms->H * (ms->W + span - 1) * sizeof(float);
+        const size_t need = (size_t)ms->N * ms->H * ((ms->W + 31) / 32 + span / 32) * sizeof(float);
         if (ms->snr2 && ms->snr2_bytes != need) {
             cudaStreamWaitEvent(ctx->astream, ms->used, 0);
             dev_free(ctx, ms->snr2);

@@ -97,7 +97,7 @@ struct kb_stack {
     cudaEvent_t used = nullptr;       // recorded after the last kernel that read the planes
     // likelihood bound planes of the thresholded search (KB_PRUNE), built on first use for
     // one span width and invalidated by kb_make_psi_phi
-    float *snr2 = nullptr;        // [N][H][W + snr2_span - 1]
+    float *snr2 = nullptr;        // [N][H][(W + 31) / 32 + snr2_span / 32]
     size_t snr2_bytes = 0;
     int snr2_span = 0;
     bool snr2_valid = false;
@@ -187,7 +187,7 @@ struct SearchArgs {
     int swz;                 // tile order: super-columns of this many tiles (0: row by row)
     int cand_only;           // candidates for FP64 rescoring: records carry vidx and nu only (the
                              // rescoring recomputes the sums), so the epilogue gathers nothing
-    const float *snr2;       // KB_PRUNE: span bound planes [N][H][W + span - 1] (stack epochs), else null
+    const float *snr2;       // KB_PRUNE: span bound planes [N][H][(W + 31) / 32 + span / 32] (stack epochs), else null
     float nu_min2_slack;     // KB_PRUNE: skip a span when its bound times (1 + 2^-14) is below this (nu_min^2)
 };
 // register-gather kernel (variant 0 = its default shape, 1..4)
@@ -202,7 +202,7 @@ struct SnrArgs {
     const float2 *scales;    // [N] 16-bit scales (device)
     long long plane_elems, origin;
     int N, H, W, pitch, span;
-    float *out;              // [N][H][W + span - 1]
+    float *out;              // [N][H][(W + 31) / 32 + span / 32]
 };
 cudaError_t launch_snr2(const SnrArgs &a, cudaStream_t st);
 // TMA-pipelined kernel (variants 5..8)

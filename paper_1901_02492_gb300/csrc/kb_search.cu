@@ -256,8 +256,9 @@ __device__ __forceinline__ void flush_queue(const uint2 *q, int n, float *s_ln, 
 // the body of both the one-search kernel and the persistent batch kernel.
 // LONG: lists longer than kRankMax (walk insertion, predicated last load batch).
 // PRUNE: before a velocity's gathers, each warp adds its shifted span's bound
-// (one value per epoch from the span bound planes, kb_prune.cu) and skips the
-// velocity when the bound cannot reach nu_min^2 (the results do not change).
+// (one value per epoch from the span bound planes, kb_prune.cu: L2-resident, one
+// per 32 columns) and skips the velocity when the bound cannot reach nu_min^2
+// (the results do not change).
 template <int STORAGE, int P, int C, bool LONG, typename I, bool PRUNE>
 __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by, float2 *s_scale, int4 *s_dyn4) {
     typedef Store<STORAGE> St;
@@ -331,13 +332,15 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
         }
     }
 
-    // PRUNE: the bound rows are W + SPAN - 1 long; the reference epochs' share is fixed
-    const long long RW = (long long)a.W + SPAN - 1;
+    // PRUNE: a bound row holds one value per 32 columns, (W + 31) / 32 + SPAN / 32 of them,
+    // the value for a span starting at column x at (x >> 5) + SPAN / 32; the reference
+    // epochs' share is fixed
+    const long long RW = (long long)(a.W + 31) / 32 + SPAN / 32;
     float b0 = 0.0f;
     if constexpr (PRUNE) {
         if (active)
             for (int j = 0; j < n0; ++j)
-                b0 = __fadd_ru(b0, __ldg(a.snr2 + ((long long)a.epoch_of[j] * a.H + y) * RW + xw + SPAN - 1));
+                b0 = __fadd_ru(b0, __ldg(a.snr2 + ((long long)a.epoch_of[j] * a.H + y) * RW + (xw >> 5) + SPAN / 32));
     }
 
     const int vchunk = min(a.V, TAB / max(NJP, 1));
@@ -365,19 +368,31 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             if constexpr (STORAGE != KB_F32) e.sc = sc_of(exp_scale(scale_exp(a.scales[ep])));
             s_tab[vi * NJP + jj] = e;
             if constexpr (PRUNE)   // the CTA's first row; a warp adds warp * RW
-                s_rid[vi * NJP + jj] = mask ? (I)(((long long)ep * a.H + y0 + oy) * RW + xw + ox + SPAN - 1) : (I)0;
+                s_rid[vi * NJP + jj] = mask ? (I)(((long long)ep * a.H + y0 + oy) * RW + ((xw + ox) >> 5) + SPAN / 32)
+                                            : (I)0;
         }
         __syncthreads();
         if (!active) continue;
+        // PRUNE: this lane's share of a velocity's span bound (its epochs jj = lane, lane + 32, ...),
+        // loaded one velocity ahead so that the loads overlap the previous velocity's gathers
+        auto bound_part = [&](int vj) {
+            float b = 0.0f;
+            if constexpr (PRUNE) {
+                const E *t = s_tab + vj * NJP;
+                const I *rid = s_rid + vj * NJP;
+                for (int jj = lane; jj < NJ; jj += 32)
+                    if (t[jj].info & wbit) b = __fadd_ru(b, __ldg(a.snr2 + rid[jj] + (long long)warp * RW));
+            }
+            return b;
+        };
+        float bnext = PRUNE ? bound_part(0) : 0.0f;
         for (int vi = 0; vi < nc; ++vi) {
             const int v = s_vid[vi];
             const E *tab = s_tab + vi * NJP;
             if constexpr (PRUNE) {
                 // the span's bound on nu^2, rounded upwards, lane 0's sum for the whole warp
-                float b = 0.0f;
-                const I *rid = s_rid + vi * NJP;
-                for (int jj = lane; jj < NJ; jj += 32)
-                    if (tab[jj].info & wbit) b = __fadd_ru(b, __ldg(a.snr2 + rid[jj] + (long long)warp * RW));
+                float b = bnext;
+                if (vi + 1 < nc) bnext = bound_part(vi + 1);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) b = __fadd_ru(b, __shfl_xor_sync(0xffffffffu, b, o));
                 b = __shfl_sync(0xffffffffu, b, 0);
@@ -662,7 +677,7 @@ cudaError_t launch_one(const SearchArgs &a, cudaStream_t st) {
 template <int STORAGE, int P, int C, bool PRUNE = false>
 cudaError_t launch_idx(const SearchArgs &a, cudaStream_t st) {
     const long long span = (STORAGE == KB_F32 ? 1LL : 2LL) * a.N * a.plane_elems;
-    const long long rspan = PRUNE ? (long long)a.N * a.H * (a.W + 32 * P * Gather<STORAGE>::PIX) : 0;
+    const long long rspan = PRUNE ? (long long)a.N * a.H * ((a.W + 31) / 32 + P * Gather<STORAGE>::PIX) : 0;
     if (span < (1LL << 31) - 1 && rspan < (1LL << 31) - 1) return launch_one<STORAGE, P, C, int, PRUNE>(a, st);
     return launch_one<STORAGE, P, C, long long, PRUNE>(a, st);
 }
