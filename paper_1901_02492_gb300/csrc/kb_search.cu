@@ -373,26 +373,15 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
         }
         __syncthreads();
         if (!active) continue;
-        // PRUNE: this lane's share of a velocity's span bound (its epochs jj = lane, lane + 32, ...),
-        // loaded one velocity ahead so that the loads overlap the previous velocity's gathers
-        auto bound_part = [&](int vj) {
-            float b = 0.0f;
-            if constexpr (PRUNE) {
-                const E *t = s_tab + vj * NJP;
-                const I *rid = s_rid + vj * NJP;
-                for (int jj = lane; jj < NJ; jj += 32)
-                    if (t[jj].info & wbit) b = __fadd_ru(b, __ldg(a.snr2 + rid[jj] + (long long)warp * RW));
-            }
-            return b;
-        };
-        float bnext = PRUNE ? bound_part(0) : 0.0f;
         for (int vi = 0; vi < nc; ++vi) {
             const int v = s_vid[vi];
             const E *tab = s_tab + vi * NJP;
             if constexpr (PRUNE) {
                 // the span's bound on nu^2, rounded upwards, lane 0's sum for the whole warp
-                float b = bnext;
-                if (vi + 1 < nc) bnext = bound_part(vi + 1);
+                float b = 0.0f;
+                const I *rid = s_rid + vi * NJP;
+                for (int jj = lane; jj < NJ; jj += 32)
+                    if (tab[jj].info & wbit) b = __fadd_ru(b, __ldg(a.snr2 + rid[jj] + (long long)warp * RW));
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) b = __fadd_ru(b, __shfl_xor_sync(0xffffffffu, b, o));
                 b = __shfl_sync(0xffffffffu, b, 0);
