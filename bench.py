@@ -530,6 +530,12 @@ def run_ours(args):
     delivered = classes["delivered_bytes_per_launch"] / (ms_search * 1e-3) / 1e9
     traffic = recorded_traffic("search_%s" % args.storage)
     levels = recorded_levels("search_%s" % args.storage)
+    if levels and "l2_to_l1_bytes_per_alg_byte" in levels:
+        # the L2 -> SM share at this size: the captured ratio to the algorithmic bytes
+        l2b = levels["l2_to_l1_bytes_per_alg_byte"] * alg_bytes
+        levels["l2_to_l1_bytes_per_launch"] = l2b
+        levels["l2_to_l1_GBps"] = l2b / (ms_search * 1e-3) / 1e9
+        levels["l2_to_l1_frac"] = levels["l2_to_l1_GBps"] / gather_peak
     hbm = peaks.get("hbm_gbs", 6800.0)
     psiphi_bytes = N * H * W * (8 + 8 + (4 + 8 if args.storage != "f32" else 0))
     cfg = workload_config(args, st, world)
