@@ -825,6 +825,8 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
     // against 117.4 ms row by row; 6 and 12 tiles within 1 %)
     a.swz = ctx->search_swizzle < 0 ? 8 : ctx->search_swizzle;
     a.cand_only = (flags & KB_RESCORE_FP64) ? 1 : 0;
+    a.key_bits = 1;
+    while ((1 << a.key_bits) < V) ++a.key_bits;
     a.snr2 = nullptr;           // set by kb_search for KB_PRUNE
     a.nu_min2_slack = 0.0f;
     if (rescore) {
@@ -845,6 +847,7 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
         r.out = job->recs64;
         r.V = V;
         r.unit = s->q16 ? (s->storage == KB_BF16 ? 0x1p-8 : 0x1p-11) : 0x1p-24;
+        r.nu_key = 0;   // set once the search's list form is known
         r.ulist = job->ulist;
         r.ucount = job->ucount;
     }
@@ -919,6 +922,7 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     else
         e = kb::launch_search(a, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "search kernel");
+    r.nu_key = kb::search_keys(a) ? a.key_bits : 0;
     if (rescore) {
         e = cudaMemsetAsync(job->ucount, 0, sizeof(int), st);
         if (e == cudaSuccess) e = kb::launch_rescore(r, st);

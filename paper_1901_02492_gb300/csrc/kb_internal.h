@@ -185,6 +185,7 @@ struct SearchArgs {
     int *status;             // device status word: KB_ETIMEOUT if a bounded wait gave up
     int by0, nby;            // register-gather kernel: row tiles by0 .. by0 + nby - 1 (nby 0: all)
     int swz;                 // tile order: super-columns of this many tiles (0: row by row)
+    int key_bits;            // bits of a velocity index in a candidate key: smallest b with V <= 2^b
     int cand_only;           // candidates for FP64 rescoring: records carry vidx and nu only (the
                              // rescoring recomputes the sums), so the epilogue gathers nothing
     const float *snr2;       // KB_PRUNE: span bound planes [N][H][(W + 31) / 32 + span / 32] (stack epochs), else null
@@ -192,6 +193,10 @@ struct SearchArgs {
 };
 // register-gather kernel (variant 0 = its default shape, 1..4)
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
+// whether launch_search(a) keeps its candidate lists in key form (a candidate search for
+// the FP64 rescoring): the records' nu are then rounded upwards to 32 - key_bits bits
+// of their order-preserving FP32 encoding
+bool search_keys(const SearchArgs &a);
 // the automatic shape's span for lists of k (pixels per warp, the KB_PRUNE window)
 int search_auto_span(int storage, int k);
 
@@ -231,6 +236,7 @@ struct RescoreArgs {
     int k;                   // results per pixel
     double nu_min;
     double unit;             // unit roundoff of the searched storage (0 for FP32)
+    int nu_key;              // key bits b of the candidates' nu (search_keys), 0: nu as searched
     Rec64 *out;              // [H*W][k]
     int *ulist;              // uncertain pixels (capacity H*W)
     int *ucount;             // their number

@@ -131,6 +131,20 @@ __device__ __forceinline__ bool betterk(unsigned long long ak, int av, unsigned 
     return ak > bk || (ak == bk && av < bv);
 }
 
+// Largest distance from nu to a value in (lo, hi], where hi is a key-form
+// candidate's nu (its order-preserving FP32 encoding a multiple of 2^b) and lo the
+// value 2^b below it in that encoding: a bound on |nu - nu16| for the unrounded
+// reduced-precision score nu16 of the candidate.  Infinite where lo or hi is not
+// finite (such a pixel is never certified).
+__device__ __forceinline__ double key_error(double nu, float hi, int b) {
+    const uint32_t u = __float_as_uint(hi);
+    const uint32_t ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    if (!(fabsf(hi) < INFINITY) || ord < 0x00800000u + (1u << b)) return INFINITY;
+    const uint32_t lo_ord = ord - (1u << b);
+    const float lo = __uint_as_float((lo_ord & 0x80000000u) ? (lo_ord & 0x7FFFFFFFu) : ~lo_ord);
+    return fmax(fabs(nu - (double)hi), fabs(nu - (double)lo));
+}
+
 // One thread per start pixel: FP64 sums of the kc candidates, re-ranking, and the
 // certificate.  A trajectory outside the candidate list had a 16-bit score at
 // most nu16 of the last candidate; the pixel is certified when the k-th
@@ -138,6 +152,9 @@ __device__ __forceinline__ bool betterk(unsigned long long ak, int av, unsigned 
 // than twice the largest 16-bit error seen among the pixel's own candidates
 // plus unit * (1 + |nu|).  Pixels whose candidate list was not full hold every
 // valid trajectory and are certified.  The others go to the repair list.
+// Key-form candidates (a.nu_key) carry nu16 rounded upwards, still an upper bound for
+// the trajectories left out; each candidate's error is then taken over the rounding
+// interval of its key.
 // The running top-K list lives in registers (K >= k, a compile-time bound).
 template <int K>
 __global__ void rescore_kernel(RescoreArgs a) {
@@ -172,7 +189,8 @@ __global__ void rescore_kernel(RescoreArgs a) {
             traj_exact(a, fp, x, y, (int)v, P, F, nobs);
             if (!(F > 0.0)) continue;
             const double nu = nu64(P, F);
-            emax = fmax(emax, fabs(nu - (double)rc.nu));
+            // a key-form nu16 is rounded upwards: the unrounded score lies in (lo, hi]
+            emax = fmax(emax, a.nu_key ? key_error(nu, rc.nu, a.nu_key) : fabs(nu - (double)rc.nu));
             if (!(nu >= a.nu_min)) continue;
             ++n;
             // bubble the candidate down the sorted register list (nu desc, vidx asc),

@@ -252,6 +252,77 @@ __device__ __forceinline__ void flush_queue(const uint2 *q, int n, float *s_ln, 
     }
 }
 
+// Candidate lists of a search that only feeds the FP64 rescoring (KEYS): one
+// 32-bit key per slot.  With b = a.key_bits bits for a velocity index, the high
+// 32 - b bits hold nu's order-preserving FP32 encoding (sign bit flipped for
+// nu >= 0, every bit flipped below) rounded upwards to a multiple of 2^b, and the
+// low b bits hold 2^b - 1 - vidx, so that a larger key is a better (nu desc,
+// vidx asc) candidate and one unsigned compare orders two of them.  The lists
+// take 4 bytes a slot instead of 6, and the rescoring gets an upper bound on the
+// reduced-precision nu of every trajectory left out: the last kept key's value (a
+// trajectory outside has a smaller key, so its rounded-up nu is at most that
+// value).  A key's value hi and the value lo one step of 2^b below it in the
+// encoding bracket the unrounded nu: lo < nu <= hi.  Empty slots are key 0, below
+// the key of every finite nu (whose encoding is at least 2^23).
+constexpr int kKeyMax = 16;   // longest candidate list in key form
+
+__device__ __forceinline__ uint32_t nu_key(float nu, int v, int b) {
+    const uint32_t u = __float_as_uint(nu), m = (1u << b) - 1u;
+    const uint32_t ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    const uint32_t q = (ord >> b) + ((ord & m) ? 1u : 0u);   // finite nu: q << b <= encoding of +inf
+    return (q << b) | (m - (uint32_t)v);
+}
+__device__ __forceinline__ float key_nu(uint32_t key, int b) {
+    const uint32_t ord = key & ~((1u << b) - 1u);
+    return __uint_as_float((ord & 0x80000000u) ? (ord & 0x7FFFFFFFu) : ~ord);
+}
+__device__ __forceinline__ int key_vidx(uint32_t key, int b) {
+    const uint32_t m = (1u << b) - 1u;
+    return (int)(m - (key & m));
+}
+
+// Rank insertion of key ck into the key list of column `col` (k <= kKeyMax slots,
+// best first), if it beats the list's last entry.
+__device__ __forceinline__ void key_insert(uint32_t *s_lk, int col, int k, int LS, uint32_t ck) {
+    uint32_t *lk = s_lk + col;
+    if (!(ck > lk[(k - 1) * LS])) return;
+    uint32_t e[kKeyMax];
+    int pos = 0;
+#pragma unroll
+    for (int i = 0; i < kKeyMax; ++i) {
+        e[i] = i < k ? lk[i * LS] : 0u;
+        pos += (i < k && e[i] > ck) ? 1 : 0;
+    }
+#pragma unroll
+    for (int i = kKeyMax - 1; i > 0; --i)
+        if (i < k && i > pos) lk[i * LS] = e[i - 1];
+    lk[pos * LS] = ck;
+}
+
+// flush_queue for key lists: entries {key, (p * 32 + lane) << 16}
+template <int PX>
+__device__ __forceinline__ void flush_keys(const uint2 *q, int n, uint32_t *s_lk, int k, int LS, int warp, int lane,
+                                           uint32_t *thk) {
+    for (int b = 0; b < n; b += 32) {
+        bool pend = b + lane < n;
+        uint2 e = make_uint2(0u, 0u);
+        if (pend) e = q[b + lane];
+        const int pc = (int)(e.y >> 16);
+        const int col = (pc >> 5) * THREADS + warp * 32 + (pc & 31);
+        for (;;) {   // at most 32 sub-rounds, as in flush_queue
+            if (!__any_sync(0xffffffffu, pend)) break;
+            const unsigned grp = __match_any_sync(0xffffffffu, pend ? pc : 256 + lane);
+            if (pend && lane == __ffs(grp) - 1) {
+                pend = false;
+                key_insert(s_lk, col, k, LS, e.x);
+            }
+            __syncwarp();
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PX; ++p) thk[p] = s_lk[p * THREADS + warp * 32 + lane + (k - 1) * LS];
+}
+
 // One CTA tile (rows by * 8 .. +7, columns bx * SPAN .. +SPAN-1) of one search:
 // the body of both the one-search kernel and the persistent batch kernel.
 // LONG: lists longer than kRankMax (walk insertion, predicated last load batch).
@@ -259,7 +330,8 @@ __device__ __forceinline__ void flush_queue(const uint2 *q, int n, float *s_ln, 
 // (one value per epoch from the span bound planes, kb_prune.cu: L2-resident, one
 // per 32 columns) and skips the velocity when the bound cannot reach nu_min^2
 // (the results do not change).
-template <int STORAGE, int P, int C, bool LONG, typename I, bool PRUNE>
+// KEYS: candidate lists in key form for the FP64 rescoring (a.cand_only, k <= kKeyMax).
+template <int STORAGE, int P, int C, bool LONG, typename I, bool PRUNE, bool KEYS = false>
 __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by, float2 *s_scale, int4 *s_dyn4) {
     typedef Store<STORAGE> St;
     typedef typename St::T T;         // one pixel's (psi, phi)
@@ -282,15 +354,20 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     const int NJP = (NJ + 1) & ~1;   // table row stride: even, so entries pair into 16-byte loads
     float *s_ln = reinterpret_cast<float *>(s_vid + TAB);
     uint16_t *s_lv = reinterpret_cast<uint16_t *>(s_ln + k * LS);
+    uint32_t *s_lk = reinterpret_cast<uint32_t *>(s_vid + TAB);   // KEYS: the lists instead
+    constexpr size_t kSlotBytes = KEYS ? sizeof(uint32_t) : sizeof(float) + sizeof(uint16_t);
     uint2 *s_q = reinterpret_cast<uint2 *>(s_dyn4) +
-                 ((TAB * (sizeof(E) + sizeof(int) + (PRUNE ? sizeof(I) : 0)) +
-                   (size_t)k * LS * (sizeof(float) + sizeof(uint16_t)) + 7) / 8);
+                 ((TAB * (sizeof(E) + sizeof(int) + (PRUNE ? sizeof(I) : 0)) + (size_t)k * LS * kSlotBytes + 7) / 8);
 
     for (int j = threadIdx.x; j < N; j += THREADS)
         s_scale[j] = (STORAGE == KB_F32) ? make_float2(1.0f, 1.0f) : exp_scale(scale_exp(a.scales[a.epoch_of[j]]));
     for (int i = threadIdx.x; i < k * LS; i += THREADS) {
-        s_ln[i] = -INFINITY;
-        s_lv[i] = kNoV;
+        if constexpr (KEYS) {
+            s_lk[i] = 0u;
+        } else {
+            s_ln[i] = -INFINITY;
+            s_lv[i] = kNoV;
+        }
     }
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -313,10 +390,12 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
 
     float thn[PX];
     int thv[PX];
+    uint32_t thk[PX];   // KEYS: the thresholds as keys
 #pragma unroll
     for (int p = 0; p < PX; ++p) {
         thn[p] = -INFINITY;
         thv[p] = kNoV;
+        thk[p] = 0u;
     }
     __syncthreads();
 
@@ -465,13 +544,20 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             // lists are updated when 32 or more are pending (the register thresholds stay
             // conservative meanwhile: a stale threshold only admits more candidates)
             float nu[PX];
+            uint32_t key[PX];
             bool cand[PX];
             bool any = false;
 #pragma unroll
             for (int p = 0; p < PX; ++p) {
                 const float F = acc[p].y;
                 nu[p] = acc[p].x * rsqrtf(F);
-                cand[p] = (F > 0.0f) && (nu[p] >= a.nu_min) && better(nu[p], v, thn[p], thv[p]);
+                if constexpr (KEYS) {
+                    key[p] = nu_key(nu[p], v, a.key_bits);
+                    cand[p] = (F > 0.0f) && (nu[p] >= a.nu_min) && key[p] > thk[p];
+                } else {
+                    key[p] = __float_as_uint(nu[p]);
+                    cand[p] = (F > 0.0f) && (nu[p] >= a.nu_min) && better(nu[p], v, thn[p], thv[p]);
+                }
                 any |= cand[p];
             }
             if (!__any_sync(0xffffffffu, any)) continue;
@@ -479,13 +565,15 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             for (int p = 0; p < PX; ++p) {
                 const unsigned m = __ballot_sync(0xffffffffu, cand[p]);
                 if (cand[p])
-                    q[qn + __popc(m & lt_mask)] =
-                        make_uint2(__float_as_uint(nu[p]), (unsigned)v | ((unsigned)(p * 32 + lane) << 16));
+                    q[qn + __popc(m & lt_mask)] = make_uint2(key[p], (unsigned)v | ((unsigned)(p * 32 + lane) << 16));
                 qn += __popc(m);
             }
             if (qn >= 32) {
                 __syncwarp();
-                flush_queue<PX, LONG>(q, qn, s_ln, s_lv, k, LS, warp, lane, thn, thv);
+                if constexpr (KEYS)
+                    flush_keys<PX>(q, qn, s_lk, k, LS, warp, lane, thk);
+                else
+                    flush_queue<PX, LONG>(q, qn, s_ln, s_lv, k, LS, warp, lane, thn, thv);
                 qn = 0;
             }
         }
@@ -493,9 +581,33 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     if (!active) return;
     if (qn > 0) {
         __syncwarp();
-        flush_queue<PX, LONG>(q, qn, s_ln, s_lv, k, LS, warp, lane, thn, thv);
+        if constexpr (KEYS)
+            flush_keys<PX>(q, qn, s_lk, k, LS, warp, lane, thk);
+        else
+            flush_queue<PX, LONG>(q, qn, s_ln, s_lv, k, LS, warp, lane, thn, thv);
     }
     __syncwarp();
+    if constexpr (KEYS) {
+        // candidates for the rescoring: vidx and the key's nu (an upper bound on the 16-bit nu),
+        // best first; the rescoring recomputes the sums
+#pragma unroll
+        for (int p = 0; p < PX; ++p) {
+            const int x = xw + (G::PIX == 1 ? lane + 32 * p : 2 * lane + 64 * (p / 2) + (p & 1));
+            if (x >= a.W) continue;
+            Rec *out = a.out + ((long long)y * a.W + x) * k;
+            const uint32_t *lk = s_lk + p * THREADS + threadIdx.x;
+            for (int i = 0; i < k; ++i) {
+                const uint32_t kk = lk[i * LS];
+                Rec r;
+                r.psi = 0.0f;
+                r.phi = 0.0f;
+                r.nu = kk ? key_nu(kk, a.key_bits) : -INFINITY;
+                r.meta = kk ? (uint32_t)key_vidx(kk, a.key_bits) : kEmptyVidx;
+                reinterpret_cast<uint4 *>(out)[i] = *reinterpret_cast<uint4 *>(&r);
+            }
+        }
+        return;
+    }
 
     // epilogue: recompute Psi, Phi (same operation sequence) and nobs of the kept entries;
     // every off-image epoch added a zero in the main loop, so it adds a zero here too.
@@ -585,7 +697,7 @@ constexpr int min_ctas_batch() {
     return (STORAGE == KB_F32 ? P <= 2 : P <= 1) ? 3 : 2;
 }
 
-template <int STORAGE, int P, int C, bool LONG, typename I, bool PRUNE>
+template <int STORAGE, int P, int C, bool LONG, typename I, bool PRUNE, bool KEYS>
 __global__ void __launch_bounds__(THREADS, min_ctas<STORAGE, P, C, LONG>()) search_kernel(SearchArgs a) {
     __shared__ float2 s_scale[KB_MAX_EPOCHS];
     extern __shared__ int4 s_dyn4[];
@@ -599,7 +711,7 @@ __global__ void __launch_bounds__(THREADS, min_ctas<STORAGE, P, C, LONG>()) sear
         by = r / w;
         bx = s * a.swz + (r - by * w);
     }
-    search_tile<STORAGE, P, C, LONG, I, PRUNE>(a, bx, a.by0 + by, s_scale, s_dyn4);
+    search_tile<STORAGE, P, C, LONG, I, PRUNE, KEYS>(a, bx, a.by0 + by, s_scale, s_dyn4);
 }
 
 // Persistent batch search: CTAs take (job, tile) work items from an atomic
@@ -628,22 +740,22 @@ __global__ void __launch_bounds__(THREADS, min_ctas_batch<STORAGE, P>())
 }
 
 // dynamic shared memory of a CTA with lists of k entries: the table, the lists and the queues
-template <int STORAGE, int P, typename I, bool PRUNE = false>
+template <int STORAGE, int P, typename I, bool PRUNE = false, bool KEYS = false>
 size_t tile_smem(int k) {
     constexpr int PX = P * Gather<STORAGE>::PIX;
     const size_t base = (size_t)tab_entries<STORAGE>() *
                             (sizeof(Entry<I, STORAGE != KB_F32>) + sizeof(int) + (PRUNE ? sizeof(I) : 0)) +
-                        (size_t)k * THREADS * PX * (sizeof(float) + sizeof(uint16_t));
+                        (size_t)k * THREADS * PX * (KEYS ? sizeof(uint32_t) : sizeof(float) + sizeof(uint16_t));
     return (base + 7) / 8 * 8 + (size_t)WARPS * 32 * (PX + 1) * sizeof(uint2);
 }
 
-template <int STORAGE, int P, int C, bool LONG, typename I, bool PRUNE>
+template <int STORAGE, int P, int C, bool LONG, typename I, bool PRUNE, bool KEYS = false>
 cudaError_t launch_pt(const SearchArgs &a, cudaStream_t st) {
     constexpr int SPAN = 32 * P * Gather<STORAGE>::PIX;
     static_assert(SPAN <= kSpan, "warp span wider than the zero columns");
-    auto kern = search_kernel<STORAGE, P, C, LONG, I, PRUNE>;
+    auto kern = search_kernel<STORAGE, P, C, LONG, I, PRUNE, KEYS>;
     dim3 grid((a.W + SPAN - 1) / SPAN, a.nby > 0 ? a.nby : (a.H + WARPS - 1) / WARPS);
-    const size_t smem = tile_smem<STORAGE, P, I, PRUNE>(a.k);
+    const size_t smem = tile_smem<STORAGE, P, I, PRUNE, KEYS>(a.k);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // Shared-memory carveout: the driver's choice unless the caller sets one
     // (kb_set_search_carveout); it trades resident CTAs against the L1 that the
@@ -660,6 +772,19 @@ template <int STORAGE, int P, int C, typename I, bool PRUNE>
 cudaError_t launch_one(const SearchArgs &a, cudaStream_t st) {
     if (a.k > kRankMax) return launch_pt<STORAGE, P, C, true, I, PRUNE>(a, st);
     return launch_pt<STORAGE, P, C, false, I, PRUNE>(a, st);
+}
+
+// the candidate search of the FP64 rescoring in key form (automatic shape, no pruning)
+template <int STORAGE, int P, int C>
+cudaError_t launch_keys(const SearchArgs &a, cudaStream_t st) {
+    const long long span = (STORAGE == KB_F32 ? 1LL : 2LL) * a.N * a.plane_elems;
+    if (span < (1LL << 31) - 1) return launch_pt<STORAGE, P, C, false, int, false, true>(a, st);
+    return launch_pt<STORAGE, P, C, false, long long, false, true>(a, st);
+}
+
+// key form where it keeps at least 11 of nu's 23 fraction bits (up to 4096 velocities)
+bool use_keys(const SearchArgs &a) {
+    return a.cand_only && !a.snr2 && a.k <= kKeyMax && a.key_bits >= 1 && a.key_bits <= 12;
 }
 
 // 32-bit element offsets when every plane of both phases (and the bound planes) fits
@@ -684,6 +809,7 @@ cudaError_t launch_storage(const SearchArgs &a, cudaStream_t st) {
             case 3: return launch_idx<STORAGE, 4, 8>(a, st);
             default:
                 if (a.snr2) return launch_idx<STORAGE, 2, 8, true>(a, st);
+                if (use_keys(a)) return launch_keys<STORAGE, 2, 8>(a, st);
                 return launch_idx<STORAGE, 2, 8>(a, st);
         }
     } else {
@@ -695,6 +821,7 @@ cudaError_t launch_storage(const SearchArgs &a, cudaStream_t st) {
             // automatic: lists longer than kRankMax take the one-pair shape, whose 512-pixel
             // CTAs keep their lists' shared memory within what 3 CTAs per SM can hold
             default:
+                if (use_keys(a)) return launch_keys<STORAGE, 2, 4>(a, st);
                 if (a.snr2)
                     return a.k > kRankMax ? launch_idx<STORAGE, 1, 4, true>(a, st) : launch_idx<STORAGE, 2, 4, true>(a, st);
                 return a.k > kRankMax ? launch_idx<STORAGE, 1, 4>(a, st) : launch_idx<STORAGE, 2, 4>(a, st);
@@ -781,6 +908,8 @@ cudaError_t launch_search_batch(const SearchArgs *jobs, const int4 *items, int n
         default: return cudaErrorInvalidValue;
     }
 }
+
+bool search_keys(const SearchArgs &a) { return a.variant == 0 && use_keys(a); }
 
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
     switch (a.storage) {

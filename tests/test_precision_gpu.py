@@ -136,3 +136,28 @@ def test_rescored_tiny_and_k16(kb, ctx):
     res = gpu_search(kb, ctx, st2, "bf16", k=16, flags=kb.KB_RESCORE_FP64)
     ref, nu_of = oracle_search(st2, k=16)
     check_topk(res, ref, nu_of)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16", "f32"])
+def test_key_lists_rescore_like_value_lists(kb, ctx, stack16, storage):
+    """The automatic shape keeps the rescoring's candidate lists as 32-bit keys (nu rounded
+    upwards in the key's high bits, the velocity index in its low bits); the value-list shape
+    (variant 1 for 16-bit storage, 2 for FP32) keeps the nu of the search.  Both end in the
+    exact FP64 top-k, so their rescored records must be the same bytes."""
+    st = stack16
+    N, H, W = st.sci.shape
+    out = []
+    for variant in (0, 2 if storage == "f32" else 1):
+        ctx.set_search_variant(variant)
+        try:
+            s = gpu_planes(kb, ctx, st, storage)
+            job = kb.Job(ctx, H, W, N, st.vx.size, st.k, kb.KB_RESCORE_FP64)
+            job.search(s, st.times, st.vx, st.vy, st.k, -math.inf, kb.KB_RESCORE_FP64)
+            out.append((job.results().tobytes(), job.repaired()))
+            torch.cuda.synchronize()
+            job.free()
+            s.free()
+        finally:
+            ctx.set_search_variant(0)
+    assert out[0][0] == out[1][0]
+    print("%s: repaired pixels, key lists %d, value lists %d" % (storage, out[0][1], out[1][1]))
