@@ -29,22 +29,41 @@ namespace kb {
 
 namespace {
 
-// Binary points of the exact coadd sums (see above): the float factors that
-// take a value to units of 2^L (2^-L, exact) and the double factors back (2^L).
+// Binary points of the exact coadd sums (see above): the exponent shifts that
+// take a value to units of 2^L and the double factors back (2^L).
 struct FixedPoint {
-    float to_p, to_f;
+    int sh_p, sh_f;          // -150 - L: a float's exponent field plus this is its shift to units of 2^L
     double from_p, from_f;
 };
 
 // one plane type: every |value| < 2^E, E from the largest per-epoch maximum (bits of
 // a non-negative float order like the float); E kept in [-60, 100] so that 2^-L and
 // 2^L stay normal floats and doubles
-__device__ __forceinline__ void fixed_point_of(unsigned maxbits, float &to, double &from) {
+__device__ __forceinline__ void fixed_point_of(unsigned maxbits, int &sh, double &from) {
     int E = maxbits == 0u ? -60 : (int)((maxbits >> 23) & 0xff) - 126;   // floor(log2 m) + 1
     E = max(-60, min(100, E));
     const int L = E - 56;
-    to = __int_as_float((127 - L) << 23);
+    sh = -150 - L;
     from = __longlong_as_double((long long)(1023 + L) << 52);
+}
+
+// round(x 2^-L) (ties away from zero) for |x| < 2^(L+56), on the integer pipe: with
+// exponent field e and significand m (the implicit bit included when e > 0),
+// |x| = m 2^(max(e, 1) - 150), so |x| 2^-L = m 2^s with s = max(e, 1) + sh <= 32.
+// A shift left is exact; a shift right by r adds 2^(r-1) first (r is clamped at 31,
+// where m + 2^30 < 2^31 shifts to 0, as every |x| 2^-L < 1/2 must).  The float to
+// 64-bit integer conversion instruction would run on the FP64 pipe, which this
+// GPU keeps narrow.
+__device__ __forceinline__ long long fixed_of(float x, int sh) {
+    const uint32_t u = __float_as_uint(x);
+    const int e = (int)((u >> 23) & 0xffu);
+    const uint32_t m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
+    const int s = max(e, 1) + sh;
+    const int r = min(max(-s, 0), 31);
+    const unsigned long long left = (unsigned long long)m << max(s, 0);
+    const uint32_t right = (m + ((1u << r) >> 1)) >> r;
+    const long long v = s >= 0 ? (long long)left : (long long)right;
+    return (u >> 31) ? -v : v;
 }
 
 // The binary points of a stack, from its 2N per-epoch maxima [max |psi|, max phi]
@@ -56,8 +75,8 @@ __device__ __forceinline__ FixedPoint stack_fixed_point(const RescoreArgs &a) {
     for (int i = threadIdx.x; i < 2 * a.N; i += blockDim.x) atomicMax(&s_m[i & 1], a.maxbits[i]);
     __syncthreads();
     FixedPoint fp;
-    fixed_point_of(s_m[0], fp.to_p, fp.from_p);
-    fixed_point_of(s_m[1], fp.to_f, fp.from_f);
+    fixed_point_of(s_m[0], fp.sh_p, fp.from_p);
+    fixed_point_of(s_m[1], fp.sh_f, fp.from_f);
     return fp;
 }
 
@@ -87,8 +106,8 @@ __device__ __forceinline__ void traj_exact(const RescoreArgs &a, const FixedPoin
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            p += __float2ll_rn(pp[q].x * fp.to_p);
-            f += __float2ll_rn(pp[q].y * fp.to_f);
+            p += fixed_of(pp[q].x, fp.sh_p);
+            f += fixed_of(pp[q].y, fp.sh_f);
             nobs += in[q] ? 1 : 0;
         }
     }
@@ -97,8 +116,8 @@ __device__ __forceinline__ void traj_exact(const RescoreArgs &a, const FixedPoin
         const int xx = x + o.x, yy = y + o.y;
         if ((unsigned)xx < (unsigned)a.W && (unsigned)yy < (unsigned)a.H) {
             const float2 pp = __ldg(base + (long long)a.epoch_of[j] * a.plane_elems + (long long)yy * a.pitch + xx);
-            p += __float2ll_rn(pp.x * fp.to_p);
-            f += __float2ll_rn(pp.y * fp.to_f);
+            p += fixed_of(pp.x, fp.sh_p);
+            f += fixed_of(pp.y, fp.sh_f);
             ++nobs;
         }
     }
@@ -145,6 +164,26 @@ __device__ __forceinline__ double key_error(double nu, float hi, int b) {
     return fmax(fabs(nu - (double)hi), fabs(nu - (double)lo));
 }
 
+// Pixel order of the rescoring: one 32 x 4 tile per CTA of 128 threads, tiles
+// walked down strips kStrip pixels wide, strip after strip.  The pixels in flight
+// at one time then form a compact region (about 256 x 300 pixels on a full GPU),
+// and the gathers of their trajectories, which reach up to the largest offset of
+// the velocity grid away, share the L2; in row order they would spread over the
+// image's full width.
+constexpr int kStrip = 256;
+
+long long rescore_tiles(int H, int W) { return (long long)((W + kStrip - 1) / kStrip) * (kStrip / 32) * ((H + 3) / 4); }
+
+// pixel (x, y) of thread t of tile `tile`, and its index y * W + x (-1 outside the image)
+__device__ __forceinline__ long long rescore_pixel(int H, int W, long long tile, int t, int &x, int &y) {
+    const long long per_strip = (long long)(kStrip / 32) * ((H + 3) / 4);
+    const int strip = (int)(tile / per_strip);
+    const long long r = tile - (long long)strip * per_strip;
+    x = strip * kStrip + (int)(r % (kStrip / 32)) * 32 + (t & 31);
+    y = (int)(r / (kStrip / 32)) * 4 + (t >> 5);
+    return (x < W && y < H) ? (long long)y * W + x : -1;
+}
+
 // One thread per start pixel: FP64 sums of the kc candidates, re-ranking, and the
 // certificate.  A trajectory outside the candidate list had a 16-bit score at
 // most nu16 of the last candidate; the pixel is certified when the k-th
@@ -157,12 +196,11 @@ __device__ __forceinline__ double key_error(double nu, float hi, int b) {
 // interval of its key.
 // The running top-K list lives in registers (K >= k, a compile-time bound).
 template <int K>
-__global__ void rescore_kernel(RescoreArgs a) {
+__global__ void __launch_bounds__(128) rescore_kernel(RescoreArgs a) {
     const FixedPoint fp = stack_fixed_point(a);
-    const long long npix = (long long)a.H * a.W;
-    for (long long pix = blockIdx.x * (long long)blockDim.x + threadIdx.x; pix < npix;
-         pix += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(pix / a.W), x = (int)(pix - (long long)y * a.W);
+    int x, y;
+    const long long pix = rescore_pixel(a.H, a.W, blockIdx.x, threadIdx.x, x, y);
+    if (pix >= 0) {
         double lp[K], lf[K];
         unsigned long long lk[K];   // nu as its order key
         int lv[K], lo[K];
@@ -375,9 +413,8 @@ __global__ void expand_kernel(ExpandArgs a) {
 }  // namespace
 
 cudaError_t launch_rescore(const RescoreArgs &a, cudaStream_t st) {
-    long long npix = (long long)a.H * a.W;
-    long long blocks = (npix + 127) / 128;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    const long long blocks = rescore_tiles(a.H, a.W);
+    if (blocks < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (a.k <= 4)
         rescore_kernel<4><<<(int)blocks, 128, 0, st>>>(a);
     else if (a.k <= 8)
