@@ -289,22 +289,29 @@ __global__ void __launch_bounds__(128) rescore_kernel(RescoreArgs a) {
     }
 }
 
-// One warp per uncertain pixel: every velocity's sums in FP64 from the FP32
-// planes (lanes take velocities lane, lane + 32, ...), a sorted top-k per lane,
-// then k rounds of a warp-shuffle arg-max merge (nu desc, vidx asc).
-__global__ void repair_kernel(RescoreArgs a) {
+// One CTA of kRepairThreads per uncertain pixel: every velocity's exact sums from
+// the FP32 planes (thread t takes velocities t, t + 256, ...), a sorted top-k per
+// thread, k rounds of a warp-shuffle arg-max merge (nu desc, vidx asc) per warp
+// into shared memory, then the same merge of the 8 warps' lists by warp 0.  A CTA
+// per pixel, rather than a warp, keeps the pixels in flight few (about 900 on a full
+// GPU) and, in the rescoring's strip order of the list, close together: their
+// trajectories' gathers then share the L2, where thousands of pixels a strip apart
+// would not.
+constexpr int kRepairThreads = 256;
+constexpr int kRepairWarps = kRepairThreads / 32;
+
+__global__ void __launch_bounds__(kRepairThreads) repair_kernel(RescoreArgs a) {
     const FixedPoint fp = stack_fixed_point(a);
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    __shared__ Rec64 s_best[kRepairWarps][KB_MAX_TOPK];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int count = *a.ucount;
-    for (int u = gw; u < count; u += nw) {
+    for (int u = blockIdx.x; u < count; u += gridDim.x) {
         const int pix = a.ulist[u];
         const int y = pix / a.W, x = pix - y * a.W;
         double ln[KB_MAX_TOPK], lp[KB_MAX_TOPK], lf[KB_MAX_TOPK];
         int lv[KB_MAX_TOPK], lo[KB_MAX_TOPK];
         int n = 0;
-        for (int v = lane; v < a.V; v += 32) {
+        for (int v = threadIdx.x; v < a.V; v += kRepairThreads) {
             double P, F;
             int nobs;
             traj_exact(a, fp, x, y, v, P, F, nobs);
@@ -327,9 +334,8 @@ __global__ void repair_kernel(RescoreArgs a) {
             lv[i] = v;
             lo[i] = nobs;
         }
-        // merge: each round the best head among the lanes is emitted and popped
+        // per warp: each round the best head among the lanes goes to s_best[warp][r]
         int head = 0;
-        Rec64 *out = a.out + (long long)pix * a.k;
         for (int r = 0; r < a.k; ++r) {
             double bn = head < n ? ln[head] : -INFINITY;
             int bv = head < n ? lv[head] : INT_MAX;
@@ -344,15 +350,14 @@ __global__ void repair_kernel(RescoreArgs a) {
                     bl = ol;
                 }
             }
-            const bool mine = (bl == lane) && bv != INT_MAX;
-            if (mine) {
+            if (bl == lane && bv != INT_MAX) {
                 Rec64 q;
                 q.psi = lp[head];
                 q.phi = lf[head];
                 q.nu = ln[head];
                 q.vidx = (uint32_t)lv[head];
                 q.nobs = (uint32_t)lo[head];
-                out[r] = q;
+                s_best[warp][r] = q;
                 ++head;
             } else if (lane == 0 && bv == INT_MAX) {
                 Rec64 q;
@@ -361,10 +366,48 @@ __global__ void repair_kernel(RescoreArgs a) {
                 q.nu = -INFINITY;
                 q.vidx = kEmptyVidx;
                 q.nobs = 0;
-                out[r] = q;
+                s_best[warp][r] = q;
             }
             __syncwarp();
         }
+        __syncthreads();
+        // warp 0: lane w < kRepairWarps walks warp w's sorted list
+        if (warp == 0) {
+            int h = 0;
+            Rec64 *out = a.out + (long long)pix * a.k;
+            for (int r = 0; r < a.k; ++r) {
+                const bool has = lane < kRepairWarps && h < a.k && s_best[lane][h].vidx != kEmptyVidx;
+                double bn = has ? s_best[lane][h].nu : -INFINITY;
+                int bv = has ? (int)s_best[lane][h].vidx : INT_MAX;
+                int bl = lane;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double on = __shfl_xor_sync(0xffffffffu, bn, o);
+                    const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+                    if (better64(on, ov, bn, bv)) {
+                        bn = on;
+                        bv = ov;
+                        bl = ol;
+                    }
+                }
+                if (bv == INT_MAX) {
+                    if (lane == 0) {   // fewer than k valid trajectories
+                        Rec64 q;
+                        q.psi = 0.0;
+                        q.phi = 0.0;
+                        q.nu = -INFINITY;
+                        q.vidx = kEmptyVidx;
+                        q.nobs = 0;
+                        out[r] = q;
+                    }
+                } else if (bl == lane) {
+                    out[r] = s_best[lane][h];
+                    ++h;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -425,7 +468,7 @@ cudaError_t launch_rescore(const RescoreArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_repair(const RescoreArgs &a, cudaStream_t st) {
-    repair_kernel<<<152 * 8, 256, 0, st>>>(a);
+    repair_kernel<<<152 * 6, kRepairThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
