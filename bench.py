@@ -118,7 +118,9 @@ def roofline_psi_phi(args, st, ms, nbytes, hbm, clocks):
     arithmetic-bound; the peak is 128 FP32 FMA lanes per SM x 2 FLOP x SM count x the SM clock
     sampled during the run."""
     import torch
-    line = {"bound": "hbm", "kernel": "psi_phi_sep_kernel", "ms_per_launch": ms,
+    K = st.psf.shape[-1]
+    stream = st.sci.shape[2] % 4 == 0 and 3 <= K <= 21   # the library's choice for separable PSFs
+    line = {"bound": "hbm", "kernel": "psi_phi_stream_kernel" if stream else "psi_phi_sep_kernel", "ms_per_launch": ms,
             "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
             "frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     if args.psf == "general":

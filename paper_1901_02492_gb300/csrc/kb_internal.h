@@ -149,6 +149,7 @@ struct PsiPhiArgs {
     int N, H, W, pitch, K;
     long long plane_elems, origin;
     bool separable;
+    int seg;               // rows per CTA of the streaming separable kernel (set by launch_psi_phi)
     const float *taps;     // device taps (see kb_psiphi.cu)
     float2 *out;           // [N][H][pitch]
     unsigned *maxbits;     // [2N] or null

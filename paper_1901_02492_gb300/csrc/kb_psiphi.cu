@@ -20,6 +20,9 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
 
 #include "kb_internal.h"
 
@@ -47,7 +50,7 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 // sigma^2, sigma^2 <= 0, n > bright_max gives (0, 0).  Selects, never 0 * NaN.
 __device__ __forceinline__ float2 weighted(float n, float v, uint8_t m, float bright_max) {
     bool bad = (m != 0) || !isfinite(n) || !isfinite(v) || !(v > 0.0f) || (n > bright_max);
-    float w = bad ? 0.0f : 1.0f / v;
+    float w = bad ? 0.0f : __frcp_rn(v);   // correctly rounded, the same value as 1.0f / v
     float nw = bad ? 0.0f : n * w;
     return make_float2(nw, w);
 }
@@ -204,6 +207,194 @@ __global__ void __launch_bounds__(THREADS) psi_phi_sep_kernel(PsiPhiArgs a) {
         unsigned bp = __reduce_max_sync(0xffffffffu, __float_as_uint(mpsi));
         unsigned bf = __reduce_max_sync(0xffffffffu, __float_as_uint(mphi));
         if ((threadIdx.x & 31) == 0) {
+            atomicMax(a.maxbits + 2 * e, bp);
+            atomicMax(a.maxbits + 2 * e + 1, bf);
+        }
+    }
+}
+
+// ---- separable PSF, streaming form --------------------------------------------
+// One CTA walks a column strip of TX outputs down a segment of a.seg rows of one
+// epoch, in batches of SY input rows:
+//   1. the batch's raw n, sigma^2 (and mask) rows, TX + 2 R4 columns from x0 - R4
+//      (R4 = r rounded up to a multiple of 4), arrive in shared memory by cp.async
+//      16-byte copies (4-byte for the mask), zero-filled outside the image; the
+//      next batch's copies are issued as soon as this one is converted, so they
+//      overlap the two passes;
+//   2. they become (n w, w) pairs (Sec. 2.1.5 weights, by select);
+//   3. the horizontal pass writes the batch's rows into a ring of RING rows;
+//   4. the vertical pass emits the output rows whose K input rows are all in the
+//      ring (one batch behind), so no halo row is ever filtered twice.
+// Every output sums its taps in tap order with one packed FMA each, as in
+// psi_phi_sep_kernel: the two kernels give bit-identical planes.  Requires
+// W % 4 == 0 and 16-byte aligned sci/var (4-byte aligned mask): 16-byte chunks
+// of a row then never straddle the image edge.
+constexpr int SY = 32;           // input rows per batch (= output rows per batch), a multiple of 8
+constexpr int RING = 2 * SY;     // ring rows: one batch plus the 2 r rows of the next (2 r <= SY)
+constexpr int SVR = SY / (THREADS / TX);   // output rows per thread in the vertical pass
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int KT>
+struct StreamGeom {
+    static constexpr int R = KT / 2;
+    static constexpr int R4 = (R + 3) & ~3;
+    static constexpr int OFF = R4 - R;               // first tap column within a staged row
+    static constexpr int AWS = TX + 2 * R4;          // staged columns (a multiple of 4)
+    static constexpr int Q = AWS / 4;                // 16-byte chunks per staged row
+    static constexpr int AST = AWS + 2;              // pair-array row stride in float2 (+16 B: rows
+    static constexpr int BST = TX + 2;               // one bank group apart, so 8 rows load conflict-free)
+    static constexpr int NQ = (OFF + KT + 3 + 1) / 2;   // 16-byte loads for four outputs' inputs
+    // shared bytes: taps | raw n, sigma^2 [SY][AWS] | pairs A [SY][AST] | ring [RING][BST] | mask [SY][AWS]
+    static constexpr size_t taps_bytes = ((4 * KT + 3) & ~3) * sizeof(float);
+    static constexpr size_t raw_bytes = 2 * (size_t)SY * AWS * sizeof(float);
+    static constexpr size_t a_bytes = (size_t)SY * AST * sizeof(float2);
+    static constexpr size_t ring_bytes = (size_t)RING * BST * sizeof(float2);
+    static constexpr size_t mask_bytes = (size_t)SY * AWS;
+    static_assert(2 * R <= SY, "the vertical window must fit one batch behind the ring's head");
+};
+
+// issue the cp.async copies of input rows [yin0, yin0 + SY) of epoch e (one commit group)
+template <int KT>
+__device__ __forceinline__ void stream_stage(const PsiPhiArgs &a, int e, int xs, int yin0, float *rn, float *rv,
+                                             uint8_t *rm) {
+    typedef StreamGeom<KT> G;
+    const size_t npix = (size_t)a.H * a.W;
+    const float *sci = a.sci + e * npix, *var = a.var + e * npix;
+    const uint8_t *msk = a.mask ? a.mask + e * npix : nullptr;
+    for (int i = threadIdx.x; i < SY * G::Q; i += THREADS) {
+        const int t = i / G::Q, q = i - t * G::Q;
+        const int y = yin0 + t, x = xs + 4 * q;   // x is a multiple of 4: a chunk is wholly in or out
+        const bool in = y >= 0 && y < a.H && x >= 0 && x < a.W;
+        const size_t gi = in ? (size_t)y * a.W + x : 0;
+        cp_async16(rn + t * G::AWS + 4 * q, sci + gi, in);
+        cp_async16(rv + t * G::AWS + 4 * q, var + gi, in);
+        if (msk) cp_async4(rm + t * G::AWS + 4 * q, msk + gi, in);
+    }
+    cp_async_commit();
+}
+
+template <int KT>
+__global__ void __launch_bounds__(THREADS) psi_phi_stream_kernel(PsiPhiArgs a) {
+    typedef StreamGeom<KT> G;
+    extern __shared__ float4 smem_raw[];
+    const int e = blockIdx.z;
+    const int x0 = blockIdx.x * TX, xs = x0 - G::R4;
+    const int ys = blockIdx.y * a.seg, ye = min(ys + a.seg, a.H);
+    const int n_out = (ye - ys + SY - 1) / SY;              // output batches
+    const int n_in = (ye - ys + 2 * G::R + SY - 1) / SY;    // input batches (n_in <= n_out + 1)
+
+    float *s_taps = reinterpret_cast<float *>(smem_raw);
+    float *rn = s_taps + G::taps_bytes / sizeof(float);
+    float *rv = rn + SY * G::AWS;
+    float2 *A = reinterpret_cast<float2 *>(rv + SY * G::AWS);
+    float2 *ring = A + SY * G::AST;
+    uint8_t *rm = reinterpret_cast<uint8_t *>(ring + RING * G::BST);
+    const float *taps = a.taps + (size_t)e * 4 * KT;
+    for (int i = threadIdx.x; i < 4 * KT; i += THREADS) s_taps[i] = taps[i];
+    const float2 *ta = reinterpret_cast<const float2 *>(s_taps), *tb = ta + KT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // input batch i holds image rows ys - R + SY i + t; ring row of image row j: (j - ys + R) mod RING
+    stream_stage<KT>(a, e, xs, ys - G::R, rn, rv, rm);
+    float2 *out = a.out + e * a.plane_elems + a.origin;
+    float mpsi = 0.0f, mphi = 0.0f;
+    for (int i = 0; i <= n_out; ++i) {
+        cp_async_wait_all();
+        __syncthreads();   // batch i staged; the previous vertical pass is done with the ring
+        if (i < n_in) {
+            for (int j = threadIdx.x; j < SY * G::Q; j += THREADS) {
+                const int t = j / G::Q, q = j - t * G::Q;
+                const float4 n4 = *reinterpret_cast<const float4 *>(rn + t * G::AWS + 4 * q);
+                const float4 v4 = *reinterpret_cast<const float4 *>(rv + t * G::AWS + 4 * q);
+                const uchar4 m4 = a.mask ? *reinterpret_cast<const uchar4 *>(rm + t * G::AWS + 4 * q)
+                                         : make_uchar4(0, 0, 0, 0);
+                const float2 w0 = weighted(n4.x, v4.x, m4.x, a.bright_max);
+                const float2 w1 = weighted(n4.y, v4.y, m4.y, a.bright_max);
+                const float2 w2 = weighted(n4.z, v4.z, m4.z, a.bright_max);
+                const float2 w3 = weighted(n4.w, v4.w, m4.w, a.bright_max);
+                float4 *dst = reinterpret_cast<float4 *>(A + t * G::AST + 4 * q);
+                dst[0] = make_float4(w0.x, w0.y, w1.x, w1.y);
+                dst[1] = make_float4(w2.x, w2.y, w3.x, w3.y);
+            }
+        }
+        __syncthreads();   // pairs ready, raw buffers free
+        if (i + 1 < n_in) stream_stage<KT>(a, e, xs, ys - G::R + SY * (i + 1), rn, rv, rm);
+        if (i < n_in) {
+            // horizontal: a task is four adjacent outputs of one row; a warp takes 8 rows x 16
+            // columns, the 8 lanes of a 16-byte load phase 8 different rows (conflict-free
+            // with the padded stride)
+            for (int s = 0; s < (SY / 8) * (TX / 16) / (THREADS / 32); ++s) {
+                const int wt = warp + (THREADS / 32) * s;
+                const int t = 8 * (wt % (SY / 8)) + (lane & 7);
+                const int c = 16 * (wt / (SY / 8)) + 4 * (lane >> 3);
+                const float4 *row = reinterpret_cast<const float4 *>(A + t * G::AST + c);
+                float2 in[2 * G::NQ];
+#pragma unroll
+                for (int j = 0; j < G::NQ; ++j) {
+                    const float4 q = row[j];
+                    in[2 * j] = make_float2(q.x, q.y);
+                    in[2 * j + 1] = make_float2(q.z, q.w);
+                }
+                float2 h[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) h[u] = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int d = 0; d < KT; ++d) {
+                    const float2 w = tb[d];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) h[u] = fma2(in[G::OFF + u + d], w, h[u]);
+                }
+                float4 *dst = reinterpret_cast<float4 *>(ring + ((SY * i + t) & (RING - 1)) * G::BST + c);
+                dst[0] = make_float4(h[0].x, h[0].y, h[1].x, h[1].y);
+                dst[1] = make_float4(h[2].x, h[2].y, h[3].x, h[3].y);
+            }
+        }
+        __syncthreads();   // the batch's ring rows written
+        if (i >= 1) {
+            // vertical: output batch o = i - 1, rows ys + SY o + [0, SY); output row y reads ring
+            // rows of image rows y - R .. y + R, i.e. relative rows SY o + row + d, d < KT
+            const int o = i - 1;
+            const int c = threadIdx.x % TX, g = threadIdx.x / TX;
+            const int x = x0 + c;
+#pragma unroll 1
+            for (int row0 = g * SVR; row0 < SY; row0 += (THREADS / TX) * SVR) {
+                float2 acc[SVR];
+#pragma unroll
+                for (int q = 0; q < SVR; ++q) acc[q] = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int d = 0; d < KT + SVR - 1; ++d) {
+                    const float2 v = ring[((SY * o + row0 + d) & (RING - 1)) * G::BST + c];
+#pragma unroll
+                    for (int q = 0; q < SVR; ++q)
+                        if (d - q >= 0 && d - q < KT) acc[q] = fma2(v, ta[d - q], acc[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < SVR; ++q) {
+                    const int y = ys + SY * o + row0 + q;
+                    if (y < ye && x < a.W) {
+                        out[(long long)y * a.pitch + x] = acc[q];
+                        track_max(a, acc[q], mpsi, mphi);
+                    }
+                }
+            }
+        }
+    }
+    if (a.maxbits) {
+        unsigned bp = __reduce_max_sync(0xffffffffu, __float_as_uint(mpsi));
+        unsigned bf = __reduce_max_sync(0xffffffffu, __float_as_uint(mphi));
+        if (lane == 0) {
             atomicMax(a.maxbits + 2 * e, bp);
             atomicMax(a.maxbits + 2 * e + 1, bf);
         }
@@ -399,9 +590,47 @@ cudaError_t launch_gen(const PsiPhiArgs &a, dim3, size_t, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// streaming separable kernel: segments of up to 512 rows (a 2 r-row warm-up each,
+// 3 % of 512 for K = 17), one CTA per (strip, segment, epoch)
+template <int KT>
+cudaError_t launch_stream(const PsiPhiArgs &a0, cudaStream_t st) {
+    typedef StreamGeom<KT> G;
+    PsiPhiArgs a = a0;
+    a.seg = std::min(512, (a.H + SY - 1) / SY * SY);
+    const dim3 grid((a.W + TX - 1) / TX, (a.H + a.seg - 1) / a.seg, a.N);
+    const size_t smem = G::taps_bytes + G::raw_bytes + G::a_bytes + G::ring_bytes + (a.mask ? G::mask_bytes : 0);
+    cudaError_t err = cudaFuncSetAttribute(psi_phi_stream_kernel<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    psi_phi_stream_kernel<KT><<<grid, THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// the streaming kernel's 16-byte row chunks need W % 4 == 0 and aligned planes; other
+// cases take the tile kernel
+static bool stream_ok(const PsiPhiArgs &a) {
+    return a.separable && a.K >= 3 && a.K <= 21 && (a.K & 1) && a.W % 4 == 0 && ((uintptr_t)a.sci & 15) == 0 &&
+           ((uintptr_t)a.var & 15) == 0 && (!a.mask || ((uintptr_t)a.mask & 3) == 0);
+}
+
 cudaError_t launch_psi_phi(const PsiPhiArgs &a, cudaStream_t st) {
     dim3 grid((a.W + TX - 1) / TX, (a.H + TY - 1) / TY, a.N);
     size_t smem = psi_phi_smem(a.K, a.separable);
+    if (stream_ok(a)) {
+        switch (a.K) {
+            case 3: return launch_stream<3>(a, st);
+            case 5: return launch_stream<5>(a, st);
+            case 7: return launch_stream<7>(a, st);
+            case 9: return launch_stream<9>(a, st);
+            case 11: return launch_stream<11>(a, st);
+            case 13: return launch_stream<13>(a, st);
+            case 15: return launch_stream<15>(a, st);
+            case 17: return launch_stream<17>(a, st);
+            case 19: return launch_stream<19>(a, st);
+            case 21: return launch_stream<21>(a, st);
+            default: break;
+        }
+    }
     if (a.separable) {
         switch (a.K) {   // the PSF sides of the workloads get fully unrolled taps
             case 3: return launch_sep<3>(a, grid, smem, st);

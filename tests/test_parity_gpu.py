@@ -96,6 +96,36 @@ def test_psi_phi_planes_f32(kb, ctx, K, sep, mask, bright):
     s.free()
 
 
+@pytest.mark.parametrize("K,mask,H,W", [(3, False, 77, 152), (7, True, 77, 152), (17, True, 77, 152),
+                                         (15, False, 45, 200), (17, False, 1100, 68), (21, False, 45, 200)])
+def test_psi_phi_stream_kernel(kb, ctx, K, mask, H, W):
+    """Separable PSFs (K <= 21) on widths divisible by 4 take the streaming kernel (column
+    strips walked down segments of up to 512 rows, in batches of 32 rows); other widths the
+    tile kernel.  Planes against the oracle, and bit for bit against the tile kernel: the
+    same stack with one more column, of NaN variance (weight 0, like the outside of the
+    image), goes to the tile kernel."""
+    st = synth.small_stack(300 + K, 3, H, W, K=K, sigma=max(K / 6.0, 0.5), var_lo=50, var_hi=150,
+                           nan_frac=0.01, mask_frac=0.02 if mask else 0.0, flux=400.0)
+    N = st.sci.shape[0]
+    planes = []
+    for extra in (0, 1):
+        sci = np.concatenate([st.sci, np.zeros((N, H, extra), np.float32)], axis=2)
+        var = np.concatenate([st.var, np.full((N, H, extra), np.nan, np.float32)], axis=2)
+        msk = None if st.mask is None else np.concatenate([st.mask, np.zeros((N, H, extra), np.uint8)], axis=2)
+        s = kb.Stack(ctx, N, H, W + extra, "f32")
+        s.make_psi_phi(to_dev(sci), to_dev(var), to_dev(msk) if msk is not None else None, st.psf)
+        out = torch.empty((N, H, W + extra, 2), dtype=torch.float32, device=DEV)
+        s.copy_planes(0, out)
+        planes.append(out.cpu().numpy()[:, :, :W])
+        s.free()
+    assert planes[0].tobytes() == planes[1].tobytes()
+    psi, phi = oracle.psi_phi(st.sci, st.var, st.mask, st.psf)
+    g = planes[0]
+    assert np.all(np.abs(g[..., 0] - psi) <= 1e-5 * (np.abs(psi) + np.sqrt(phi)) + 1e-30)
+    assert np.all(np.abs(g[..., 1] - phi) <= 1e-5 * phi + 1e-30)
+    assert np.array_equal(g[..., 1] == 0, phi == 0)
+
+
 # ------------------------------------------------------------------ stage (b), FP32
 
 @pytest.mark.parametrize("k", [1, 4, 8, 16])
