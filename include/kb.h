@@ -103,12 +103,29 @@ const char *kb_last_error(const kb_ctx *ctx);
 /* Bytes of device memory currently held by the context's stacks and jobs. */
 size_t kb_hbm_in_use(const kb_ctx *ctx);
 
+/* Bounds words of a KB_DEBUG build (libkb_debug.so, built by
+ * paper_1901_02492_gb300.build.build(debug=True)).  In such a build every gather
+ * of the search kernels from the psi/phi planes, every write of their offset
+ * tables in shared memory and every list column they insert into is checked
+ * against its extent; an access outside is skipped (a gather reads zero) and the
+ * first one since the last reset is recorded, never trapped.
+ * kb_debug_build: 1 in a KB_DEBUG build, 0 otherwise.
+ * kb_debug_word: *word = (site << 56) | offset of that first access (0 if none;
+ * sites: 1 reference-epoch gather, 2 batched gather, 3 remainder gather,
+ * 4 predicated gather, byte offsets from the planes' base; 5 table entry,
+ * 6 list column, element indices); reset != 0 clears it afterwards.  It
+ * synchronises the device.  KB_EINVAL in a build without KB_DEBUG or for a
+ * NULL argument. */
+int kb_debug_build(void);
+int kb_debug_word(kb_ctx *ctx, unsigned long long *word, int reset);
+
 /* Tuning hook: force the search kernel used by later kb_search calls of this
  * context; results do not depend on the choice.
- *   0      automatic: the register-gather kernel in its default shape
+ *   0      automatic: the register-gather kernel in its default shape, (2,8) for
+ *          FP32 and (2,4) for 16-bit storage ((1,4) for value lists longer than 8)
  *   1..4   register-gather kernel, (loads per lane, epochs per load batch) =
  *          (4,4), (2,4), (4,8), (2,8) for FP32 and (2,4), (1,4), (2,8), (1,8)
- *          for 16-bit storage, whose loads are pixel pairs; default (2,8) / (1,8)
+ *          for 16-bit storage, whose loads are pixel pairs
  *   5..8   TMA-pipelined kernel, (pixels per lane, stages, epochs per wait
  *          group) = (2,8,2), (2,12,4), (4,8,2), (4,12,4)
  * KB_EINVAL for other values. */

@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libkb.so")
+# KB_LIBRARY selects another build of the same library, e.g. libkb_debug.so
+LIB_PATH = os.environ.get("KB_LIBRARY") or os.path.join(_HERE, "libkb.so")
 
 KB_OK, KB_EINVAL, KB_ENOMEM, KB_ECUDA, KB_ETIMEOUT, KB_ERANGE = 0, 1, 2, 3, 4, 5
 KB_F32, KB_BF16, KB_F16 = 0, 1, 2
@@ -44,8 +45,8 @@ assert MOMENTS_DTYPE.itemsize == 56
 KB_STAMP_MEAN, KB_STAMP_MEDIAN, KB_MAX_STAMP_RADIUS = 0, 1, 15
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError("libkb.so is not built (run paper_1901_02492_gb300.build.build() or "
-                      "__graft_entry__.build()); there is no fallback path")
+    raise ImportError("%s is not built (run paper_1901_02492_gb300.build.build() or "
+                      "__graft_entry__.build()); there is no fallback path" % LIB_PATH)
 
 _lib = ctypes.CDLL(LIB_PATH)
 _P = ctypes.c_void_p
@@ -63,6 +64,8 @@ _kb_init = _sig("kb_init", _i32, [ctypes.POINTER(_P), _i32, _sz])
 _kb_destroy = _sig("kb_destroy", None, [_P])
 _kb_last_error = _sig("kb_last_error", ctypes.c_char_p, [_P])
 _kb_hbm_in_use = _sig("kb_hbm_in_use", _sz, [_P])
+_kb_debug_build = _sig("kb_debug_build", _i32, [])
+_kb_debug_word = _sig("kb_debug_word", _i32, [_P, _P, _i32])
 _kb_set_search_variant = _sig("kb_set_search_variant", _i32, [_P, _i32])
 _kb_set_search_carveout = _sig("kb_set_search_carveout", _i32, [_P, _i32])
 _kb_set_search_swizzle = _sig("kb_set_search_swizzle", _i32, [_P, _i32])
@@ -97,7 +100,8 @@ _kb_batch_run = _sig("kb_batch_run", _i32, [_P, _P])
 _kb_batch_groups = _sig("kb_batch_groups", _i32, [_P, _P, _i32, ctypes.POINTER(_i32)])
 _kb_batch_free = _sig("kb_batch_free", None, [_P])
 
-EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_set_search_variant",
+EXPORTED = ["kb_init", "kb_destroy", "kb_last_error", "kb_hbm_in_use", "kb_debug_build", "kb_debug_word",
+            "kb_set_search_variant",
             "kb_set_search_carveout", "kb_set_search_swizzle", "kb_set_search_order", "kb_measure_gather_peak", "kb_stack_create", "kb_stack_free",
             "kb_make_psi_phi", "kb_stack_copy_planes", "kb_stack_scales", "kb_offsets", "kb_job_create",
             "kb_job_free", "kb_search", "kb_job_wait", "kb_job_repaired", "kb_results", "kb_make_psi_phi_static",
@@ -189,6 +193,13 @@ class Context:
     @property
     def hbm_in_use(self) -> int:
         return int(_kb_hbm_in_use(self.h))
+
+    def debug_word(self, reset: bool = True) -> int:
+        """KB_DEBUG builds: the first out-of-bounds access the search kernels met,
+        (site << 56) | offset, 0 if none (kb_debug_word)."""
+        w = ctypes.c_ulonglong(0)
+        self.check(_kb_debug_word(self.h, ctypes.byref(w), 1 if reset else 0))
+        return int(w.value)
 
     def cluster(self, cand, w_pos, w_vel, eps, min_samples, core=False, stream=None):
         """Sec. 3.3 DBSCAN de-duplication of device kb_result records `cand` (a CUDA tensor
@@ -307,6 +318,11 @@ def make_psi_phi_static(sci, var, mask, psf, out, bright_max=math.inf, stream=No
                                  float(bright_max), _ptr(out), _stream(stream))
     if rc != KB_OK:
         raise KBError(rc, "kb_make_psi_phi_static failed")
+
+
+def debug_build() -> bool:
+    """Whether the loaded library is a KB_DEBUG build (kb_debug_build)."""
+    return bool(_kb_debug_build())
 
 
 def estimate_bytes(N, H, W, storage, K, V, topk, flags=0):

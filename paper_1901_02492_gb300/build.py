@@ -2,7 +2,10 @@
 
 Each translation unit under csrc/ is compiled by nvcc in parallel for
 sm_103a only, then linked into paper_1901_02492_gb300/libkb.so next to this
-file.  No cmake, no torch extension machinery.
+file.  No cmake, no torch extension machinery.  build(debug=True) makes
+libkb_debug.so instead: the same sources with -DKB_DEBUG, whose search kernels
+check every gather and shared-memory index and record the first one out of
+bounds (kb_debug_word) instead of making it.
 """
 from __future__ import annotations
 
@@ -17,6 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkb.so")
 STAMP = LIB + ".sha256"     # digest of the sources and flags the library was built from
+LIB_DEBUG = os.path.join(HERE, "libkb_debug.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -33,12 +37,16 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(INCLUDE, "kb.h"), __file__]
 
 
-def source_digest() -> str:
+def _flags(debug: bool):
+    return FLAGS + (["-DKB_DEBUG"] if debug else [])
+
+
+def source_digest(debug: bool = False) -> str:
     """sha256 over every input of the build (sources, headers, this script) and the
     compiler flags.  File times are not used: a copied tree keeps the times of the
     copy, so a library newer than changed sources would otherwise be reused."""
     h = hashlib.sha256()
-    h.update(" ".join([NVCC] + ARCH + FLAGS).encode())
+    h.update(" ".join([NVCC] + ARCH + _flags(debug)).encode())
     for d in sorted(set(_deps())):
         h.update(os.path.relpath(d, os.path.dirname(HERE)).encode())
         with open(d, "rb") as f:
@@ -46,24 +54,30 @@ def source_digest() -> str:
     return h.hexdigest()
 
 
-def up_to_date() -> bool:
-    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
+def up_to_date(debug: bool = False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    stamp = lib + ".sha256"
+    if not (os.path.exists(lib) and os.path.exists(stamp)):
         return False
-    with open(STAMP) as f:
-        return f.read().strip() == source_digest()
+    with open(stamp) as f:
+        return f.read().strip() == source_digest(debug)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libkb.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    digest = source_digest()
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile and link libkb.so (libkb_debug.so with debug=True); returns its path."""
+    lib = LIB_DEBUG if debug else LIB
+    stamp = lib + ".sha256"
+    if not force and up_to_date(debug):
+        return lib
+    digest = source_digest(debug)
+    bdir = BUILD + ("_debug" if debug else "")
+    os.makedirs(bdir, exist_ok=True)
     srcs = _sources()
+    flags = _flags(debug)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [NVCC] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+        cmd = [NVCC] + ARCH + flags + ["-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -77,16 +91,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in results:
             print(log)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    with open(STAMP + ".tmp%d" % os.getpid(), "w") as f:
+    os.replace(tmp, lib)
+    with open(stamp + ".tmp%d" % os.getpid(), "w") as f:
         f.write(digest + "\n")
-    os.replace(STAMP + ".tmp%d" % os.getpid(), STAMP)
-    return LIB
+    os.replace(stamp + ".tmp%d" % os.getpid(), stamp)
+    return lib
 
 
 if __name__ == "__main__":

@@ -293,6 +293,23 @@ int kb_set_search_variant(kb_ctx *ctx, int variant) {
     return KB_OK;
 }
 
+int kb_debug_build(void) {
+#ifdef KB_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int kb_debug_word(kb_ctx *ctx, unsigned long long *word, int reset) {
+    if (!ctx || !word) return fail(ctx, KB_EINVAL, "kb_debug_word: null argument");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = kb::debug_word(word, reset != 0);
+    if (e == cudaErrorNotSupported) return fail(ctx, KB_EINVAL, "kb_debug_word: not a KB_DEBUG build");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kb_debug_word");
+    return KB_OK;
+}
+
 // ---- stacks ------------------------------------------------------------------
 
 int kb_stack_create(kb_ctx *ctx, int N, int H, int W, int storage, kb_stack **out) {
@@ -358,6 +375,7 @@ void kb_stack_free(kb_stack *s) {
 
 int kb_make_psi_phi(kb_stack *s, const float *sci, const float *var, const uint8_t *mask, const float *psf, int K,
                     float bright_max, void *stream) {
+    kb::NvtxRange nvtx("kb_make_psi_phi");
     if (!s) return KB_EINVAL;
     kb_ctx *ctx = s->ctx;
     if (!sci || !var || !psf) return fail(ctx, KB_EINVAL, "kb_make_psi_phi: sci, var and psf are required");
@@ -801,6 +819,7 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
     a.plane_elems = s->L.plane_elems;
     a.origin = s->L.origin;
     a.phase1 = (long long)N * s->L.plane_elems;
+    a.planes_elems = (s->q16 ? 2LL : 1LL) * N * s->L.plane_elems;
     a.pad_x = s->L.pad_x;
     a.H = s->H;
     a.W = s->W;
@@ -862,6 +881,7 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
 
 int kb_search(kb_job *job, const kb_stack *s, const double *times, const double *vx, const double *vy, int V,
               int topk, float nu_min, int flags, void *stream) {
+    kb::NvtxRange nvtx("kb_search");
     if (!job) return KB_EINVAL;
     kb_ctx *ctx = job->ctx;
     DeviceGuard g(ctx->device);
@@ -924,6 +944,7 @@ int kb_search(kb_job *job, const kb_stack *s, const double *times, const double 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "search kernel");
     r.nu_key = kb::search_keys(a) ? a.key_bits : 0;
     if (rescore) {
+        kb::NvtxRange nvtx_r("kb_rescore");
         e = cudaMemsetAsync(job->ucount, 0, sizeof(int), st);
         if (e == cudaSuccess) e = kb::launch_rescore(r, st);
         if (e == cudaSuccess) e = kb::launch_repair(r, st);
@@ -1214,6 +1235,7 @@ int kb_batch_create(kb_ctx *ctx, int count, const kb_batch_item *items, int flag
 }
 
 int kb_batch_run(kb_batch *b, void *stream) {
+    kb::NvtxRange nvtx("kb_batch_run");
     if (!b) return KB_EINVAL;
     kb_ctx *ctx = b->ctx;
     DeviceGuard dg(ctx->device);
@@ -1409,6 +1431,7 @@ int kb_results_compact_async(kb_job *job, kb_result_compact *out, size_t capacit
 
 int kb_filter_lightcurves(kb_job *job, const kb_stack *s, double nsigma, kb_filtered *out, size_t capacity,
                           size_t *n_written, void *stream) {
+    kb::NvtxRange nvtx("kb_filter_lightcurves");
     if (!job) return KB_EINVAL;
     kb_ctx *ctx = job->ctx;
     if (job->k == 0) return fail(ctx, KB_EINVAL, "kb_filter_lightcurves: no search has run on this job");
@@ -1447,6 +1470,7 @@ int kb_filter_lightcurves(kb_job *job, const kb_stack *s, double nsigma, kb_filt
 int kb_stamps(kb_job *job, const float *sci, const uint8_t *mask, int N, int H, int W, const int32_t *x0,
               const int32_t *y0, const int32_t *vidx, int n, int radius, int mode, double aperture,
               const kb_moment_cuts *cuts, float *stamps, kb_moments *moments, void *stream) {
+    kb::NvtxRange nvtx("kb_stamps");
     if (!job) return KB_EINVAL;
     kb_ctx *ctx = job->ctx;
     if (job->k == 0) return fail(ctx, KB_EINVAL, "kb_stamps: no search has run on this job");
@@ -1503,6 +1527,7 @@ int kb_stamps(kb_job *job, const float *sci, const uint8_t *mask, int N, int H, 
 
 int kb_cluster(kb_ctx *ctx, const kb_result *cand, size_t n, const kb_cluster_params *p, int32_t *label,
                uint8_t *keep, uint8_t *core, size_t *n_groups, void *stream) {
+    kb::NvtxRange nvtx("kb_cluster");
     if (!ctx || !p) return fail(ctx, KB_EINVAL, "kb_cluster: null context or parameters");
     if (n_groups) *n_groups = 0;
     if (n > ((size_t)1 << 29))

@@ -12,7 +12,20 @@
 
 #include "../../include/kb.h"
 
+// NVTX ranges around the library's entry points (header-only NVTX3: without a
+// tool attached, a push or pop is a check of one function pointer).  Profilers
+// attribute the kernels an entry point launches to its range, e.g.
+// ncu --nvtx --nvtx-include "kb_search/".
+#include <nvtx3/nvToolsExt.h>
+
 namespace kb {
+
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Packed 16-bit (psi, phi) pair: low half psi, high half phi.
 typedef uint32_t pair16;
@@ -169,6 +182,7 @@ struct SearchArgs {
     long long plane_elems;   // elements per plane (layout)
     long long origin;        // element of pixel (0, 0) within a plane
     long long phase1;        // element offset of the 16-bit phase-1 copy (N * plane_elems)
+    long long planes_elems;  // elements (pixels) of the planes' allocation, both phases (KB_DEBUG checks)
     int pad_x;               // zero columns left of every row (layout)
     int H, W, pitch, N;      // N epochs, in time order through epoch_of
     int n0;                  // leading time-ordered epochs at offset 0 for every velocity
@@ -194,6 +208,10 @@ struct SearchArgs {
 };
 // register-gather kernel (variant 0 = its default shape, 1..4)
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
+// KB_DEBUG builds: the first out-of-bounds access the search kernels recorded
+// ((site << 56) | offset, 0 if none), then cleared if reset; cudaErrorNotSupported
+// in other builds
+cudaError_t debug_word(unsigned long long *word, bool reset);
 // whether launch_search(a) keeps its candidate lists in key form (a candidate search for
 // the FP64 rescoring): the records' nu are then rounded upwards to 32 - key_bits bits
 // of their order-preserving FP32 encoding

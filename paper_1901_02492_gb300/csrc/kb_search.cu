@@ -56,7 +56,68 @@
 
 namespace kb {
 
+#ifdef KB_DEBUG
+// KB_DEBUG: the first out-of-bounds access of the search kernels, (site << 56) | offset
+__device__ unsigned long long g_debug_word;
+#endif
+
+cudaError_t debug_word(unsigned long long *word, bool reset) {
+#ifdef KB_DEBUG
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(word, g_debug_word, sizeof(*word));
+    if (e == cudaSuccess && reset) {
+        const unsigned long long zero = 0;
+        e = cudaMemcpyToSymbol(g_debug_word, &zero, sizeof(zero));
+    }
+    return e;
+#else
+    (void)word;
+    (void)reset;
+    return cudaErrorNotSupported;
+#endif
+}
+
 namespace {
+
+#ifdef KB_DEBUG
+__device__ __noinline__ void debug_record(int site, long long at) {
+    atomicCAS(&g_debug_word, 0ull, ((unsigned long long)site << 56) | ((unsigned long long)at & 0x00ffffffffffffffull));
+}
+#endif
+
+// One load of a gather from the planes.  KB_DEBUG builds check that it lies inside
+// the planes' allocation (elems pixels of type T from `planes`); one outside is
+// recorded with its site and read as zero.
+template <typename LT, typename T>
+__device__ __forceinline__ LT gather(const LT *src, const T *planes, long long elems, int site) {
+#ifdef KB_DEBUG
+    const long long at = (long long)((const char *)src - (const char *)planes);
+    if (at < 0 || at + (long long)sizeof(LT) > elems * (long long)sizeof(T)) {
+        debug_record(site, at);
+        return LT{};
+    }
+#else
+    (void)planes;
+    (void)elems;
+    (void)site;
+#endif
+    return __ldg(src);
+}
+
+// KB_DEBUG builds: index i must lie in [0, n) (site 5: offset-table entry, 6: list column)
+__device__ __forceinline__ bool debug_in(long long i, long long n, int site) {
+#ifdef KB_DEBUG
+    if (i < 0 || i >= n) {
+        debug_record(site, i);
+        return false;
+    }
+#else
+    (void)i;
+    (void)n;
+    (void)site;
+#endif
+    return true;
+}
 
 using namespace dev;
 
@@ -239,7 +300,7 @@ __device__ __forceinline__ void flush_queue(const uint2 *q, int n, float *s_ln, 
             const unsigned grp = __match_any_sync(0xffffffffu, pend ? pc : 256 + lane);
             if (pend && lane == __ffs(grp) - 1) {
                 pend = false;
-                list_insert<LONG>(s_ln, s_lv, col, k, LS, cn, cv);
+                if (debug_in(col, LS, 6)) list_insert<LONG>(s_ln, s_lv, col, k, LS, cn, cv);
             }
             __syncwarp();
         }
@@ -314,7 +375,7 @@ __device__ __forceinline__ void flush_keys(const uint2 *q, int n, uint32_t *s_lk
             const unsigned grp = __match_any_sync(0xffffffffu, pend ? pc : 256 + lane);
             if (pend && lane == __ffs(grp) - 1) {
                 pend = false;
-                key_insert(s_lk, col, k, LS, e.x);
+                if (debug_in(col, LS, 6)) key_insert(s_lk, col, k, LS, e.x);
             }
             __syncwarp();
         }
@@ -407,7 +468,8 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
         for (int j = 0; j < n0; ++j) {
             const LT *src = reinterpret_cast<const LT *>(planes + (long long)a.epoch_of[j] * a.plane_elems + tb);
 #pragma unroll
-            for (int p = 0; p < P; ++p) G::acc(acc0 + p * G::PIX, __ldg(src + 32 * p), sc_of(s_scale[j]));
+            for (int p = 0; p < P; ++p)
+                G::acc(acc0 + p * G::PIX, gather(src + 32 * p, planes, a.planes_elems, 1), sc_of(s_scale[j]));
         }
     }
 
@@ -445,7 +507,7 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             e.idx = (I)g;
             e.info = mask;
             if constexpr (STORAGE != KB_F32) e.sc = sc_of(exp_scale(scale_exp(a.scales[ep])));
-            s_tab[vi * NJP + jj] = e;
+            if (debug_in(vi * NJP + jj, TAB, 5)) s_tab[vi * NJP + jj] = e;
             if constexpr (PRUNE)   // the CTA's first row; a warp adds warp * RW
                 s_rid[vi * NJP + jj] = mask ? (I)(((long long)ep * a.H + y0 + oy) * RW + ((xw + ox) >> 5) + SPAN / 32)
                                             : (I)0;
@@ -489,7 +551,7 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
                             sx[q2 + h] = entry_sc(t[h]);
                             const LT *src = reinterpret_cast<const LT *>(planes_t + ((t[h].info & wbit) ? t[h].idx : zidx));
 #pragma unroll
-                            for (int p = 0; p < P; ++p) val[q2 + h][p] = __ldg(src + 32 * p);
+                            for (int p = 0; p < P; ++p) val[q2 + h][p] = gather(src + 32 * p, planes, a.planes_elems, 2);
                         }
                     }
 #pragma unroll
@@ -503,7 +565,7 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
                     const LT *src = reinterpret_cast<const LT *>(planes_t + ((t.info & wbit) ? t.idx : zidx));
                     LT val[P];
 #pragma unroll
-                    for (int p = 0; p < P; ++p) val[p] = __ldg(src + 32 * p);
+                    for (int p = 0; p < P; ++p) val[p] = gather(src + 32 * p, planes, a.planes_elems, 3);
                     const uint32_t sc = entry_sc(t);
 #pragma unroll
                     for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[p], sc);
@@ -526,7 +588,8 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
                                     const LT *src = reinterpret_cast<const LT *>(
                                         planes_t + ((t[h].info & wbit) ? t[h].idx : zidx));
 #pragma unroll
-                                    for (int p = 0; p < P; ++p) val[q2 + h][p] = __ldg(src + 32 * p);
+                                    for (int p = 0; p < P; ++p)
+                                        val[q2 + h][p] = gather(src + 32 * p, planes, a.planes_elems, 4);
                                 }
                             }
                         }

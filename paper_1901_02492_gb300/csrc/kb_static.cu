@@ -54,6 +54,7 @@ bool is_device(const void *p) {
 
 extern "C" int kb_make_psi_phi_static(const float *sci, const float *var, const uint8_t *mask, const float *psf,
                                       int N, int H, int W, int K, float bright_max, float *out, void *stream) {
+    kb::NvtxRange nvtx("kb_make_psi_phi_static");
     cudaStream_t st = (cudaStream_t)stream;
     // first, before any other CUDA call: a capturing stream is refused (see above)
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;

@@ -13,6 +13,17 @@ velocity grid).  Its life:
           -> done     (its memory and slot are released; waiting requests are
                        admitted in the same pass)
 
+A request can be cancelled at any stage, by `Scheduler.cancel(id)` from another
+thread or by its `cancel_at` time: waiting, it leaves the queue; resident, its
+device memory is released (`backend.release`) without running; running, its
+kernels finish (nothing stops a launch in flight) and its result is dropped.
+Its Completion then has status "cancelled".  A request whose admission fails
+completes with status "failed" and the error, and the loop goes on with the
+others; when the failure is a shortage of device memory (the backend raises
+OutOfMemory, e.g. the budget's estimate missed fragmentation) while other
+requests hold memory, the request instead goes back to the head of the queue
+and is admitted again after the next completion.
+
 Admission is first-come first-served on the request's device footprint
 (kb_estimate_bytes: its psi/phi planes and search buffers), so the budget is never exceeded
 and a large request is not starved by smaller ones behind it.  Requests that
@@ -28,10 +39,15 @@ from __future__ import annotations
 import collections
 import dataclasses
 import math
+import threading
 import time
 from typing import Any, Callable, List
 
 import numpy as np
+
+
+class OutOfMemory(MemoryError):
+    """Raised by a backend's admit when device memory is short right now."""
 
 
 @dataclasses.dataclass
@@ -46,6 +62,7 @@ class Request:
     topk: int
     payload: Any = None       # what the backend needs (images, PSF, times, grid)
     nbytes: int = 0           # device footprint, set by the backend's estimate
+    cancel_at: float = math.inf   # seconds after the start of the run: cancelled if not finished by then
 
 
 @dataclasses.dataclass
@@ -56,6 +73,7 @@ class Completion:
     started: float
     finished: float
     result: Any = None
+    status: str = "done"      # "done", "cancelled" (admitted / started are nan where not reached) or "failed"
 
     @property
     def latency(self) -> float:
@@ -84,6 +102,13 @@ class Scheduler:
         self.policy = policy
         self.max_wait = float(max_wait)
         self.peak_bytes = 0
+        self._lock = threading.Lock()
+        self._cancel = set()
+
+    def cancel(self, request_id: int):
+        """Cancel a request (any thread, any time during or before `run`)."""
+        with self._lock:
+            self._cancel.add(int(request_id))
 
     def _next(self, resident, now):
         """Index in `resident` of the request to dispatch next."""
@@ -110,10 +135,34 @@ class Scheduler:
         free_slots = list(range(self.slots))[::-1]
         in_use = 0
         out: List[Completion] = []
+        deadlines = any(math.isfinite(r.cancel_at) for r in requests)
+        dropping = set()                               # running requests whose result is dropped
+        retry_blocked = False                          # an admission ran out of memory: wait for a completion
         t0 = clock()
         while pending or waiting or resident or running:
             now = clock() - t0
             progressed = False
+            with self._lock:
+                ids = set(self._cancel)
+            if ids or deadlines:
+                def gone(r):
+                    return r.id in ids or now >= r.cancel_at
+                for q in (pending, waiting):
+                    for r in [r for r in q if gone(r)]:
+                        q.remove(r)
+                        out.append(Completion(r.id, r.arrival, math.nan, math.nan, now, None, "cancelled"))
+                        progressed = True
+                for item in [x for x in resident if gone(x[0])]:
+                    r, h, t_adm = item
+                    resident.remove(item)
+                    be.release(h)
+                    in_use -= r.nbytes
+                    retry_blocked = False
+                    out.append(Completion(r.id, r.arrival, t_adm, math.nan, clock() - t0, None, "cancelled"))
+                    progressed = True
+                for slot, (r, h, t_adm, t_start) in running.items():
+                    if gone(r):
+                        dropping.add(r.id)
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
                 progressed = True
@@ -122,16 +171,34 @@ class Scheduler:
                 if be.done(h):
                     res = be.finish(h)
                     t_fin = clock() - t0
-                    out.append(Completion(r.id, r.arrival, t_adm, t_start, t_fin, res))
+                    if r.id in dropping:
+                        out.append(Completion(r.id, r.arrival, t_adm, t_start, t_fin, None, "cancelled"))
+                    else:
+                        out.append(Completion(r.id, r.arrival, t_adm, t_start, t_fin, res))
                     in_use -= r.nbytes
                     del running[slot]
                     free_slots.append(slot)
+                    retry_blocked = False
                     progressed = True
-            while waiting and in_use + waiting[0].nbytes <= self.budget:
+            while waiting and in_use + waiting[0].nbytes <= self.budget and not retry_blocked:
                 r = waiting.popleft()
+                try:
+                    h = be.admit(r)
+                except OutOfMemory as e:               # the backend released what it had taken
+                    if resident or running:
+                        waiting.appendleft(r)          # again after the next completion
+                        retry_blocked = True
+                        continue
+                    out.append(Completion(r.id, r.arrival, math.nan, math.nan, clock() - t0, e, "failed"))
+                    progressed = True
+                    continue
+                except Exception as e:
+                    out.append(Completion(r.id, r.arrival, math.nan, math.nan, clock() - t0, e, "failed"))
+                    progressed = True
+                    continue
                 in_use += r.nbytes
                 self.peak_bytes = max(self.peak_bytes, in_use)
-                resident.append((r, be.admit(r), clock() - t0))
+                resident.append((r, h, clock() - t0))
                 progressed = True
             while resident and free_slots:
                 i = self._next(resident, clock() - t0)
@@ -235,16 +302,31 @@ class CudaBackend:
         n = r.N * r.H * r.W
         if n > self.max_planes or r.H * r.W * r.topk * kb.RESULT_DTYPE.itemsize > self.dev_out[0].numel():
             raise ValueError("request %d is larger than the backend's staging" % r.id)
-        st = kb.Stack(self.ctx, r.N, r.H, r.W, self.storage)
-        job = kb.Job(self.ctx, r.H, r.W, r.N, r.V, r.topk, self.flags)
-        with torch.cuda.stream(self.upload):
-            sci = self.stage[:n].view(r.N, r.H, r.W)
-            var = self.stage[self.max_planes:self.max_planes + n].view(r.N, r.H, r.W)
-            sci.copy_(p["sci"][:r.N], non_blocking=True)
-            var.copy_(p["var"][:r.N], non_blocking=True)
-            st.make_psi_phi(sci, var, None, p["psf"][:r.N], stream=self.upload)
-            ready = torch.cuda.Event()
-            ready.record(self.upload)
+        try:
+            st = kb.Stack(self.ctx, r.N, r.H, r.W, self.storage)
+        except kb.KBError as e:
+            if e.code == kb.KB_ENOMEM:
+                raise OutOfMemory(str(e)) from e
+            raise
+        job = None
+        try:                                  # on failure, free what this admission took
+            job = kb.Job(self.ctx, r.H, r.W, r.N, r.V, r.topk, self.flags)
+            with torch.cuda.stream(self.upload):
+                sci = self.stage[:n].view(r.N, r.H, r.W)
+                var = self.stage[self.max_planes:self.max_planes + n].view(r.N, r.H, r.W)
+                sci.copy_(p["sci"][:r.N], non_blocking=True)
+                var.copy_(p["var"][:r.N], non_blocking=True)
+                st.make_psi_phi(sci, var, None, p["psf"][:r.N], stream=self.upload)
+                ready = torch.cuda.Event()
+                ready.record(self.upload)
+        except Exception as e:
+            self.upload.synchronize()
+            if job is not None:
+                job.free()
+            st.free()
+            if isinstance(e, kb.KBError) and e.code == kb.KB_ENOMEM:
+                raise OutOfMemory(str(e)) from e
+            raise
         return dict(r=r, stack=st, job=job, ready=ready, done=None)
 
     def dispatch(self, h, slot: int):
@@ -272,6 +354,12 @@ class CudaBackend:
 
     def done(self, h) -> bool:
         return h["done"].query()
+
+    def release(self, h):
+        """Free an admitted request that will not run (cancelled while resident)."""
+        h["ready"].synchronize()              # its uploads and psi/phi are done with the staging
+        h["job"].free()
+        h["stack"].free()
 
     def finish(self, h):
         h["job"].wait()                       # raises on a device-side status

@@ -152,3 +152,12 @@ def test_build_digest_follows_the_sources(tmp_path, lib):
     assert build.up_to_date()
     with open(build.STAMP) as f:
         assert f.read().strip() == build.source_digest()
+
+
+def test_release_build_is_not_a_debug_build(lib):
+    """kb_debug_build needs no device: 0 in the release library; the debug build's
+    digest differs (its flags add -DKB_DEBUG), so the two never share a stamp."""
+    from paper_1901_02492_gb300 import build
+    assert lib.debug_build() is False
+    assert build.source_digest(debug=True) != build.source_digest()
+    assert build.LIB_DEBUG != build.LIB

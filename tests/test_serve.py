@@ -5,12 +5,16 @@ once dispatched and run side by side on the slots; the scheduler is driven by a
 virtual clock.  Checked: the memory budget is never exceeded, admission is in
 arrival order, at most `slots` requests run at once, requests arriving while
 others run are admitted as soon as memory allows, every request completes
-once, and the serial-baseline and busy-fraction arithmetic.
+once, the serial-baseline and busy-fraction arithmetic, and the host-side
+failure paths: cancellation of waiting, resident and running requests, failed
+admissions (a malformed request, an allocation failure under a fake budget).
 """
+import math
+
 import numpy as np
 import pytest
 
-from paper_1901_02492_gb300.serve import Request, Scheduler, busy_fraction, fifo_latencies
+from paper_1901_02492_gb300.serve import OutOfMemory, Request, Scheduler, busy_fraction, fifo_latencies
 
 
 class Clock:
@@ -33,6 +37,8 @@ class SimBackend:
         self.max_running = 0
         self.admitted = []
         self.events = []
+        self.finished = []
+        self.released = []
 
     def estimate(self, r):
         return r.N * r.H * r.W
@@ -56,7 +62,29 @@ class SimBackend:
     def finish(self, h):
         self.running -= 1
         self.in_use -= h["r"].nbytes
+        self.finished.append(h["r"].id)
         return h["r"].id
+
+    def release(self, h):
+        self.in_use -= h["r"].nbytes
+        self.released.append(h["r"].id)
+
+
+class FaultyBackend(SimBackend):
+    """Admission fails for a malformed request (payload "bad") and, like a device
+    whose allocator runs out first, when the memory taken would pass `device_bytes`
+    (a fake budget below the scheduler's); a failed admission takes nothing."""
+
+    def __init__(self, clock, service, device_bytes):
+        super().__init__(clock, service)
+        self.device_bytes = device_bytes
+
+    def admit(self, r):
+        if r.payload == "bad":
+            raise ValueError("malformed request %d" % r.id)
+        if self.in_use + r.nbytes > self.device_bytes:
+            raise OutOfMemory("out of device memory for request %d" % r.id)
+        return super().admit(r)
 
 
 def _requests(n, seed=0, rate=50.0):
@@ -167,3 +195,65 @@ def test_sjf_lowers_median_latency_on_a_mixed_stream():
         assert be.max_in_use <= 200000
         res[policy] = np.median([c.latency for c in done])
     assert res["sjf"] <= res["fifo"]
+
+
+def test_cancel_mid_queue_resident_and_running():
+    """One slot, budget for two requests: request 0 runs, 1 is resident, 2-5 wait.
+    Cancelled by time: 3 while waiting, 1 while resident, 0 while running; request
+    4 by Scheduler.cancel from the clock (another caller) while waiting."""
+    clk = Clock()
+    reqs = [Request(i, 0.001 * i, 5, 10, 10, 7, 256, 8) for i in range(6)]      # 500 bytes each
+    reqs[3].cancel_at = 0.05
+    reqs[1].cancel_at = 0.2
+    reqs[0].cancel_at = 0.5
+    be = SimBackend(clk, lambda r: 1.0)
+    sched = Scheduler(be, 1000, 1)
+
+    def sleep(dt):
+        clk.sleep(dt)
+        if clk.t >= 0.1:
+            sched.cancel(4)
+
+    out = {c.id: c for c in sched.run(reqs, clock=clk, sleep=sleep)}
+    assert sorted(out) == list(range(6))
+    assert [out[i].status for i in range(6)] == ["cancelled", "cancelled", "done", "cancelled", "cancelled", "done"]
+    # 0 ran to the end of its kernels, its result dropped; 1 was released without running
+    assert out[0].result is None and 0 in be.finished and out[0].finished >= 1.0
+    assert be.released == [1] and math.isnan(out[1].started) and out[1].finished < 1.0
+    # 3 and 4 never reached the device
+    assert 3 not in be.admitted and 4 not in be.admitted
+    assert math.isnan(out[3].admitted) and 0.05 <= out[3].finished < 0.1
+    assert out[2].result == 2 and out[5].result == 5
+    assert be.in_use == 0 and be.running == 0 and be.max_in_use <= 1000
+
+
+def test_cancel_before_arrival():
+    clk = Clock()
+    reqs = [Request(0, 0.0, 5, 10, 10, 7, 256, 8), Request(1, 0.5, 5, 10, 10, 7, 256, 8)]
+    be = SimBackend(clk, lambda r: 0.01)
+    sched = Scheduler(be, 10 ** 6, 2)
+    sched.cancel(1)
+    out = {c.id: c for c in sched.run(reqs, clock=clk, sleep=clk.sleep)}
+    assert out[0].status == "done" and out[1].status == "cancelled" and be.admitted == [0]
+
+
+def test_failed_admissions_complete_and_the_rest_run():
+    """A malformed request completes as "failed" with the error; requests whose
+    allocation fails (the device holds less than the scheduler's budget) go back to
+    the head of the queue and run after the next completion; one that cannot fit
+    even alone fails.  Nothing a failed admission took stays taken."""
+    clk = Clock()
+    reqs = [Request(i, 0.001 * i, 5, 10, 10, 7, 256, 8) for i in range(8)]     # 500 bytes each
+    reqs[2].payload = "bad"
+    be = FaultyBackend(clk, lambda r: 0.05 if r.id else 0.2, device_bytes=1000)
+    out = {c.id: c for c in Scheduler(be, 1500, 4).run(reqs, clock=clk, sleep=clk.sleep)}
+    assert sorted(out) == list(range(8))
+    assert out[2].status == "failed" and isinstance(out[2].result, ValueError)
+    assert all(out[i].status == "done" and out[i].result == i for i in out if i != 2)
+    assert be.admitted == [0, 1, 3, 4, 5, 6, 7]        # admission order kept through the retries
+    assert out[3].admitted >= min(out[0].finished, out[1].finished)
+    assert be.in_use == 0 and be.max_in_use <= 1000
+    clk2 = Clock()
+    be2 = FaultyBackend(clk2, lambda r: 0.01, device_bytes=400)
+    out2 = Scheduler(be2, 1500, 4).run([Request(0, 0.0, 5, 10, 10, 7, 256, 8)], clock=clk2, sleep=clk2.sleep)
+    assert out2[0].status == "failed" and isinstance(out2[0].result, OutOfMemory)

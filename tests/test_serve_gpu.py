@@ -82,3 +82,43 @@ def test_each_result_same_alone_and_in_the_mix(kb, storage, rescore):
             oref, nu_of = oracle_search(st, k=r.topk)
             check_topk(c.result, oref, nu_of)
     ctx.close()
+
+
+def test_cancelled_requests_release_their_memory(kb):
+    """Cancellation on the device backend.  Every request arrives at once, one slot,
+    budget for three: at the dispatch of request 0, requests 1 and 2 are resident,
+    and request 1 is cancelled (released without running); request 3 is cancelled
+    from its own dispatch (it runs, its result is dropped); request 6 before the run
+    (it never reaches the device).  All memory is released, and the other results
+    equal their searches alone."""
+    from paper_1901_02492_gb300 import serve
+    reqs, stacks = _requests(serve)
+    for r in reqs:
+        r.arrival = 0.0
+    ctx = kb.Context(0)
+
+    class Backend(serve.CudaBackend):
+        def dispatch(self, h, slot):
+            super().dispatch(h, slot)
+            if h["r"].id == 0:
+                sched.cancel(1)
+            if h["r"].id == 3:
+                sched.cancel(3)
+
+    be = Backend(ctx, DEV, storage="bf16", rescore=True, slots=1,
+                 max_npix=max(r.H * r.W for r in reqs), max_planes=max(r.N * r.H * r.W for r in reqs),
+                 max_topk=8, keep_results=True)
+    foot = sorted(be.estimate(r) for r in reqs)
+    sched = serve.Scheduler(be, sum(foot[-3:]), slots=1)
+    sched.cancel(6)
+    done = {c.id: c for c in sched.run(reqs)}
+    assert sorted(done) == list(range(len(reqs)))
+    assert ctx.hbm_in_use == 0
+    assert all(done[i].status == "cancelled" and done[i].result is None for i in (1, 3, 6))
+    assert math.isnan(done[1].started) and not math.isnan(done[3].started) and math.isnan(done[6].admitted)
+    for i, c in done.items():
+        if i not in (1, 3, 6):
+            assert c.status == "done"
+            ref = _alone(kb, ctx, stacks[i], "bf16", kb.KB_RESCORE_FP64, reqs[i].topk)
+            assert c.result.tobytes() == ref.tobytes()
+    ctx.close()
