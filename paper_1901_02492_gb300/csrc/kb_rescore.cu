@@ -33,18 +33,25 @@ namespace {
 // take a value to units of 2^L and the double factors back (2^L).
 struct FixedPoint {
     int sh_p, sh_f;          // -150 - L: a float's exponent field plus this is its shift to units of 2^L
-    double from_p, from_f;
+    int L_p, L_f;            // the binary points
 };
 
 // one plane type: every |value| < 2^E, E from the largest per-epoch maximum (bits of
 // a non-negative float order like the float); E kept in [-60, 100] so that 2^-L and
 // 2^L stay normal floats and doubles
-__device__ __forceinline__ void fixed_point_of(unsigned maxbits, int &sh, double &from) {
+__device__ __forceinline__ void fixed_point_of(unsigned maxbits, int &sh, int &L) {
     int E = maxbits == 0u ? -60 : (int)((maxbits >> 23) & 0xff) - 126;   // floor(log2 m) + 1
     E = max(-60, min(100, E));
-    const int L = E - 56;
+    L = E - 56;
     sh = -150 - L;
-    from = __longlong_as_double((long long)(1023 + L) << 52);
+}
+
+// A fixed-point sum s in units of 2^L, rounded once to FP64: (double)s * 2^L, the
+// power-of-two scaling done by adding L to the exponent field (exact: |s| >= 1 and
+// L in [-116, 44] keep the result normal) on the integer pipe, not by an FP64 multiply.
+__device__ __forceinline__ double scaled(long long s, int L) {
+    const double d = (double)s;
+    return s == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(d) + ((long long)L << 52));
 }
 
 // round(x 2^-L) (ties away from zero) for |x| < 2^(L+56), on the integer pipe: with
@@ -75,20 +82,22 @@ __device__ __forceinline__ FixedPoint stack_fixed_point(const RescoreArgs &a) {
     for (int i = threadIdx.x; i < 2 * a.N; i += blockDim.x) atomicMax(&s_m[i & 1], a.maxbits[i]);
     __syncthreads();
     FixedPoint fp;
-    fixed_point_of(s_m[0], fp.sh_p, fp.from_p);
-    fixed_point_of(s_m[1], fp.sh_f, fp.from_f);
+    fixed_point_of(s_m[0], fp.sh_p, fp.L_p);
+    fixed_point_of(s_m[1], fp.sh_f, fp.L_f);
     return fp;
 }
 
-// Exact coadd of one trajectory from the FP32 planes (fixed point, see above),
-// rounded once to FP64.  Four epochs at a time: their offsets, then their four
+// Exact coadd of one trajectory from the FP32 planes: the fixed-point sums p, f in
+// units of 2^L_p, 2^L_f (see above; scaled() rounds them once to FP64) and the
+// count of in-image epochs.  Four epochs at a time: their offsets, then their four
 // plane gathers, then the sums, so that the scattered loads overlap instead of
 // forming one dependent chain.
-__device__ __forceinline__ void traj_exact(const RescoreArgs &a, const FixedPoint &fp, int x, int y, int v, double &P,
-                                           double &F, int &nobs) {
+__device__ __forceinline__ void traj_exact(const RescoreArgs &a, const FixedPoint &fp, int x, int y, int v,
+                                           long long &p, long long &f, int &nobs) {
     const int2 *ov = a.offs + (long long)v * a.N;
     const float2 *base = a.f32 + a.origin;
-    long long p = 0, f = 0;
+    p = 0;
+    f = 0;
     nobs = 0;
     int j = 0;
     for (; j + 4 <= a.N; j += 4) {
@@ -121,14 +130,8 @@ __device__ __forceinline__ void traj_exact(const RescoreArgs &a, const FixedPoin
             ++nobs;
         }
     }
-    P = (double)p * fp.from_p;
-    F = (double)f * fp.from_f;
 }
 
-// (nu desc, vidx asc)
-__device__ __forceinline__ bool better64(double an, int av, double bn, int bv) {
-    return an > bn || (an == bn && av < bv);
-}
 
 // FP64 nu of a coadd, Psi / sqrt(Phi) as Psi * rsqrt(Phi) (CUDA's double rsqrt):
 // one reciprocal square root instead of a correctly rounded square root and a
@@ -145,23 +148,32 @@ __device__ __forceinline__ unsigned long long okey(double d) {
 __device__ __forceinline__ double okey_value(unsigned long long k) {
     return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffULL) : ~k));
 }
-// (key desc, vidx asc): the same order as better64 on the doubles the keys encode
+// (key desc, vidx asc): the order (nu desc, vidx asc) of the doubles the keys encode
 __device__ __forceinline__ bool betterk(unsigned long long ak, int av, unsigned long long bk, int bv) {
     return ak > bk || (ak == bk && av < bv);
 }
 
-// Largest distance from nu to a value in (lo, hi], where hi is a key-form
-// candidate's nu (its order-preserving FP32 encoding a multiple of 2^b) and lo the
-// value 2^b below it in that encoding: a bound on |nu - nu16| for the unrounded
-// reduced-precision score nu16 of the candidate.  Infinite where lo or hi is not
-// finite (such a pixel is never certified).
-__device__ __forceinline__ double key_error(double nu, float hi, int b) {
-    const uint32_t u = __float_as_uint(hi);
-    const uint32_t ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-    if (!(fabsf(hi) < INFINITY) || ord < 0x00800000u + (1u << b)) return INFINITY;
-    const uint32_t lo_ord = ord - (1u << b);
-    const float lo = __uint_as_float((lo_ord & 0x80000000u) ? (lo_ord & 0x7FFFFFFFu) : ~lo_ord);
-    return fmax(fabs(nu - (double)hi), fabs(nu - (double)lo));
+// Upper bound on |nu - nu16| for a candidate of FP64 score nu whose reduced-
+// precision score nu16 lies in (lo, hi]: in key form (b > 0) hi is its key's value
+// (an order-preserving FP32 encoding that is a multiple of 2^b) and lo the value 2^b
+// below it in that encoding; in value form (b = 0) nu16 = hi = lo.  The bound is
+// max(|nu - lo|, |nu - hi|), formed in FP32 on the FP32 pipe: nf, nu rounded to FP32,
+// is within 2^-24 |nf| of nu (twice that is added, and 2^-126 for the subnormal
+// range), and every difference and sum rounds upwards.  Infinite where lo, hi or nf
+// is not finite (such a pixel is never certified).
+__device__ __forceinline__ float cand_error(double nu, float hi, int b) {
+    const float nf = __double2float_rn(nu);
+    if (!(fabsf(hi) < INFINITY) || !(fabsf(nf) < INFINITY)) return INFINITY;
+    float lo = hi;
+    if (b > 0) {
+        const uint32_t u = __float_as_uint(hi);
+        const uint32_t ord = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+        if (ord < 0x00800000u + (1u << b)) return INFINITY;
+        const uint32_t lo_ord = ord - (1u << b);
+        lo = __uint_as_float((lo_ord & 0x80000000u) ? (lo_ord & 0x7FFFFFFFu) : ~lo_ord);
+    }
+    const float d = fmaxf(__fsub_ru(fmaxf(nf, hi), fminf(nf, hi)), __fsub_ru(fmaxf(nf, lo), fminf(nf, lo)));
+    return __fadd_ru(__fadd_ru(d, __fmul_ru(fabsf(nf), 0x1p-23f)), 0x1p-126f);
 }
 
 // Pixel order of the rescoring: one 32 x 4 tile per CTA of 128 threads, tiles
@@ -213,7 +225,7 @@ __global__ void __launch_bounds__(128) rescore_kernel(RescoreArgs a) {
             lo[i] = 0;
         }
         int ncand = 0, n = 0;
-        double emax = 0.0;
+        float emax = 0.0f;   // largest bound on a candidate's own |nu - nu16|
         float nu16_last = -INFINITY;
         const Rec *cand = a.cand + pix * a.kc;
         for (int c = 0; c < a.kc; ++c) {
@@ -222,13 +234,14 @@ __global__ void __launch_bounds__(128) rescore_kernel(RescoreArgs a) {
             if (v == kEmptyVidx) break;
             ++ncand;
             nu16_last = rc.nu;
-            double P, F;
+            long long ps, fs;
             int nobs;
-            traj_exact(a, fp, x, y, (int)v, P, F, nobs);
-            if (!(F > 0.0)) continue;
+            traj_exact(a, fp, x, y, (int)v, ps, fs, nobs);
+            if (fs <= 0) continue;   // Phi = 0: no valid trajectory
+            const double P = scaled(ps, fp.L_p), F = scaled(fs, fp.L_f);
             const double nu = nu64(P, F);
             // a key-form nu16 is rounded upwards: the unrounded score lies in (lo, hi]
-            emax = fmax(emax, a.nu_key ? key_error(nu, rc.nu, a.nu_key) : fabs(nu - (double)rc.nu));
+            emax = fmaxf(emax, cand_error(nu, rc.nu, a.nu_key));
             if (!(nu >= a.nu_min)) continue;
             ++n;
             // bubble the candidate down the sorted register list (nu desc, vidx asc),
@@ -280,7 +293,7 @@ __global__ void __launch_bounds__(128) rescore_kernel(RescoreArgs a) {
 #pragma unroll
             for (int i = 0; i < K; ++i)
                 if (i == a.k - 1 && n >= a.k) bar = okey_value(lk[i]);
-            const double margin = 2.0 * emax + a.unit * (1.0 + fabs((double)nu16_last));
+            const double margin = 2.0 * (double)emax + a.unit * (1.0 + fabs((double)nu16_last));
             if (!((double)nu16_last + margin < bar)) {
                 const int slot = atomicAdd(a.ucount, 1);
                 a.ulist[slot] = (int)pix;
@@ -308,27 +321,31 @@ __global__ void __launch_bounds__(kRepairThreads) repair_kernel(RescoreArgs a) {
     for (int u = blockIdx.x; u < count; u += gridDim.x) {
         const int pix = a.ulist[u];
         const int y = pix / a.W, x = pix - y * a.W;
-        double ln[KB_MAX_TOPK], lp[KB_MAX_TOPK], lf[KB_MAX_TOPK];
+        // nu as its order key: the list's compares and the merge's shuffles on the integer pipe
+        unsigned long long lk[KB_MAX_TOPK];
+        double lp[KB_MAX_TOPK], lf[KB_MAX_TOPK];
         int lv[KB_MAX_TOPK], lo[KB_MAX_TOPK];
         int n = 0;
         for (int v = threadIdx.x; v < a.V; v += kRepairThreads) {
-            double P, F;
+            long long ps, fs;
             int nobs;
-            traj_exact(a, fp, x, y, v, P, F, nobs);
-            if (!(F > 0.0)) continue;
+            traj_exact(a, fp, x, y, v, ps, fs, nobs);
+            if (fs <= 0) continue;   // Phi = 0: no valid trajectory
+            const double P = scaled(ps, fp.L_p), F = scaled(fs, fp.L_f);
             const double nu = nu64(P, F);
             if (!(nu >= a.nu_min)) continue;
-            if (n == a.k && !better64(nu, v, ln[n - 1], lv[n - 1])) continue;
+            const unsigned long long key = okey(nu);
+            if (n == a.k && !betterk(key, v, lk[n - 1], lv[n - 1])) continue;
             int i = (n < a.k) ? n++ : a.k - 1;
-            while (i > 0 && better64(nu, v, ln[i - 1], lv[i - 1])) {
-                ln[i] = ln[i - 1];
+            while (i > 0 && betterk(key, v, lk[i - 1], lv[i - 1])) {
+                lk[i] = lk[i - 1];
                 lp[i] = lp[i - 1];
                 lf[i] = lf[i - 1];
                 lv[i] = lv[i - 1];
                 lo[i] = lo[i - 1];
                 --i;
             }
-            ln[i] = nu;
+            lk[i] = key;
             lp[i] = P;
             lf[i] = F;
             lv[i] = v;
@@ -337,15 +354,16 @@ __global__ void __launch_bounds__(kRepairThreads) repair_kernel(RescoreArgs a) {
         // per warp: each round the best head among the lanes goes to s_best[warp][r]
         int head = 0;
         for (int r = 0; r < a.k; ++r) {
-            double bn = head < n ? ln[head] : -INFINITY;
+            // key 0 is below the key of every score, -inf included
+            unsigned long long bk = head < n ? lk[head] : 0ull;
             int bv = head < n ? lv[head] : INT_MAX;
             int bl = lane;
             for (int o = 16; o > 0; o >>= 1) {
-                const double on = __shfl_xor_sync(0xffffffffu, bn, o);
+                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
                 const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
                 const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-                if (better64(on, ov, bn, bv)) {
-                    bn = on;
+                if (betterk(ok, ov, bk, bv)) {
+                    bk = ok;
                     bv = ov;
                     bl = ol;
                 }
@@ -354,7 +372,7 @@ __global__ void __launch_bounds__(kRepairThreads) repair_kernel(RescoreArgs a) {
                 Rec64 q;
                 q.psi = lp[head];
                 q.phi = lf[head];
-                q.nu = ln[head];
+                q.nu = okey_value(lk[head]);
                 q.vidx = (uint32_t)lv[head];
                 q.nobs = (uint32_t)lo[head];
                 s_best[warp][r] = q;
@@ -377,15 +395,15 @@ __global__ void __launch_bounds__(kRepairThreads) repair_kernel(RescoreArgs a) {
             Rec64 *out = a.out + (long long)pix * a.k;
             for (int r = 0; r < a.k; ++r) {
                 const bool has = lane < kRepairWarps && h < a.k && s_best[lane][h].vidx != kEmptyVidx;
-                double bn = has ? s_best[lane][h].nu : -INFINITY;
+                unsigned long long bk = has ? okey(s_best[lane][h].nu) : 0ull;
                 int bv = has ? (int)s_best[lane][h].vidx : INT_MAX;
                 int bl = lane;
                 for (int o = 16; o > 0; o >>= 1) {
-                    const double on = __shfl_xor_sync(0xffffffffu, bn, o);
+                    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
                     const int ov = __shfl_xor_sync(0xffffffffu, bv, o);
                     const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-                    if (better64(on, ov, bn, bv)) {
-                        bn = on;
+                    if (betterk(ok, ov, bk, bv)) {
+                        bk = ok;
                         bv = ov;
                         bl = ol;
                     }
