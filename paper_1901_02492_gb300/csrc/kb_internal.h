@@ -59,6 +59,18 @@ struct Rec {
 constexpr uint32_t kEmptyVidx = 0xFFFFu;
 static_assert(sizeof(Rec) == sizeof(kb_result_compact), "the device record is the compact transfer record");
 
+// A candidate of the rescoring's key-form search (one 32-bit key, 0 = empty): with
+// b bits for a velocity index, the high 32 - b bits hold nu's order-preserving FP32
+// encoding rounded upwards to a multiple of 2^b, the low b bits 2^b - 1 - vidx.
+__device__ __forceinline__ float cand_key_nu(uint32_t key, int b) {
+    const uint32_t ord = key & ~((1u << b) - 1u);
+    return __uint_as_float((ord & 0x80000000u) ? (ord & 0x7FFFFFFFu) : ~ord);
+}
+__device__ __forceinline__ int cand_key_vidx(uint32_t key, int b) {
+    const uint32_t m = (1u << b) - 1u;
+    return (int)(m - (key & m));
+}
+
 // Device record after FP64 rescoring (32 bytes).
 struct Rec64 {
     double psi, phi;
@@ -250,7 +262,7 @@ struct RescoreArgs {
     const int *epoch_of;
     const int2 *offs;        // [V][N] time order
     const unsigned *maxbits; // [2N] per-epoch max |psi|, max phi (float bits), for the exact sums
-    const Rec *cand;         // [H*W][kc]
+    const Rec *cand;         // [H*W][kc] records, or 32-bit candidate keys when nu_key > 0
     int kc;                  // candidates per pixel
     int k;                   // results per pixel
     double nu_min;

@@ -228,12 +228,23 @@ __global__ void __launch_bounds__(128) rescore_kernel(RescoreArgs a) {
         float emax = 0.0f;   // largest bound on a candidate's own |nu - nu16|
         float nu16_last = -INFINITY;
         const Rec *cand = a.cand + pix * a.kc;
+        const uint32_t *ckey = reinterpret_cast<const uint32_t *>(a.cand) + pix * a.kc;
         for (int c = 0; c < a.kc; ++c) {
-            const Rec rc = cand[c];
-            const uint32_t v = rc.meta & 0xffffu;
-            if (v == kEmptyVidx) break;
+            uint32_t v;
+            float nu16;
+            if (a.nu_key) {   // key form: 0 is an empty slot
+                const uint32_t kk = ckey[c];
+                if (kk == 0u) break;
+                v = (uint32_t)cand_key_vidx(kk, a.nu_key);
+                nu16 = cand_key_nu(kk, a.nu_key);
+            } else {
+                const Rec rc = cand[c];
+                v = rc.meta & 0xffffu;
+                if (v == kEmptyVidx) break;
+                nu16 = rc.nu;
+            }
             ++ncand;
-            nu16_last = rc.nu;
+            nu16_last = nu16;
             long long ps, fs;
             int nobs;
             traj_exact(a, fp, x, y, (int)v, ps, fs, nobs);
@@ -241,7 +252,7 @@ __global__ void __launch_bounds__(128) rescore_kernel(RescoreArgs a) {
             const double P = scaled(ps, fp.L_p), F = scaled(fs, fp.L_f);
             const double nu = nu64(P, F);
             // a key-form nu16 is rounded upwards: the unrounded score lies in (lo, hi]
-            emax = fmaxf(emax, cand_error(nu, rc.nu, a.nu_key));
+            emax = fmaxf(emax, cand_error(nu, nu16, a.nu_key));
             if (!(nu >= a.nu_min)) continue;
             ++n;
             // bubble the candidate down the sorted register list (nu desc, vidx asc),

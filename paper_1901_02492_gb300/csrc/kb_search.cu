@@ -333,14 +333,6 @@ __device__ __forceinline__ uint32_t nu_key(float nu, int v, int b) {
     const uint32_t q = (ord >> b) + ((ord & m) ? 1u : 0u);   // finite nu: q << b <= encoding of +inf
     return (q << b) | (m - (uint32_t)v);
 }
-__device__ __forceinline__ float key_nu(uint32_t key, int b) {
-    const uint32_t ord = key & ~((1u << b) - 1u);
-    return __uint_as_float((ord & 0x80000000u) ? (ord & 0x7FFFFFFFu) : ~ord);
-}
-__device__ __forceinline__ int key_vidx(uint32_t key, int b) {
-    const uint32_t m = (1u << b) - 1u;
-    return (int)(m - (key & m));
-}
 
 // Rank insertion of key ck into the key list of column `col` (k <= kKeyMax slots,
 // best first), if it beats the list's last entry.
@@ -651,23 +643,15 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     }
     __syncwarp();
     if constexpr (KEYS) {
-        // candidates for the rescoring: vidx and the key's nu (an upper bound on the 16-bit nu),
-        // best first; the rescoring recomputes the sums
+        // candidates for the rescoring, best first, as the keys themselves (4 bytes each,
+        // decoded by the rescoring, which recomputes the sums)
 #pragma unroll
         for (int p = 0; p < PX; ++p) {
             const int x = xw + (G::PIX == 1 ? lane + 32 * p : 2 * lane + 64 * (p / 2) + (p & 1));
             if (x >= a.W) continue;
-            Rec *out = a.out + ((long long)y * a.W + x) * k;
+            uint32_t *out = reinterpret_cast<uint32_t *>(a.out) + ((long long)y * a.W + x) * k;
             const uint32_t *lk = s_lk + p * THREADS + threadIdx.x;
-            for (int i = 0; i < k; ++i) {
-                const uint32_t kk = lk[i * LS];
-                Rec r;
-                r.psi = 0.0f;
-                r.phi = 0.0f;
-                r.nu = kk ? key_nu(kk, a.key_bits) : -INFINITY;
-                r.meta = kk ? (uint32_t)key_vidx(kk, a.key_bits) : kEmptyVidx;
-                reinterpret_cast<uint4 *>(out)[i] = *reinterpret_cast<uint4 *>(&r);
-            }
+            for (int i = 0; i < k; ++i) out[i] = lk[i * LS];
         }
         return;
     }
