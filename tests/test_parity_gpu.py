@@ -97,13 +97,15 @@ def test_psi_phi_planes_f32(kb, ctx, K, sep, mask, bright):
 
 
 @pytest.mark.parametrize("K,mask,H,W", [(3, False, 77, 152), (7, True, 77, 152), (17, True, 77, 152),
-                                         (15, False, 45, 200), (17, False, 1100, 68), (21, False, 45, 200)])
+                                         (15, False, 45, 200), (17, False, 1100, 68), (21, False, 45, 200),
+                                         (17, True, 70, 1000), (5, False, 1030, 508)])
 def test_psi_phi_stream_kernel(kb, ctx, K, mask, H, W):
     """Separable PSFs (K <= 21) on widths divisible by 4 take the streaming kernel (column
-    strips walked down segments of up to 512 rows, in batches of 32 rows); other widths the
-    tile kernel.  Planes against the oracle, and bit for bit against the tile kernel: the
-    same stack with one more column, of NaN variance (weight 0, like the outside of the
-    image), goes to the tile kernel."""
+    strips walked down segments of up to 512 rows, in batches of 32 rows; the last two cases
+    span many strips, and the second also several segments); other widths the tile kernel.
+    Planes against the oracle, and bit for bit against the tile kernel: the same stack with
+    one more column, of NaN variance (weight 0, like the outside of the image), goes to the
+    tile kernel."""
     st = synth.small_stack(300 + K, 3, H, W, K=K, sigma=max(K / 6.0, 0.5), var_lo=50, var_hi=150,
                            nan_frac=0.01, mask_frac=0.02 if mask else 0.0, flux=400.0)
     N = st.sci.shape[0]
