@@ -76,6 +76,10 @@ def parse():
     ap.add_argument("--threshold", type=float, default=0.0, metavar="NU_MIN",
                     help="also time the thresholded search (nu >= NU_MIN) with and without likelihood-bound "
                          "pruning (KB_PRUNE, Sec. 5.3); reported apart from the headline")
+    ap.add_argument("--rp-steps", type=int, default=5,
+                    help="default line: steps of the BF16 + FP64-rescoring leg beside the FP32 step (0 = off)")
+    ap.add_argument("--serve-sample", type=int, default=150,
+                    help="default line: jobs of the bounded serving sample with p50/p99 (0 = off)")
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-load", type=float, default=0.75,
                     help="arrival rate as a fraction of the capacity measured on a saturated sample")
@@ -679,19 +683,96 @@ def run_ours(args):
         line["rescore"] = {"candidates_per_pixel": job_kkeep(k, True, args.storage),
                            "repaired_pixels": repaired,
                            "repaired_fraction": repaired / float(H * W)}
+    if world == 1 and args.rp_steps > 0 and args.storage == "f32" and not args.rescore:
+        line["reduced_precision"] = reduced_precision_leg(args, kb, ctx, st, sci, var, stream, dev, jobs[0],
+                                                          ms / args.steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         e, s, p = oracle_sample(st, args.cpu_seconds, np.random.default_rng(7))
         line["cpu_baseline"] = {"value": e / s, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
                                 "sample": "%d random start pixels x %d velocities x %d epochs of the workload, "
                                           "psi/phi evaluated from the raw images, %.1f s" % (p, V, N, s)}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     for j in jobs:
         j.free()
     stack.free()
     ctx.close()
+    del sci, var, sci_d, var_d, res_h
+    torch.cuda.empty_cache()
+    if world == 1 and args.serve_sample > 0 and args.size == 4096:
+        line["serving_sample"] = serving_sample_leg(args, dev, kb)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     replicas.finish()
+
+
+def reduced_precision_leg(args, kb, ctx, st, sci, var, stream, dev, job32, ms_fp32):
+    """The same stack and grid with BF16 planes (per-epoch power-of-two scales) and the top-k
+    rescored in FP64 from the FP32 planes: ms per step (psi/phi, quantize, candidate search,
+    rescoring, repair) against the FP32 step just timed, and the slots whose velocity index equals
+    the FP32 path's (they differ only at near-ties of the FP32 search, which the FP64 oracle
+    decides: the rescored top-k is the oracle's, see the precision tests)."""
+    import torch
+    N, H, W = st.sci.shape
+    V, k = st.vx.size, st.k
+    flags = kb.KB_RESCORE_FP64
+    stack = kb.Stack(ctx, N, H, W, "bf16")
+    job = kb.Job(ctx, H, W, N, V, k, flags)
+
+    def step():
+        stack.make_psi_phi(sci, var, None, st.psf, stream=stream)
+        job.search(stack, st.times, st.vx, st.vy, k, -math.inf, flags, stream=stream)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize(dev)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.rp_steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = t0.elapsed_time(t1) / args.rp_steps
+    nrec = H * W * k
+    a = torch.empty(nrec * kb.COMPACT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    b = torch.empty_like(a)
+    job32.results_compact_async(a, stream=stream)
+    job.results_compact_async(b, stream=stream)
+    torch.cuda.synchronize(dev)
+    ra, rb = a.view(torch.int32).view(nrec, 4), b.view(torch.int32).view(nrec, 4)
+    same = (ra[:, 3] & 0xFFFF) == (rb[:, 3] & 0xFFFF)
+    nu_a, nu_b = ra[:, 2].view(torch.float32)[same], rb[:, 2].view(torch.float32)[same]
+    rel = ((nu_a - nu_b).abs() / nu_b.abs().clamp(min=1.0)).max().item() if bool(same.any()) else None
+    out = {"storage": "bf16", "rescore_fp64": True, "steps": args.rp_steps, "ms_per_step": ms,
+           "evals_per_s": N * H * W * V / (ms * 1e-3), "fp32_ms_per_step": ms_fp32,
+           "speed_vs_fp32_step": ms_fp32 / ms,
+           "candidates_per_pixel": job_kkeep(k, True, "bf16"), "repaired_pixels": job.repaired(),
+           "slots_equal_to_fp32": float(same.float().mean().item()),
+           "nu_max_rel_diff_vs_fp32_on_equal_slots": rel,
+           "timing": "CUDA events over %d steps after 2 warm-up steps, inputs resident" % args.rp_steps}
+    del a, b, ra, rb
+    job.free()
+    stack.free()
+    return out
+
+
+def serving_sample_leg(args, dev, kb):
+    """A bounded sample of the serving workload for the default line: the first
+    `--serve-sample` jobs of the serving stream, FIFO dispatch at `--serve-load` of the capacity
+    measured on a saturated sample of 60 of them, p50/p99 latency beside the serial plain-FP32
+    loop on the same arrivals (`--workload serve` runs the whole 2,000-job stream)."""
+    r = serve_measure(args, dev, kb, args.serve_sample, 60, ["fifo"])
+    lat, ser_lat, svc = r["lat"], r["ser_lat"], r["svc"]
+    pct = lambda x, q: float(np.percentile(x, q))
+    return {"jobs": len(r["done"]), "policy": "fifo", "slots": args.serve_slots,
+            "hbm_budget_gb": args.serve_budget_gb, "arrival_rate_hz": r["rate"], "capacity_jobs_s": r["cap_jobs_s"],
+            "served_bf16_rescored": {"p50_s": pct(lat, 50), "p99_s": pct(lat, 99), "mean_s": float(lat.mean()),
+                                     "jobs_per_s": len(r["done"]) / r["wall"],
+                                     "gpu_busy_fraction": r["main"]["busy"]},
+            "serial_fp32": {"p50_s": pct(ser_lat, 50), "p99_s": pct(ser_lat, 99),
+                            "capacity_jobs_s": len(r["reqs"]) / float(svc.sum())},
+            "capacity_vs_serial_fp32": r["cap_jobs_s"] / (len(r["reqs"]) / float(svc.sum())),
+            "clocks": r["main"]["clocks"],
+            "note": "sample of the serving workload's job stream; p99 over this many jobs is near its maximum"}
 
 
 def run_batch(args):
@@ -818,20 +899,70 @@ def run_serve(args):
     `--serve-load` of the loop's measured capacity.  Beside it, the plain FP32 serial loop: each
     job alone (upload, psi/phi, FP32 search, results to the host), its measured service times
     queued first-come first-served on the same arrival times."""
-    import torch
-    import synth
     from paper_1901_02492_gb300 import replicas
     rank, world, local = dist_info()
     dev = setup_device(world, local)
     import __graft_entry__
     __graft_entry__.build()
     from paper_1901_02492_gb300 import binding as kb
+
+    r = serve_measure(args, dev, kb, args.serve_jobs, 300, ["fifo", "sjf"] if args.serve_policy == "both"
+                      else [args.serve_policy])
+    policies, jobs, done, wall, lat = r["policies"], r["jobs"], r["done"], r["wall"], r["lat"]
+    main, served, evals, reqs, svc, ser_lat = r["main"], r["served"], r["evals"], r["reqs"], r["svc"], r["ser_lat"]
+    total_evals = sum(evals[c.id] for c in done)
+
+    def pct(x, q):
+        return float(np.percentile(x, q))
+
+    line = {"metric": "serving: p50/p99 job latency and throughput vs a serial plain-FP32 loop",
+            "value": total_evals / wall, "unit": "evals/s", "n_gpus": world, "steps": 1, "warmup": 1,
+            "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "serving: %d Poisson-arrival jobs of 512^2, 4096x2048, 4096^2 px, 5-15 epochs, "
+                                   "256-1024 velocities, k=8, BF16 + FP64 rescoring" % len(jobs),
+                       "jobs": len(jobs), "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb,
+                       "dispatch_policy": policies[-1],
+                       "arrival_rate_hz": r["rate"], "capacity_jobs_s": r["cap_jobs_s"],
+                       "target_load": args.serve_load,
+                       "inputs": "pinned host stacks per size class (drawn on the device), copied to the device "
+                                 "per job", "generate_s": round(r["t_gen"], 1), "parallelism": "replicas%d" % world},
+            "serving": {"p50_s": pct(lat, 50), "p99_s": pct(lat, 99), "mean_s": float(lat.mean()),
+                        "jobs_per_s": len(done) / wall, "gpu_busy_fraction": main["busy"],
+                        "peak_device_bytes": int(main["peak"])},
+            "serving_by_policy": {pol: {"p50_s": pct(v["lat"], 50), "p99_s": pct(v["lat"], 99),
+                                        "mean_s": float(v["lat"].mean()), "jobs_per_s": len(v["done"]) / v["wall"],
+                                        "gpu_busy_fraction": v["busy"]} for pol, v in served.items()},
+            "serial_fp32": {"p50_s": pct(ser_lat, 50), "p99_s": pct(ser_lat, 99),
+                            "jobs_per_s": len(reqs) / float(svc.sum()),
+                            "evals_per_s": sum(evals.values()) / float(svc.sum()),
+                            "mean_service_s": float(svc.mean())},
+            "clocks": main["clocks"],
+            "e2e": {"value": total_evals / wall, "unit": "evals/s",
+                    "h2d_bytes_per_step": int(sum(2 * 4 * jobs[c.id]["N"] * jobs[c.id]["H"] * jobs[c.id]["W"]
+                                                  for c in done)),
+                    "d2h_bytes_per_step": int(sum(48 * 8 * jobs[c.id]["H"] * jobs[c.id]["W"] for c in done))},
+            # per job: psi/phi, quantize, search, rescore, repair, expand (results to the device buffer)
+            "gpu_launches": 6 * len(done)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    replicas.finish()
+
+
+def serve_measure(args, dev, kb, n_jobs, n_calib, policies):
+    """Serving measurement shared by the serve workload and the default line's sample: the first
+    n_jobs jobs of the serving stream (BF16 + FP64 rescoring, `--serve-slots` slots, the HBM
+    budget), arriving at `--serve-load` of the capacity measured on a saturated sample of n_calib
+    jobs, under each dispatch policy in turn; then the serial plain-FP32 loop's service times, queued
+    first-come first-served on the same arrivals.  Uses a context of its own (the budget)."""
+    import torch
+    import synth
     from paper_1901_02492_gb300 import serve
 
     budget = int(args.serve_budget_gb * 1e9)
     ctx = kb.Context(dev.index, budget)
     t_gen = time.perf_counter()
-    jobs = synth.serving_jobs(count=args.serve_jobs, rate_hz=1.0)
+    jobs = synth.serving_jobs(count=n_jobs, rate_hz=1.0)
     max_n = max(j["N"] for j in jobs)
     pools = {}
     for (H, W) in sorted({(j["H"], j["W"]) for j in jobs}):
@@ -865,7 +996,7 @@ def run_serve(args):
     # warm-up, then capacity: a saturated sample of the job mix (all arriving at once), dispatched in
     # arrival order whatever the policy under test, so that every policy sees the same arrival rate
     calib = serve.Scheduler(be, budget - be.fixed_bytes, args.serve_slots, policy="fifo")
-    sample = list(range(min(len(jobs), 300)))
+    sample = list(range(min(len(jobs), n_calib)))
     calib.run(requests(None, sample[:6]))
     t0 = time.perf_counter()
     calib.run(requests(None, sample))
@@ -874,7 +1005,6 @@ def run_serve(args):
     cap_evals_s = sum(evals[i] for i in sample) / (time.perf_counter() - t0)
     cap_jobs_s = cap_evals_s / (sum(evals.values()) / len(jobs))
     rate = args.serve_load * cap_jobs_s
-    policies = ["fifo", "sjf"] if args.serve_policy == "both" else [args.serve_policy]
     served = {}
     for pol in policies:
         sched = serve.Scheduler(be, budget - be.fixed_bytes, args.serve_slots, policy=pol)
@@ -888,7 +1018,6 @@ def run_serve(args):
                            peak=sched.peak_bytes + be.fixed_bytes, clocks=clk.summary())
     main = served[policies[-1]]
     done, wall, lat = main["done"], main["wall"], main["lat"]
-    total_evals = sum(evals[c.id] for c in done)
     del be
     torch.cuda.synchronize(dev)
 
@@ -908,42 +1037,9 @@ def run_serve(args):
             svc[idx - 3] = time.perf_counter() - a
     ser_lat = serve.fifo_latencies(np.array([r.arrival for r in reqs]), svc)
     del ser
-
-    def pct(x, q):
-        return float(np.percentile(x, q))
-
-    line = {"metric": "serving: p50/p99 job latency and throughput vs a serial plain-FP32 loop",
-            "value": total_evals / wall, "unit": "evals/s", "n_gpus": world, "steps": 1, "warmup": 1,
-            "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "serving: %d Poisson-arrival jobs of 512^2, 4096x2048, 4096^2 px, 5-15 epochs, "
-                                   "256-1024 velocities, k=8, BF16 + FP64 rescoring" % len(jobs),
-                       "jobs": len(jobs), "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb,
-                       "dispatch_policy": policies[-1],
-                       "arrival_rate_hz": rate, "capacity_jobs_s": cap_jobs_s, "target_load": args.serve_load,
-                       "inputs": "pinned host stacks per size class (drawn on the device), copied to the device "
-                                 "per job", "generate_s": round(t_gen, 1), "parallelism": "replicas%d" % world},
-            "serving": {"p50_s": pct(lat, 50), "p99_s": pct(lat, 99), "mean_s": float(lat.mean()),
-                        "jobs_per_s": len(done) / wall, "gpu_busy_fraction": main["busy"],
-                        "peak_device_bytes": int(main["peak"])},
-            "serving_by_policy": {pol: {"p50_s": pct(v["lat"], 50), "p99_s": pct(v["lat"], 99),
-                                        "mean_s": float(v["lat"].mean()), "jobs_per_s": len(v["done"]) / v["wall"],
-                                        "gpu_busy_fraction": v["busy"]} for pol, v in served.items()},
-            "serial_fp32": {"p50_s": pct(ser_lat, 50), "p99_s": pct(ser_lat, 99),
-                            "jobs_per_s": len(reqs) / float(svc.sum()),
-                            "evals_per_s": sum(evals.values()) / float(svc.sum()),
-                            "mean_service_s": float(svc.mean())},
-            "clocks": main["clocks"],
-            "e2e": {"value": total_evals / wall, "unit": "evals/s",
-                    "h2d_bytes_per_step": int(sum(2 * 4 * jobs[c.id]["N"] * jobs[c.id]["H"] * jobs[c.id]["W"]
-                                                  for c in done)),
-                    "d2h_bytes_per_step": int(sum(48 * 8 * jobs[c.id]["H"] * jobs[c.id]["W"] for c in done))},
-            # per job: psi/phi, quantize, search, rescore, repair, expand (results to the device buffer)
-            "gpu_launches": 6 * len(done)}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     ctx.close()
-    replicas.finish()
+    return dict(policies=policies, jobs=jobs, done=done, wall=wall, lat=lat, main=main, served=served,
+                evals=evals, reqs=reqs, svc=svc, ser_lat=ser_lat, rate=rate, cap_jobs_s=cap_jobs_s, t_gen=t_gen)
 
 
 def main():
