@@ -171,7 +171,7 @@ int kb_measure_gather_peak(kb_ctx *ctx, int warp_bytes, int align_bytes, double 
  * 1 <= H, W <= KB_MAX_SIDE).  The FP32 (psi, phi) planes are always kept; with
  * storage KB_BF16 or KB_F16 a 16-bit copy with per-epoch scales is kept as well
  * (twice: also shifted by one pixel, so that any two adjacent pixels are one
- * aligned load) and is what kb_search reads.  Device memory: N * H * (W + 260)
+ * aligned load) and is what kb_search reads.  Device memory: N * (H + 16) * (W + 260)
  * * 8 bytes, twice that with 16-bit storage.  *out is owned by the caller:
  * kb_stack_free. */
 int kb_stack_create(kb_ctx *ctx, int N, int H, int W, int storage, kb_stack **out);

@@ -821,6 +821,7 @@ static int prepare_search(kb_job *job, const kb_stack *s, const double *times, c
     a.phase1 = (long long)N * s->L.plane_elems;
     a.planes_elems = (s->q16 ? 2LL : 1LL) * N * s->L.plane_elems;
     a.pad_x = s->L.pad_x;
+    a.pad_y = s->L.pad_y;
     a.H = s->H;
     a.W = s->W;
     a.pitch = s->L.pitch;

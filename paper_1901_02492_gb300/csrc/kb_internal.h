@@ -31,23 +31,27 @@ struct NvtxRange {
 typedef uint32_t pair16;
 
 // Plane layout.  Every psi/phi plane row carries pad_x = kSpan zero pixels on
-// its left and right; pixel (x, y) of epoch e is element
-// e * plane_elems + origin + y * pitch + x with origin = pad_x.  A warp span of
-// up to kSpan pixels that overlaps the image only partly therefore reads exactly
-// 0 for its off-image pixels ("outside contributes nothing") with no per-lane
-// bounds checks.
+// its left and right, and every plane pad_y = kPadRows zero rows above and
+// below; pixel (x, y) of epoch e is element e * plane_elems + origin + y * pitch
+// + x with origin = pad_y * pitch + pad_x.  A warp span of up to kSpan pixels
+// that overlaps the image only partly therefore reads exactly 0 for its
+// off-image pixels ("outside contributes nothing") with no per-lane bounds
+// checks, and so does a band of up to kPadRows rows that overlaps the image's
+// rows only partly.
 constexpr int kSpan = 128;
+constexpr int kPadRows = 8;   // >= the rows of a search CTA
 struct Layout {
-    int pad_x = 0, pitch = 0, rows = 0;
+    int pad_x = 0, pad_y = 0, pitch = 0, rows = 0;
     long long plane_elems = 0, origin = 0;
 };
 inline Layout make_layout(int H, int W) {
     Layout L;
     L.pad_x = kSpan;
+    L.pad_y = kPadRows;
     L.pitch = (W + 2 * kSpan + 3) & ~3;
-    L.rows = H;
+    L.rows = H + 2 * kPadRows;
     L.plane_elems = (long long)L.rows * L.pitch;
-    L.origin = L.pad_x;
+    L.origin = (long long)L.pad_y * L.pitch + L.pad_x;
     return L;
 }
 
@@ -196,6 +200,7 @@ struct SearchArgs {
     long long phase1;        // element offset of the 16-bit phase-1 copy (N * plane_elems)
     long long planes_elems;  // elements (pixels) of the planes' allocation, both phases (KB_DEBUG checks)
     int pad_x;               // zero columns left of every row (layout)
+    int pad_y;               // zero rows above every plane (layout)
     int H, W, pitch, N;      // N epochs, in time order through epoch_of
     int n0;                  // leading time-ordered epochs at offset 0 for every velocity
     const int *epoch_of;     // [N]

@@ -391,6 +391,14 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     typedef Gather<STORAGE> G;
     typedef typename G::LT LT;        // one load
     typedef Entry<I, STORAGE != KB_F32> E;
+    // Compact entries (FP32 planes, 32-bit offsets, no pruning): one 4-byte offset per
+    // (velocity, epoch), four to a 16-byte shared load.  The planes' zero rows above and
+    // below make every warp's row of a band that overlaps the image's rows valid, so no
+    // per-warp mask is needed; a band that misses the image gets the offset of the CTA's
+    // rows of zeros above row 0 of plane 0 (any warp lands in them).
+    constexpr bool CE = STORAGE == KB_F32 && sizeof(I) == 4 && !PRUNE;
+    static_assert(!CE || C % 4 == 0, "compact entries are read four at a time");
+    static_assert(WARPS <= kPadRows, "a band of warps' rows must fit the planes' zero rows");
     constexpr int TAB = tab_entries<STORAGE>();
     constexpr int PX = P * G::PIX;    // pixels per lane
     constexpr int SPAN = 32 * PX;     // pixels per warp row segment
@@ -404,7 +412,10 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     I *s_rid = reinterpret_cast<I *>(s_tab + TAB);
     int *s_vid = reinterpret_cast<int *>(s_rid + (PRUNE ? TAB : 0));
     const int N = a.N, n0 = a.n0, NJ = N - n0, k = a.k;
-    const int NJP = (NJ + 1) & ~1;   // table row stride: even, so entries pair into 16-byte loads
+    // table row stride: even, so that entries pair into 16-byte loads; compact entries: a
+    // multiple of 4 (the table region keeps its size, the compact rows use its first half)
+    const int NJP = CE ? (NJ + 3) & ~3 : (NJ + 1) & ~1;
+    int *s_tab4 = reinterpret_cast<int *>(s_dyn4);
     float *s_ln = reinterpret_cast<float *>(s_vid + TAB);
     uint16_t *s_lv = reinterpret_cast<uint16_t *>(s_ln + k * LS);
     uint32_t *s_lk = reinterpret_cast<uint32_t *>(s_vid + TAB);   // KEYS: the lists instead
@@ -495,11 +506,18 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             }
             long long g = (long long)ep * a.plane_elems + (long long)oy * a.pitch + ox;
             if (STORAGE != KB_F32 && (ox & 1)) g += a.phase1 - 1;   // odd shift: the phase-1 copy
-            E e;
-            e.idx = (I)g;
-            e.info = mask;
-            if constexpr (STORAGE != KB_F32) e.sc = sc_of(exp_scale(scale_exp(a.scales[ep])));
-            if (debug_in(vi * NJP + jj, TAB, 5)) s_tab[vi * NJP + jj] = e;
+            if constexpr (CE) {
+                // a warp's loads start at its lane base plus the offset; rows 0..WARPS-1 of the
+                // allocation are zero (the pad rows above plane 0), one per warp
+                const long long zero_rows = -(a.origin + (long long)y0 * a.pitch + xw);
+                if (debug_in(vi * NJP + jj, TAB, 5)) s_tab4[vi * NJP + jj] = (int)(mask ? g : zero_rows);
+            } else {
+                E e;
+                e.idx = (I)g;
+                e.info = mask;
+                if constexpr (STORAGE != KB_F32) e.sc = sc_of(exp_scale(scale_exp(a.scales[ep])));
+                if (debug_in(vi * NJP + jj, TAB, 5)) s_tab[vi * NJP + jj] = e;
+            }
             if constexpr (PRUNE)   // the CTA's first row; a warp adds warp * RW
                 s_rid[vi * NJP + jj] = mask ? (I)(((long long)ep * a.H + y0 + oy) * RW + ((xw + ox) >> 5) + SPAN / 32)
                                             : (I)0;
@@ -523,7 +541,68 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
             float2 acc[PX];
 #pragma unroll
             for (int p = 0; p < PX; ++p) acc[p] = acc0[p];
-            if constexpr (!LONG) {
+            if constexpr (CE && !LONG) {
+                // epochs in batches of C loads in flight (offsets four to a shared load), then
+                // one at a time
+                const int *tab4 = s_tab4 + vi * NJP;
+                int jj = 0;
+                for (; jj + C <= NJ; jj += C) {
+                    LT val[C][P];
+#pragma unroll
+                    for (int q4 = 0; q4 < C; q4 += 4) {
+                        const int4 o = *reinterpret_cast<const int4 *>(tab4 + jj + q4);
+                        const int oo[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const LT *src = reinterpret_cast<const LT *>(planes_t + oo[h]);
+#pragma unroll
+                            for (int p = 0; p < P; ++p) val[q4 + h][p] = gather(src + 32 * p, planes, a.planes_elems, 2);
+                        }
+                    }
+#pragma unroll
+                    for (int q2 = 0; q2 < C; ++q2) {
+#pragma unroll
+                        for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[q2][p], 0u);
+                    }
+                }
+                for (; jj < NJ; ++jj) {
+                    const LT *src = reinterpret_cast<const LT *>(planes_t + tab4[jj]);
+                    LT val[P];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) val[p] = gather(src + 32 * p, planes, a.planes_elems, 3);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[p], 0u);
+                }
+            } else if constexpr (CE) {
+                // LONG: every batch of C predicated (warp-uniform), the row padding read but unused
+                const int *tab4 = s_tab4 + vi * NJP;
+                for (int jj = 0; jj < NJ; jj += C) {
+                    LT val[C][P];
+#pragma unroll
+                    for (int q4 = 0; q4 < C; q4 += 4) {
+                        if (jj + q4 < NJ) {
+                            const int4 o = *reinterpret_cast<const int4 *>(tab4 + jj + q4);
+                            const int oo[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                if (jj + q4 + h < NJ) {
+                                    const LT *src = reinterpret_cast<const LT *>(planes_t + oo[h]);
+#pragma unroll
+                                    for (int p = 0; p < P; ++p)
+                                        val[q4 + h][p] = gather(src + 32 * p, planes, a.planes_elems, 4);
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int q2 = 0; q2 < C; ++q2) {
+                        if (jj + q2 < NJ) {
+#pragma unroll
+                            for (int p = 0; p < P; ++p) G::acc(acc + p * G::PIX, val[q2][p], 0u);
+                        }
+                    }
+                }
+            } else if constexpr (!LONG) {
                 // epochs in batches of C loads in flight, then one at a time
                 int jj = 0;
                 for (; jj + C <= NJ; jj += C) {

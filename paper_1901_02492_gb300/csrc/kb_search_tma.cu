@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(TTHREADS) search_tma_kernel(const __grid_const
                             const int sh = xs & (Tl::AL - 1);
                             flag[s] = sh;
                             mbar_arrive_expect_tx(full + s, Tl::BOX_BYTES);
-                            tma_load_3d(slots + (size_t)s * Tl::SLOT, &tmap, full + s, a.pad_x + xs - sh, ys,
+                            tma_load_3d(slots + (size_t)s * Tl::SLOT, &tmap, full + s, a.pad_x + xs - sh, a.pad_y + ys,
                                         s_epoch[n0 + jj]);
                         } else {
                             flag[s] = -1;
