@@ -208,6 +208,18 @@ struct Entry<long long, true> {
     int info;
     uint32_t sc;
 };
+// FP32 planes, 32-bit offsets, no pruning: compact 4-byte entries (search_tile), twice as
+// many per chunk of the table in the same shared bytes
+template <int STORAGE, typename I, bool PRUNE>
+__host__ __device__ constexpr bool compact_entries() { return STORAGE == KB_F32 && sizeof(I) == 4 && !PRUNE; }
+template <int STORAGE, typename I, bool PRUNE>
+__host__ __device__ constexpr int table_entries() {
+    return compact_entries<STORAGE, I, PRUNE>() ? 2 * tab_entries<STORAGE>() : tab_entries<STORAGE>();
+}
+template <int STORAGE, typename I, bool PRUNE>
+__host__ __device__ constexpr size_t table_entry_bytes() {
+    return compact_entries<STORAGE, I, PRUNE>() ? sizeof(int) : sizeof(Entry<I, STORAGE != KB_F32>);
+}
 template <typename I>
 __device__ __forceinline__ uint32_t entry_sc(const Entry<I, false> &) { return 0u; }
 template <typename I>
@@ -396,10 +408,11 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     // below make every warp's row of a band that overlaps the image's rows valid, so no
     // per-warp mask is needed; a band that misses the image gets the offset of the CTA's
     // rows of zeros above row 0 of plane 0 (any warp lands in them).
-    constexpr bool CE = STORAGE == KB_F32 && sizeof(I) == 4 && !PRUNE;
+    constexpr bool CE = compact_entries<STORAGE, I, PRUNE>();
     static_assert(!CE || C % 4 == 0, "compact entries are read four at a time");
     static_assert(WARPS <= kPadRows, "a band of warps' rows must fit the planes' zero rows");
-    constexpr int TAB = tab_entries<STORAGE>();
+    constexpr int TAB = table_entries<STORAGE, I, PRUNE>();
+    constexpr size_t EB = table_entry_bytes<STORAGE, I, PRUNE>();
     constexpr int PX = P * G::PIX;    // pixels per lane
     constexpr int SPAN = 32 * PX;     // pixels per warp row segment
     constexpr int LS = THREADS * PX;  // list columns (pixels) of the CTA
@@ -409,11 +422,11 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     // velocity ids [TAB] | list nu float [k * LS] | list vidx u16 [k * LS] | (8-byte aligned)
     // per-warp queues uint2 [WARPS][QCAP].
     E *s_tab = reinterpret_cast<E *>(s_dyn4);
-    I *s_rid = reinterpret_cast<I *>(s_tab + TAB);
+    I *s_rid = reinterpret_cast<I *>(reinterpret_cast<char *>(s_dyn4) + TAB * EB);
     int *s_vid = reinterpret_cast<int *>(s_rid + (PRUNE ? TAB : 0));
     const int N = a.N, n0 = a.n0, NJ = N - n0, k = a.k;
     // table row stride: even, so that entries pair into 16-byte loads; compact entries: a
-    // multiple of 4 (the table region keeps its size, the compact rows use its first half)
+    // multiple of 4, four to a 16-byte load
     const int NJP = CE ? (NJ + 3) & ~3 : (NJ + 1) & ~1;
     int *s_tab4 = reinterpret_cast<int *>(s_dyn4);
     float *s_ln = reinterpret_cast<float *>(s_vid + TAB);
@@ -421,7 +434,7 @@ __device__ __forceinline__ void search_tile(const SearchArgs &a, int bx, int by,
     uint32_t *s_lk = reinterpret_cast<uint32_t *>(s_vid + TAB);   // KEYS: the lists instead
     constexpr size_t kSlotBytes = KEYS ? sizeof(uint32_t) : sizeof(float) + sizeof(uint16_t);
     uint2 *s_q = reinterpret_cast<uint2 *>(s_dyn4) +
-                 ((TAB * (sizeof(E) + sizeof(int) + (PRUNE ? sizeof(I) : 0)) + (size_t)k * LS * kSlotBytes + 7) / 8);
+                 ((TAB * (EB + sizeof(int) + (PRUNE ? sizeof(I) : 0)) + (size_t)k * LS * kSlotBytes + 7) / 8);
 
     for (int j = threadIdx.x; j < N; j += THREADS)
         s_scale[j] = (STORAGE == KB_F32) ? make_float2(1.0f, 1.0f) : exp_scale(scale_exp(a.scales[a.epoch_of[j]]));
@@ -869,8 +882,8 @@ __global__ void __launch_bounds__(THREADS, min_ctas_batch<STORAGE, P>())
 template <int STORAGE, int P, typename I, bool PRUNE = false, bool KEYS = false>
 size_t tile_smem(int k) {
     constexpr int PX = P * Gather<STORAGE>::PIX;
-    const size_t base = (size_t)tab_entries<STORAGE>() *
-                            (sizeof(Entry<I, STORAGE != KB_F32>) + sizeof(int) + (PRUNE ? sizeof(I) : 0)) +
+    const size_t base = (size_t)table_entries<STORAGE, I, PRUNE>() *
+                            (table_entry_bytes<STORAGE, I, PRUNE>() + sizeof(int) + (PRUNE ? sizeof(I) : 0)) +
                         (size_t)k * THREADS * PX * (KEYS ? sizeof(uint32_t) : sizeof(float) + sizeof(uint16_t));
     return (base + 7) / 8 * 8 + (size_t)WARPS * 32 * (PX + 1) * sizeof(uint2);
 }
