@@ -837,7 +837,8 @@ constexpr int min_ctas_batch() {
 }
 
 template <int STORAGE, int P, int C, bool LONG, typename I, bool PRUNE, bool KEYS>
-__global__ void __launch_bounds__(THREADS, min_ctas<STORAGE, P, C, LONG>()) search_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(THREADS, (PRUNE && min_ctas<STORAGE, P, C, LONG>() == 5) ? 4 : min_ctas<STORAGE, P, C, LONG>())
+    search_kernel(SearchArgs a) {
     __shared__ float2 s_scale[KB_MAX_EPOCHS];
     extern __shared__ int4 s_dyn4[];
     int bx = blockIdx.x, by = blockIdx.y;
